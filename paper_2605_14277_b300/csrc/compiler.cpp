@@ -1,0 +1,504 @@
+// Host game compiler: flat game trees -> level-sorted CSR/segment layout.
+//
+// Builds, per player, the tree-form sequential decision process of each game
+// (decision points = infosets, sequences (j, a), parent sequence p_j; Sec. 2.1),
+// the payoff matrix M[s1, s2] = sum over terminals z with those sequences of
+// chance reach * u1(z) (two-player utilities as one sparse product, Sec. 2.1),
+// and the breadth-first forest numbering described in layout.h.  The logic
+// matrices A, B, C and the level graphs L^(d) of Sec. 3.1-3.2 are not stored
+// as matrices: each has at most one nonzero per column, so each becomes an
+// index array (inf_seq, seq_child, inf_par) over the breadth-first order.
+// Finally each player's levels are cut into work items that fit one
+// shared-memory buffer of the CUDA passes.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "layout.h"
+
+namespace cfrb {
+
+namespace {
+
+enum { K_CHANCE = 0, K_P1 = 1, K_P2 = 2, K_TERM = 3 };
+
+struct PlayerSF {
+    int32_t J = 0, S = 0;
+    std::vector<int32_t> nact, off, par;    // per caller infoset; par = caller seq, -1 = empty
+    std::vector<int32_t> kid_ptr, kid_inf;  // child infosets of caller seq s at kid_ptr[s+1]..; [0] = empty
+};
+
+struct GameSF {
+    PlayerSF p[2];
+    std::vector<int32_t> ts1, ts2;          // caller seq of each terminal, -1 = empty
+    std::vector<double> tw;                 // chance reach * payoff
+    double range = 0.0;
+    int64_t nodes = 0;
+};
+
+bool fail(std::string *err, const std::string &m) {
+    if (err) *err = m;
+    return false;
+}
+
+bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
+    const int64_t n = t.n_nodes;
+    g->nodes = n;
+    if (n < 1) return fail(err, "empty tree");
+    if (t.parent[0] != -1) return fail(err, "node 0 must be the root (parent -1)");
+    std::vector<int32_t> nch(n, 0);
+    for (int64_t i = 0; i < n; i++) {
+        const int k = t.kind[i];
+        if (k < 0 || k > 3) return fail(err, "bad node kind at " + std::to_string(i));
+        if (i > 0) {
+            const int64_t q = t.parent[i];
+            if (q < 0 || q >= i) return fail(err, "parent must precede child at " + std::to_string(i));
+            if (t.kind[q] == K_TERM) return fail(err, "terminal with children at " + std::to_string(q));
+            nch[q]++;
+        }
+        if ((k == K_P1 || k == K_P2) && t.infoset[i] < 0)
+            return fail(err, "decision node without infoset at " + std::to_string(i));
+        if (k == K_TERM && !std::isfinite(t.payoff[i]))
+            return fail(err, "non-finite payoff at " + std::to_string(i));
+    }
+    for (int64_t i = 0; i < n; i++)
+        if (t.kind[i] != K_TERM && nch[i] == 0)
+            return fail(err, "non-terminal without children at " + std::to_string(i));
+    // action labels 0..nch-1 once each; chance probabilities valid
+    {
+        std::vector<int64_t> coff(n + 1, 0);
+        for (int64_t i = 0; i < n; i++) coff[i + 1] = coff[i] + nch[i];
+        std::vector<uint8_t> seen(n > 1 ? n - 1 : 1, 0);
+        std::vector<double> psum(n, 0.0);
+        for (int64_t i = 1; i < n; i++) {
+            const int64_t q = t.parent[i];
+            const int32_t a = t.action[i];
+            if (a < 0 || a >= nch[q]) return fail(err, "action label out of range at " + std::to_string(i));
+            if (seen[coff[q] + a]) return fail(err, "duplicate action label below " + std::to_string(q));
+            seen[coff[q] + a] = 1;
+            if (t.kind[q] == K_CHANCE) {
+                const double pr = t.chance_prob[i];
+                if (!(pr >= 0.0 && pr <= 1.0)) return fail(err, "bad chance probability at " + std::to_string(i));
+                psum[q] += pr;
+            }
+        }
+        for (int64_t i = 0; i < n; i++)
+            if (t.kind[i] == K_CHANCE && std::fabs(psum[i] - 1.0) > 1e-9)
+                return fail(err, "chance probabilities do not sum to 1 at " + std::to_string(i));
+    }
+    // per player infosets and caller sequence numbering
+    for (int p = 0; p < 2; p++) {
+        PlayerSF &P = g->p[p];
+        const int kp = p + 1;
+        int64_t J = 0;
+        for (int64_t i = 0; i < n; i++)
+            if (t.kind[i] == kp) J = std::max<int64_t>(J, (int64_t)t.infoset[i] + 1);
+        if (J > INT32_MAX / 2) return fail(err, "too many infosets");
+        P.J = (int32_t)J;
+        P.nact.assign(J, 0);
+        P.par.assign(J, INT32_MIN);
+        for (int64_t i = 0; i < n; i++) {
+            if (t.kind[i] != kp) continue;
+            const int32_t j = t.infoset[i];
+            if (P.nact[j] == 0) P.nact[j] = nch[i];
+            else if (P.nact[j] != nch[i]) return fail(err, "infoset action-count mismatch");
+        }
+        P.off.assign(J, 0);
+        int64_t s = 0;
+        for (int64_t j = 0; j < J; j++) {
+            if (P.nact[j] == 0) return fail(err, "infoset ids are not dense");
+            P.off[j] = (int32_t)s;
+            s += P.nact[j];
+        }
+        if (s > INT32_MAX / 2) return fail(err, "too many sequences");
+        P.S = (int32_t)s;
+    }
+    // own sequence per node (top-down; parents precede children), chance reach
+    std::vector<int32_t> seq1(n, -1), seq2(n, -1);
+    std::vector<double> reach(n, 1.0);
+    for (int64_t i = 1; i < n; i++) {
+        const int64_t q = t.parent[i];
+        const int kq = t.kind[q];
+        seq1[i] = (kq == K_P1) ? g->p[0].off[t.infoset[q]] + t.action[i] : seq1[q];
+        seq2[i] = (kq == K_P2) ? g->p[1].off[t.infoset[q]] + t.action[i] : seq2[q];
+        reach[i] = reach[q] * (kq == K_CHANCE ? t.chance_prob[i] : 1.0);
+    }
+    // parent sequence per infoset: all nodes of an infoset must agree (perfect recall)
+    for (int64_t i = 0; i < n; i++) {
+        const int k = t.kind[i];
+        if (k != K_P1 && k != K_P2) continue;
+        PlayerSF &P = g->p[k - 1];
+        const int32_t own = (k == K_P1) ? seq1[i] : seq2[i];
+        int32_t &pj = P.par[t.infoset[i]];
+        if (pj == INT32_MIN) pj = own;
+        else if (pj != own)
+            return fail(err, "imperfect recall: infoset " + std::to_string(t.infoset[i]) + " of player " +
+                                 std::to_string(k) + " has two parent sequences");
+    }
+    // children of each caller sequence (index 0 = empty sequence), sorted by
+    // infoset id; a cycle leaves infosets unreachable, which the forest
+    // numbering detects
+    for (int p = 0; p < 2; p++) {
+        PlayerSF &P = g->p[p];
+        P.kid_ptr.assign((size_t)P.S + 2, 0);
+        for (int32_t j = 0; j < P.J; j++) P.kid_ptr[P.par[j] + 2]++;
+        for (int64_t s = 1; s < (int64_t)P.S + 2; s++) P.kid_ptr[s] += P.kid_ptr[s - 1];
+        P.kid_inf.assign(P.J, 0);
+        std::vector<int32_t> fill(P.kid_ptr.begin(), P.kid_ptr.end() - 1);
+        for (int32_t j = 0; j < P.J; j++) P.kid_inf[fill[P.par[j] + 1]++] = j;
+    }
+    // terminals
+    double mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        if (t.kind[i] != K_TERM) continue;
+        g->ts1.push_back(seq1[i]);
+        g->ts2.push_back(seq2[i]);
+        g->tw.push_back(reach[i] * t.payoff[i]);
+        mn = std::min(mn, t.payoff[i]);
+        mx = std::max(mx, t.payoff[i]);
+    }
+    g->range = g->ts1.empty() ? 0.0 : mx - mn;
+    return true;
+}
+
+template <class F>
+void parallel_for(int64_t n, F f) {
+    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 32u));
+    if (n < 4 || nt == 1) {
+        for (int64_t i = 0; i < n; i++) f(i);
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> th;
+    for (unsigned k = 0; k < nt; k++)
+        th.emplace_back([&]() {
+            for (int64_t i; (i = next.fetch_add(1)) < n;) f(i);
+        });
+    for (auto &x : th) x.join();
+}
+
+}  // namespace
+
+int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, Layout *out, std::string *err) {
+    if (G < 1) {
+        if (err) *err = "no games";
+        return ST_INVALID;
+    }
+    std::vector<GameSF> gs(G);
+    std::vector<std::string> errs(G);
+    std::vector<char> ok(G, 0);
+    parallel_for(G, [&](int64_t g) { ok[g] = compile_game(games[g], &gs[g], &errs[g]); });
+    for (int64_t g = 0; g < G; g++)
+        if (!ok[g]) {
+            if (err) *err = "game " + std::to_string(g) + ": " + errs[g];
+            return ST_INVALID;
+        }
+    Layout &L = *out;
+    L.G = G;
+    L.game_nodes.resize(G);
+    L.game_range.resize(G);
+    for (int64_t g = 0; g < G; g++) {
+        L.game_nodes[g] = gs[g].nodes;
+        L.game_range[g] = gs[g].range;
+    }
+    // caller seq -> forest seq, per game and player
+    std::vector<std::vector<int32_t>> gseq[2];
+    // per player, per game, per level: infoset range
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> glvs[2];
+    for (int p = 0; p < 2; p++) {
+        PlayerLayout &P = L.pl[p];
+        gseq[p].resize(G);
+        int64_t S = G, J = G;
+        for (int64_t g = 0; g < G; g++) {
+            S += gs[g].p[p].S;
+            J += gs[g].p[p].J;
+            gseq[p][g].assign(gs[g].p[p].S, -1);
+        }
+        if (S >= INT32_MAX || J >= INT32_MAX) {
+            if (err) *err = "forest too large for 32-bit indices";
+            return ST_INVALID;
+        }
+        P.S = S;
+        P.J = J;
+        P.inf_seq.assign(J + 1, 0);
+        P.seq_child.assign(S + 1, 0);
+        P.inf_par.assign(J, -1);
+        P.seq_game.assign(S, 0);
+        P.game_J.resize(G);
+        P.game_S.resize(G);
+        P.game_jbase.assign(G + 1, 0);
+        P.game_sbase.assign(G + 1, 0);
+        for (int64_t g = 0; g < G; g++) {
+            P.game_J[g] = gs[g].p[p].J;
+            P.game_S[g] = gs[g].p[p].S;
+            P.game_jbase[g + 1] = P.game_jbase[g] + gs[g].p[p].J;
+            P.game_sbase[g + 1] = P.game_sbase[g] + gs[g].p[p].S;
+        }
+        P.ext_inf.assign(P.game_jbase[G], -1);
+        P.ext_seq0.assign(P.game_jbase[G], 0);
+        // breadth-first numbering over the forest.  A frontier entry is
+        // (game, caller seq or -1, forest seq).
+        struct Fr {
+            int32_t g, cs, fs;
+        };
+        std::vector<Fr> cur, nxt;
+        int32_t jn = 0, sn = 0;
+        std::vector<int32_t> lvl_lo;   // first infoset of each level
+        for (int64_t g = 0; g < G; g++) {   // level 0: one root pseudo-infoset per game
+            P.inf_seq[jn] = sn;
+            P.inf_par[jn] = -1;
+            P.seq_game[sn] = (int32_t)g;
+            cur.push_back({(int32_t)g, -1, sn});
+            jn++;
+            sn++;
+        }
+        lvl_lo.push_back(0);
+        while (!cur.empty()) {
+            lvl_lo.push_back(jn);   // start of the level created in this pass
+            nxt.clear();
+            for (const Fr &f : cur) {
+                const PlayerSF &Q = gs[f.g].p[p];
+                P.seq_child[f.fs] = jn;
+                for (int32_t k = Q.kid_ptr[f.cs + 1]; k < Q.kid_ptr[f.cs + 2]; k++) {
+                    const int32_t jx = Q.kid_inf[k];
+                    P.inf_seq[jn] = sn;
+                    P.inf_par[jn] = f.fs;
+                    const int64_t e = P.game_jbase[f.g] + jx;
+                    P.ext_inf[e] = jn;
+                    P.ext_seq0[e] = Q.off[jx];
+                    for (int32_t a = 0; a < Q.nact[jx]; a++) {
+                        gseq[p][f.g][Q.off[jx] + a] = sn;
+                        P.seq_game[sn] = f.g;
+                        nxt.push_back({f.g, Q.off[jx] + a, sn});
+                        sn++;
+                    }
+                    P.max_actions = std::max(P.max_actions, Q.nact[jx]);
+                    jn++;
+                }
+            }
+            cur.swap(nxt);
+        }
+        if (jn != J || sn != S) {
+            if (err)
+                *err = "player " + std::to_string(p + 1) +
+                       ": infosets unreachable from the root (cyclic parent sequences)";
+            return ST_INVALID;
+        }
+        P.inf_seq[J] = sn;
+        P.seq_child[S] = jn;
+        for (int64_t s = 1; s <= S; s++)
+            if (P.seq_child[s] < P.seq_child[s - 1]) {
+                if (err) *err = "internal: non-monotone child pointers";
+                return ST_INVALID;
+            }
+        // the last pass created an empty level whose start closes the list
+        P.n_levels = (int32_t)lvl_lo.size() - 1;
+        // per game, per level infoset ranges
+        auto &glv = glvs[p];
+        glv.assign(G, {});
+        for (int32_t d = 0; d < P.n_levels; d++) {
+            int32_t j = lvl_lo[d];
+            const int32_t e = lvl_lo[d + 1];
+            while (j < e) {
+                const int32_t g = P.seq_game[P.inf_seq[j]];
+                int32_t k = j;
+                while (k < e && P.seq_game[P.inf_seq[k]] == g) k++;
+                glv[g].push_back({j, k});
+                j = k;
+            }
+        }
+    }
+    // ---- payoff matrix in forest numbering, CSR by player-1 rows and by player-2 rows
+    int64_t Z0 = 0;
+    for (int64_t g = 0; g < G; g++) Z0 += (int64_t)gs[g].tw.size();
+    if (Z0 >= INT32_MAX) {
+        if (err) *err = "too many terminals for 32-bit offsets";
+        return ST_INVALID;
+    }
+    auto fseq = [&](int p, int64_t g, int32_t cs) -> int32_t { return cs < 0 ? (int32_t)g : gseq[p][g][cs]; };
+    {
+        PlayerLayout &A = L.pl[0];
+        std::vector<int32_t> cnt(A.S + 1, 0);
+        for (int64_t g = 0; g < G; g++)
+            for (size_t z = 0; z < gs[g].tw.size(); z++) cnt[fseq(0, g, gs[g].ts1[z]) + 1]++;
+        for (int64_t s = 0; s < A.S; s++) cnt[s + 1] += cnt[s];
+        std::vector<int32_t> col(Z0);
+        std::vector<double> val(Z0);
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t g = 0; g < G; g++)
+            for (size_t z = 0; z < gs[g].tw.size(); z++) {
+                const int32_t r = fseq(0, g, gs[g].ts1[z]);
+                const int32_t k = fill[r]++;
+                col[k] = fseq(1, g, gs[g].ts2[z]);
+                val[k] = gs[g].tw[z];
+            }
+        // merge duplicates within each row (sorted by column, stable)
+        A.m_ptr.assign(A.S + 1, 0);
+        A.m_col.clear();
+        A.m_val64.clear();
+        std::vector<std::pair<int32_t, double>> row;
+        for (int64_t r = 0; r < A.S; r++) {
+            row.clear();
+            for (int32_t k = cnt[r]; k < cnt[r + 1]; k++) row.push_back({col[k], val[k]});
+            std::stable_sort(row.begin(), row.end(),
+                             [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                                 return a.first < b.first;
+                             });
+            for (size_t k = 0; k < row.size(); k++) {
+                if ((int64_t)A.m_col.size() > A.m_ptr[r] && A.m_col.back() == row[k].first)
+                    A.m_val64.back() += row[k].second;
+                else {
+                    A.m_col.push_back(row[k].first);
+                    A.m_val64.push_back(row[k].second);
+                }
+            }
+            A.m_ptr[r + 1] = (int32_t)A.m_col.size();
+        }
+        L.Z = (int64_t)A.m_col.size();
+        A.m_val.resize(L.Z);
+        for (int64_t k = 0; k < L.Z; k++) A.m_val[k] = (float)A.m_val64[k];
+        // transpose for player-2 rows
+        PlayerLayout &B = L.pl[1];
+        B.m_ptr.assign(B.S + 1, 0);
+        for (int64_t k = 0; k < L.Z; k++) B.m_ptr[A.m_col[k] + 1]++;
+        for (int64_t s = 0; s < B.S; s++) B.m_ptr[s + 1] += B.m_ptr[s];
+        B.m_col.resize(L.Z);
+        B.m_val64.resize(L.Z);
+        B.m_val.resize(L.Z);
+        std::vector<int32_t> f2(B.m_ptr.begin(), B.m_ptr.end() - 1);
+        for (int64_t r = 0; r < A.S; r++)
+            for (int32_t k = A.m_ptr[r]; k < A.m_ptr[r + 1]; k++) {
+                const int32_t q = f2[A.m_col[k]]++;
+                B.m_col[q] = (int32_t)r;
+                B.m_val64[q] = A.m_val64[k];
+                B.m_val[q] = A.m_val[k];
+            }
+    }
+    // ---- work items: a cut level per game and player, subtrees below it packed
+    // into units that fit one shared-memory buffer -------------------------
+    for (int p = 0; p < 2; p++) {
+        PlayerLayout &P = L.pl[p];
+        const auto &glv = glvs[p];
+        const int64_t J = P.J;
+        // per-infoset subtree footprint (raw bytes, without per-level slack)
+        std::vector<int64_t> raw_up(J, 0);
+        for (int64_t j = J - 1; j >= 0; j--) {
+            int64_t u = 8 + 8;   // infoset: segment pointer + ev
+            for (int32_t q = P.inf_seq[j]; q < P.inf_seq[j + 1]; q++) {
+                const int64_t nz = P.m_ptr[q + 1] - P.m_ptr[q];
+                u += 24 + 8 * nz;
+                for (int32_t c = P.seq_child[q]; c < P.seq_child[q + 1]; c++) u += raw_up[c];
+            }
+            raw_up[j] = u;
+        }
+        int64_t total_raw = 0;
+        for (int64_t g = 0; g < G; g++) total_raw += raw_up[g];
+        // item size: enough items for ~2 per resident CTA, within the buffer
+        const int64_t slack_per_level = 8 * 48;
+        int64_t target = total_raw / std::max<int64_t>(1, 2 * opt.slots);
+        target = std::max(opt.min_item_bytes, std::min(target, opt.item_bytes));
+        P.game_nitems.assign(G, 0);
+        P.game_cut.assign(G, 1);
+        P.trunks.resize(G);
+        P.items.clear();
+        P.ranges.clear();
+        auto push_level = [&](int32_t j0, int32_t j1) {
+            const int32_t s0 = P.inf_seq[j0], s1 = P.inf_seq[j1];
+            P.ranges.push_back(j0);
+            P.ranges.push_back(j1);
+            P.ranges.push_back(s0);
+            P.ranges.push_back(s1);
+            P.ranges.push_back(P.m_ptr[s0]);
+            P.ranges.push_back(P.m_ptr[s1]);
+        };
+        for (int64_t g = 0; g < G; g++) {
+            const auto &lv = glv[g];
+            const int32_t nl = (int32_t)lv.size();   // levels 0..nl-1
+            // the shallowest cut whose subtrees all fit the item target with a
+            // trunk of at most trunk_max sequences; otherwise the cut with the
+            // smallest largest subtree among those with a small trunk
+            int32_t c = 1;
+            if (nl > 1) {
+                int64_t trunk = 0;
+                int32_t best = -1, fallback = 1;
+                int64_t fb_mx = INT64_MAX;
+                for (int32_t cc = 1; cc < nl; cc++) {
+                    trunk += P.inf_seq[lv[cc - 1].second] - P.inf_seq[lv[cc - 1].first];
+                    if (cc > 1 && trunk > opt.trunk_max) break;
+                    int64_t mx = 0;
+                    for (int32_t j = lv[cc].first; j < lv[cc].second; j++) mx = std::max(mx, raw_up[j]);
+                    const int64_t need = mx + slack_per_level * (nl - cc);
+                    if (need <= target && best < 0) best = cc;
+                    if (mx < fb_mx) {
+                        fb_mx = mx;
+                        fallback = cc;
+                    }
+                }
+                c = best > 0 ? best : fallback;
+            }
+            c = std::min(c, std::max(1, nl));
+            P.game_cut[g] = c;
+            P.trunks[g] = {(int32_t)g, 0, std::min(c, nl), (int32_t)P.ranges.size(), 0};
+            for (int32_t d = 0; d < std::min(c, nl); d++) push_level(lv[d].first, lv[d].second);
+            auto emit = [&](int32_t a, int32_t b) {
+                Item it{(int32_t)g, c, 0, (int32_t)P.ranges.size(), 0};
+                int32_t lo = a, hi = b;
+                int64_t fu = 0, fd = 0;
+                while (lo < hi) {
+                    push_level(lo, hi);
+                    const int32_t slo = P.inf_seq[lo], shi = P.inf_seq[hi];
+                    fu += up_level_bytes(shi - slo, hi - lo, P.m_ptr[shi] - P.m_ptr[slo]);
+                    fd += down_level_bytes(shi - slo, hi - lo);
+                    it.nlvl++;
+                    lo = P.seq_child[slo];
+                    hi = P.seq_child[shi];
+                }
+                if (it.nlvl <= kMaxStagedLevels && fu <= opt.item_bytes && fd <= opt.item_bytes) it.flags |= kStaged;
+                P.items.push_back(it);
+                P.game_nitems[g]++;
+            };
+            if (c >= nl) {
+                emit(0, 0);   // nothing below the cut: an empty item still triggers the trunk
+            } else {
+                const int64_t cap = std::max<int64_t>(target - slack_per_level * (nl - c), 1);
+                int32_t a = lv[c].first;
+                int64_t acc = 0;
+                for (int32_t j = lv[c].first; j < lv[c].second; j++) {
+                    if (acc > 0 && acc + raw_up[j] > cap) {
+                        emit(a, j);
+                        a = j;
+                        acc = 0;
+                    }
+                    acc += raw_up[j];
+                }
+                emit(a, lv[c].second);
+            }
+        }
+        // largest items first: a dynamic queue then finishes with small ones
+        std::vector<int64_t> isz(P.items.size());
+        for (size_t k = 0; k < P.items.size(); k++) {
+            const Item &it = P.items[k];
+            int64_t s = 0;
+            for (int32_t d = 0; d < it.nlvl; d++)
+                s += P.ranges[it.rng + kLvl * d + 3] - P.ranges[it.rng + kLvl * d + 2] +
+                     P.ranges[it.rng + kLvl * d + 5] - P.ranges[it.rng + kLvl * d + 4];
+            isz[k] = s;
+        }
+        std::vector<size_t> ord(P.items.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return isz[a] > isz[b]; });
+        std::vector<Item> sorted;
+        sorted.reserve(ord.size());
+        for (size_t k : ord) sorted.push_back(P.items[k]);
+        P.items.swap(sorted);
+    }
+    L.game_nnz.assign(G, 0);
+    for (int64_t r = 0; r < L.pl[0].S; r++)
+        L.game_nnz[L.pl[0].seq_game[r]] += L.pl[0].m_ptr[r + 1] - L.pl[0].m_ptr[r];
+    return ST_OK;
+}
+
+}  // namespace cfrb

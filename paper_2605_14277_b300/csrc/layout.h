@@ -1,0 +1,106 @@
+// Host-side layout of a forest of games for the CUDA passes.
+//
+// Every per-player vector follows one numbering, a breadth-first order over
+// the forest of all loaded games: level 0 holds one pseudo-infoset per game
+// (the root, whose single sequence is the empty sequence of that game), level
+// d holds the infosets whose parent sequence is at level d-1, sorted by parent
+// sequence.  Sequences are numbered in infoset order.  With that order:
+//   * the sequences of infoset j are [inf_seq[j], inf_seq[j+1])            (logic matrix C, Sec. 3.1)
+//   * the child infosets of sequence s are [seq_child[s], seq_child[s+1])  (level graphs L^(d), Sec. 3.2)
+//   * within one level, each game's infosets are contiguous, and so is each
+//     subtree below a cut level: a work item is one contiguous range per level.
+#pragma once
+#include <cstdint>
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+#include <string>
+#include <vector>
+
+namespace cfrb {
+
+struct TreeView {
+    int64_t n_nodes;
+    const int32_t *parent;
+    const int8_t *kind;
+    const int32_t *infoset;
+    const int32_t *action;
+    const double *chance_prob;
+    const double *payoff;
+};
+
+// one unit of work: levels [lvl0, lvl0 + nlvl) of one game.  Level k of the
+// unit is described by kLvl ints at ranges[rng + kLvl * k]:
+//   infosets [j0, j1), sequences [s0, s1), payoff nonzeros [n0, n1)
+// (rows s0..s1 of this player's payoff CSR), so a kernel can issue every copy
+// of the unit without first reading index arrays.
+constexpr int kLvl = 6;
+struct Item {
+    int32_t game, lvl0, nlvl, rng;
+    int32_t flags;   // kStaged: the unit fits a shared-memory buffer
+};
+constexpr int kStaged = 1;
+constexpr int kMaxStagedLevels = 24;
+
+// Shared-memory bytes a staged unit level needs (host and device agree on
+// these): copied ranges get 32 bytes of slack for 16-byte alignment.
+__host__ __device__ inline int64_t span16(int64_t n, int e) { return (n * e + 32 + 15) / 16 * 16; }
+__host__ __device__ inline int64_t work16(int64_t n, int e) { return (n * e + 15) / 16 * 16; }
+__host__ __device__ inline int64_t up_level_bytes(int64_t ns, int64_t ni, int64_t nz) {
+    // r (float2), b, seq_child, payoff row pointers, infoset segments, payoff
+    // columns, payoff values; work: V per sequence, ev per infoset
+    return span16(ns, 8) + span16(ns, 4) + 2 * span16(ns + 1, 4) + span16(ni + 1, 4) + 2 * span16(nz, 4) +
+           work16(ns, 4) + work16(ni, 4);
+}
+__host__ __device__ inline int64_t down_level_bytes(int64_t ns, int64_t ni) {
+    // b, x, xbar (float2), infoset parents, infoset segments
+    return 2 * span16(ns, 4) + span16(ns, 8) + span16(ni, 4) + span16(ni + 1, 4);
+}
+
+struct PlayerLayout {
+    int64_t S = 0, J = 0;               // forest totals (including the G empty sequences / roots)
+    int32_t n_levels = 0;
+    std::vector<int32_t> inf_seq;       // [J + 1]
+    std::vector<int32_t> seq_child;     // [S + 1]
+    std::vector<int32_t> inf_par;       // [J]   parent sequence, -1 for roots
+    std::vector<int32_t> seq_game;      // [S]
+    std::vector<int32_t> m_ptr;         // [S + 1] payoff rows indexed by this player's sequence
+    std::vector<int32_t> m_col;         // [Z]     other player's sequence
+    std::vector<float> m_val;           // [Z]     sum over terminals of chance reach * u1
+    std::vector<double> m_val64;        // [Z]
+    std::vector<Item> items;            // bulk work items (levels >= cut)
+    std::vector<Item> trunks;           // per game: levels [0, cut)
+    std::vector<int32_t> ranges;        // kLvl ints per level of every item and trunk
+    std::vector<int32_t> game_nitems;   // [G]
+    std::vector<int32_t> game_cut;      // [G]
+    // caller order: game g's caller infoset k is ext_inf[game_jbase[g] + k]; its
+    // sequences start at caller index ext_seq0[game_jbase[g] + k]
+    std::vector<int32_t> ext_inf, ext_seq0;
+    std::vector<int64_t> game_jbase, game_sbase;   // caller-order prefix sums over games
+    std::vector<int32_t> game_J, game_S;           // caller counts per game
+    int32_t max_actions = 0;
+};
+
+struct Layout {
+    int64_t G = 0, Z = 0;
+    PlayerLayout pl[2];
+    std::vector<int64_t> game_nodes;
+    std::vector<int64_t> game_nnz;
+    std::vector<double> game_range;     // max u1 - min u1 over terminals
+};
+
+struct CompileOptions {
+    int64_t item_bytes = 96 * 1024;    // shared-memory buffer of one staged work item
+    int64_t min_item_bytes = 8 * 1024; // smallest item the packer aims for
+    int64_t slots = 148;               // CTAs resident at once (items are sized to give each ~2)
+    int64_t trunk_max = 8192;          // most sequences a trunk may hold when a deeper cut is possible
+};
+
+// status codes shared with the C ABI
+enum { ST_OK = 0, ST_INVALID = -1, ST_OOM = -2 };
+
+int compile_forest(const TreeView *games, int64_t n_games, const CompileOptions &opt, Layout *out,
+                   std::string *err);
+
+}  // namespace cfrb

@@ -1,0 +1,241 @@
+"""Host game compiler: layout invariants and an FP64 replay of the kernels'
+schedule (units deepest level first, then each game's trunk, then top-down)
+over the compiled index arrays, checked against the oracle.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2605_14277_b300 import games as G
+from tests.layout_probe import Layout, down_bytes, up_bytes
+from tests.refimpl import SeqForm
+
+
+def small_set():
+    return [G.small_random_game(1), G.poker_game(), G.rps(),
+            G.random_game(5, depth=5, chance={0: 3, 3: 2}, actions=(2, 3), payoff="normal"),
+            G.matrix_game(G.random_2x2_no_saddle(1))]
+
+
+def check_invariants(lay, G_):
+    for p in (0, 1):
+        d = lay.pl[p]
+        inf_seq, seq_child, inf_par = d["inf_seq"], d["seq_child"], d["inf_par"]
+        J, S = inf_seq.shape[0] - 1, seq_child.shape[0] - 1
+        assert inf_seq[0] == 0 and inf_seq[-1] == S and (np.diff(inf_seq) >= 1).all()
+        assert seq_child[0] == G_ and seq_child[-1] == J and (np.diff(seq_child) >= 0).all()
+        assert (inf_par[:G_] == -1).all()
+        for j in range(G_, J):
+            q = inf_par[j]
+            assert seq_child[q] <= j < seq_child[q + 1]
+        # every infoset covered exactly once by trunks + items
+        cover = np.zeros(J, np.int64)
+        rng = d["ranges"]
+        unit_of = {}
+        for kind, units in (("trunk", d["trunks"]), ("item", d["items"])):
+            for ui, (g, lvl0, nlvl, r0, flags) in enumerate(units):
+                prev = None
+                for k in range(nlvl):
+                    lo, hi, s0, s1, n0, n1 = rng[r0 + 6 * k: r0 + 6 * k + 6]
+                    assert s0 == inf_seq[lo] and s1 == inf_seq[hi]
+                    assert n0 == d["m_ptr"][s0] and n1 == d["m_ptr"][s1]
+                    cover[lo:hi] += 1
+                    for j in range(lo, hi):
+                        unit_of[j] = (kind, ui, k)
+                    if prev is not None and hi > lo:
+                        ps = inf_par[lo:hi]
+                        assert (ps >= inf_seq[prev[0]]).all() and (ps < inf_seq[prev[1]]).all()
+                    prev = (lo, hi)
+        assert (cover == 1).all()
+        # an item's top level hangs below trunk sequences of the same game
+        for ui, (g, lvl0, nlvl, r0, flags) in enumerate(d["items"]):
+            if nlvl == 0:
+                continue
+            lo, hi = rng[r0], rng[r0 + 1]
+            for j in range(lo, hi):
+                pj = inf_par[j]
+                pinf = np.searchsorted(inf_seq, pj, side="right") - 1
+                assert unit_of[pinf][0] == "trunk" and d["trunks"][unit_of[pinf][1]][0] == g
+        assert np.bincount(d["items"][:, 0], minlength=G_).tolist() == d["game_nitems"].tolist()
+
+
+@pytest.mark.parametrize("item_bytes", [0, 600, 4000])
+def test_layout_invariants_single_and_batch(item_bytes):
+    trees = small_set()
+    for t in trees:
+        check_invariants(Layout([t], item_bytes=item_bytes), 1)
+    check_invariants(Layout(trees, item_bytes=item_bytes), len(trees))
+
+
+def test_staged_units_fit_their_buffer():
+    """every unit flagged as staged fits the shared-memory buffer (both passes)"""
+    for item_bytes in (2000, 8000, 96 * 1024):
+        lay = Layout([G.poker_game(), G.random_game(5, depth=5, chance={0: 3, 3: 2}, actions=(2, 3),
+                                                    payoff="normal")], item_bytes=item_bytes)
+        for p in (0, 1):
+            d = lay.pl[p]
+            n_staged = 0
+            for (g, lvl0, nlvl, r0, flags) in d["items"]:
+                rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
+                fu = sum(up_bytes(s1 - s0, j1 - j0, n1 - n0) for j0, j1, s0, s1, n0, n1 in rng)
+                fd = sum(down_bytes(s1 - s0, j1 - j0) for j0, j1, s0, s1, n0, n1 in rng)
+                if flags & 1:
+                    n_staged += 1
+                    assert fu <= item_bytes and fd <= item_bytes and nlvl <= 24
+            assert n_staged > 0
+
+
+def test_payoff_matrix_matches_sequence_form():
+    trees = small_set()
+    lay = Layout(trees, item_bytes=3000)
+    d1, d2 = lay.pl[0], lay.pl[1]
+    S1, S2 = d1["m_ptr"].shape[0] - 1, d2["m_ptr"].shape[0] - 1
+    M = np.zeros((S1, S2))
+    for r in range(S1):
+        for k in range(d1["m_ptr"][r], d1["m_ptr"][r + 1]):
+            M[r, d1["m_col"][k]] += d1["m_val64"][k]
+    MT = np.zeros((S2, S1))
+    for r in range(S2):
+        for k in range(d2["m_ptr"][r], d2["m_ptr"][r + 1]):
+            MT[r, d2["m_col"][k]] += d2["m_val64"][k]
+    assert np.array_equal(M, MT.T)
+    for g, t in enumerate(trees):
+        sf = SeqForm(t)
+        f1 = np.concatenate([[g], lay.caller_to_forest(0, g)])
+        f2 = np.concatenate([[g], lay.caller_to_forest(1, g)])
+        assert np.allclose(M[np.ix_(f1, f2)], sf.M, rtol=1e-15, atol=1e-15)
+        # no payoff between games
+        assert np.abs(M[np.ix_(f1, np.setdiff1d(np.arange(S2), f2))]).max(initial=0) == 0
+
+
+# ---------------------------------------------------------------- schedule replay
+
+class Sim:
+    """FP64 replay of the kernel schedule on the compiled layout."""
+
+    def __init__(self, lay, G_):
+        self.lay, self.G = lay, G_
+
+    def rows(self, p, xo, sign):
+        d = self.lay.pl[p]
+        ptr, col, val = d["m_ptr"], d["m_col"], d["m_val64"]
+        u = np.zeros(ptr.shape[0] - 1)
+        for r in range(u.shape[0]):
+            u[r] = sign * np.dot(val[ptr[r]:ptr[r + 1]], xo[col[ptr[r]:ptr[r + 1]]])
+        return u
+
+    def up(self, p, st, xo, sign, variant, t, alpha, beta):
+        d = self.lay.pl[p]
+        inf_seq, seq_child, rng = d["inf_seq"], d["seq_child"], d["ranges"]
+        u = self.rows(p, xo, sign)
+        ev = np.full(inf_seq.shape[0] - 1, np.nan)
+        r, b = st[p]["r"], st[p]["b"]
+
+        def step(j, tg):
+            s0, s1 = inf_seq[j], inf_seq[j + 1]
+            V = np.array([u[s] + ev[seq_child[s]:seq_child[s + 1]].sum() for s in range(s0, s1)])
+            assert not np.isnan(V).any()
+            e = float(b[s0:s1] @ V)
+            ev[j] = e
+            rn = r[s0:s1] + (V - e)
+            if variant in (1, 3):
+                rn = np.maximum(rn, 0.0)
+            elif variant == 2:
+                fp = tg ** alpha / (tg ** alpha + 1)
+                fn = tg ** beta / (tg ** beta + 1)
+                rn = np.where(rn > 0, rn * fp, np.where(rn < 0, rn * fn, rn))
+            r[s0:s1] = rn
+            q = rn + (V - e) if variant == 3 else rn
+            q = np.maximum(q, 0)
+            b[s0:s1] = q / q.sum() if q.sum() > 0 else 1.0 / (s1 - s0)
+
+        def run(unit):
+            g, lvl0, nlvl, r0, flags = unit
+            for k in range(nlvl - 1, -1, -1):
+                for j in range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]):
+                    step(j, t[g])
+
+        for it in d["items"]:
+            run(it)
+        xn = np.zeros_like(st[p]["x"])
+        for g in range(self.G):
+            tr = d["trunks"][g]
+            run(tr)
+            xn[g] = 1.0
+            for k in range(1, tr[2]):
+                for j in range(rng[tr[3] + 6 * k], rng[tr[3] + 6 * k + 1]):
+                    for s in range(inf_seq[j], inf_seq[j + 1]):
+                        xn[s] = xn[d["inf_par"][j]] * b[s]
+        st[p]["xn"] = xn
+
+    def down(self, p, st, w):
+        d = self.lay.pl[p]
+        inf_seq, rng, inf_par = d["inf_seq"], d["ranges"], d["inf_par"]
+        x, xn, xbar, b = st[p]["x"], st[p]["xn"], st[p]["xbar"], st[p]["b"]
+        for g in range(self.G):
+            tr = d["trunks"][g]
+            for k in range(tr[2]):
+                for s in range(inf_seq[rng[tr[3] + 6 * k]], inf_seq[rng[tr[3] + 6 * k + 1]]):
+                    xbar[s] += w[g] * x[s]
+                    x[s] = xn[s]
+        for (g, lvl0, nlvl, r0, flags) in d["items"]:
+            for k in range(nlvl):
+                src = xn if k == 0 else x
+                for j in range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]):
+                    for s in range(inf_seq[j], inf_seq[j + 1]):
+                        xbar[s] += w[g] * x[s]
+                        x[s] = src[inf_par[j]] * b[s]
+
+    def iteration(self, st, variant, alpha, beta, gamma, alternating, t_done):
+        t = t_done + 1.0
+        w = t ** gamma
+        if alternating:
+            self.up(0, st, st[1]["x"], 1.0, variant, t, alpha, beta)
+            self.down(0, st, w)
+            self.up(1, st, st[0]["x"], -1.0, variant, t, alpha, beta)
+            self.down(1, st, w)
+        else:
+            self.up(0, st, st[1]["x"], 1.0, variant, t, alpha, beta)
+            self.up(1, st, st[0]["x"], -1.0, variant, t, alpha, beta)
+            self.down(0, st, w)
+            self.down(1, st, w)
+
+
+@pytest.mark.parametrize("variant,alt", [(0, False), (1, True), (2, True), (3, True), (2, False)])
+def test_schedule_matches_oracle_one_iteration(variant, alt):
+    trees = [G.random_game(5, depth=5, chance={0: 3, 3: 2}, actions=(2, 3), payoff="normal"),
+             G.poker_game(), G.rps()]
+    lay = Layout(trees, item_bytes=5000)
+    rng = np.random.default_rng(7)
+    alpha, beta, gamma = 1.5, 0.0, 2.0
+    t0 = 4
+    st = {0: {}, 1: {}}
+    oracles = []
+    for p in (0, 1):
+        S = lay.pl[p]["inf_seq"][-1]
+        st[p] = {"r": np.zeros(S), "b": np.ones(S), "x": np.zeros(S), "xbar": np.zeros(S)}
+    for g, t in enumerate(trees):
+        o = Oracle(t)
+        for p in (0, 1):
+            f = lay.caller_to_forest(p, g)
+            r = rng.standard_normal(o.S[p + 1])
+            b = o.regret_matching(p + 1, r)
+            xb = np.abs(rng.standard_normal(o.S[p + 1] + 1))
+            o.set_state(p + 1, r, b, xb, t0)
+            st[p]["r"][f] = r
+            st[p]["b"][f] = b
+            st[p]["xbar"][f] = xb[1:]
+            st[p]["xbar"][g] = xb[0]
+            x = o.sequence_form(p + 1, b)
+            st[p]["x"][f] = x[1:]
+            st[p]["x"][g] = 1.0
+        o.iterate(1, variant, alpha=alpha, beta=beta, gamma=gamma, alternating=alt)
+        oracles.append(o)
+    Sim(lay, len(trees)).iteration(st, variant, alpha, beta, gamma, alt, np.full(len(trees), float(t0)))
+    for g, o in enumerate(oracles):
+        for p in (0, 1):
+            f = lay.caller_to_forest(p, g)
+            os_ = o.get_state(p + 1)
+            assert np.allclose(st[p]["r"][f], os_["r"], rtol=1e-12, atol=1e-12)
+            assert np.allclose(st[p]["b"][f], os_["b"], rtol=1e-12, atol=1e-12)
+            assert np.allclose(st[p]["xbar"][f], os_["xbar"][1:], rtol=1e-12, atol=1e-12)
+            assert abs(st[p]["xbar"][g] - os_["xbar"][0]) < 1e-12
