@@ -1,0 +1,168 @@
+/*
+ * cfr.h -- C ABI of the B300 sequence-form CFR library (libcfr.so).
+ *
+ * The library runs the hot path of "Parallelizing Counterfactual Regret
+ * Minimization" (Kim & Sandholm): sequence-form CFR (Sec. 2.1, Alg. 1) written
+ * as passes over a flattened game tree (Alg. 2), with the CFR+, DCFR and PCFR+
+ * variants (Alg. 3-5) and alternating updates (Sec. 3.5.1), for two-player
+ * zero-sum extensive-form games with perfect recall.  Every step runs in CUDA
+ * kernels on the current device; there is no CPU fallback.  Best response and
+ * exploitability run in FP64 on the GPU.
+ *
+ * Conventions for every call:
+ *   - All functions return an int status: CFR_OK (0) or a negative CFR_ERR_*.
+ *     No call aborts the process and no C++ exception crosses this boundary.
+ *   - The library copies every input it is given; output buffers belong to the
+ *     caller.  Buffers named host_* are host memory; nothing in this ABI takes a
+ *     device pointer.
+ *   - All device work of a context is issued on the CUDA stream passed at load
+ *     time (a cudaStream_t given as void*; NULL = a non-blocking stream the
+ *     context creates and owns).  Calls that return data synchronise that
+ *     stream before returning.
+ *   - Sequence-indexed vectors are in the caller's (infoset id, action) order:
+ *     player p's sequence k is action a of caller infoset j where
+ *     k = sum_{j' < j} |A_j'| + a.  Average-sum vectors (xbar) carry the empty
+ *     sequence first: xbar[0] = empty, xbar[1 + k] = sequence k.
+ *   - Not thread-safe per context: one host thread at a time per context.
+ */
+#ifndef CFR_B300_H
+#define CFR_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CFR_OK 0
+#define CFR_ERR_INVALID (-1)   /* malformed tree: see cfr_last_error() */
+#define CFR_ERR_OOM (-2)       /* device or host allocation failed */
+#define CFR_ERR_CUDA (-3)      /* a CUDA call failed (message in cfr_last_error()) */
+#define CFR_ERR_TIMEOUT (-4)   /* a bounded device wait gave up; the context is unusable */
+#define CFR_ERR_STATE (-5)     /* call not valid in the context's current state */
+#define CFR_ERR_ARG (-6)       /* bad argument (NULL pointer, length, index, variant) */
+
+/* regret-minimiser variants (Sec. 2.1, Alg. 1, Alg. 3, Alg. 4, Alg. 5) */
+typedef enum {
+    CFR_VANILLA = 0,    /* regret matching */
+    CFR_PLUS = 1,       /* regret matching+ : r := r^+ after ObserveUtility (Alg. 3) */
+    CFR_DCFR = 2,       /* discounted: r *= t^a/(t^a+1) where r>0, t^b/(t^b+1) where r<0 (Alg. 4) */
+    CFR_PCFR_PLUS = 3   /* predictive RM+ with prediction m^t = u^(t-1) (Alg. 5) */
+} cfr_variant;
+
+/* update schedule (Sec. 3.5.1) */
+#define CFR_UPDATES_DEFAULT 0       /* vanilla: simultaneous; the other variants: alternating */
+#define CFR_UPDATES_SIMULTANEOUS 1
+#define CFR_UPDATES_ALTERNATING 2
+
+/* A game tree, flat.  Node 0 is the root and every parent precedes its
+ * children (parent[i] < i).  Node kinds: 0 chance, 1 player-1 decision,
+ * 2 player-2 decision, 3 terminal.  Decision nodes carry an infoset id, dense
+ * 0..J_p-1 per player; all nodes of an infoset must have the same number of
+ * children and the same parent sequence (perfect recall).  action[i] is the
+ * index (0..children-1) of the edge from parent[i] to i.  chance_prob[i] is the
+ * probability of that edge when the parent is a chance node (ignored
+ * otherwise); payoff_p1[i] is player 1's utility at terminal i (player 2 gets
+ * the negative).  The arrays are host memory, read during the call only. */
+typedef struct {
+    int64_t n_nodes;
+    const int32_t *parent;
+    const int8_t *kind;
+    const int32_t *infoset;
+    const int32_t *action;
+    const double *chance_prob;
+    const double *payoff_p1;
+} cfr_tree_desc;
+
+typedef struct cfr_ctx cfr_ctx;   /* opaque; owns all its device memory */
+
+/* Compile a tree (Sec. 2.1 sequence form, Sec. 3.1-3.2 logic matrices and
+ * level graphs as index arrays) and upload it.  Validates the tree
+ * (CFR_ERR_INVALID with a message on imperfect recall, action-count
+ * mismatches, chance probabilities not summing to 1, non-finite payoffs,
+ * bad ordering).  The initial state is r = 0, uniform strategies, t = 0.
+ * On success *out owns the context; free it with cfr_free(). */
+int cfr_load_tree(const cfr_tree_desc *tree, void *cuda_stream, cfr_ctx **out);
+
+/* Same for n_games independent games sharing one context ("batch"): every
+ * kernel launch advances all active games together.  Game g keeps its own
+ * iteration counter.  games: host array of n_games descriptors. */
+int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream, cfr_ctx **out);
+
+/* Run n iterations of the chosen variant on every game (Alg. 2 NextStrategy /
+ * ObserveUtility per player; Alg. 3/4/5 post-ops).  alpha, beta: DCFR
+ * exponents (ignored by the other variants).  gamma: average-strategy weight
+ * exponent, xbar += t^gamma x^t for every variant (0 = uniform average).
+ * Iterations continue from each game's stored counter: 10 calls of n = 100
+ * equal one call of n = 1000.  Asynchronous on the context's stream. */
+int cfr_iterate(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma);
+
+/* As cfr_iterate, advancing only the games whose host_active[g] is nonzero
+ * (host_active: n_games bytes; NULL = all games). */
+int cfr_iterate_batch(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma,
+                      const uint8_t *host_active);
+
+/* Choose the update schedule (CFR_UPDATES_*). */
+int cfr_set_update_mode(cfr_ctx *ctx, int mode);
+
+/* Number of iterations captured per CUDA graph replay (1..4096, default 64). */
+int cfr_set_graph_iterations(cfr_ctx *ctx, int k);
+
+/* Sizes of game g: out[0..9] = S1, S2 (non-empty sequences), J1, J2
+ * (infosets), nnz of the payoff matrix, game-tree nodes, completed
+ * iterations, number of games in the context, device bytes the context holds,
+ * bytes copied host-to-device when it was loaded. */
+int cfr_sizes(cfr_ctx *ctx, int64_t game, int64_t *host_out10);
+
+/* Average behavioural strategy of game g, player p (1 or 2), FP64:
+ * xbar[(j,a)] / xbar[p_j], uniform where xbar[p_j] = 0.  len must be S_p. */
+int cfr_get_average_strategy(cfr_ctx *ctx, int64_t game, int player, double *host_out, int64_t len);
+
+/* Exploitability of the average profile of game 0, computed in FP64 on the
+ * GPU: BR1 = max_x x^T M ybar, BR2 = max_y -xbar^T M y over the normalised
+ * averages (current strategies when no iteration has run);
+ * expl = (BR1 + BR2) / 2.  Any output pointer may be NULL. */
+int cfr_exploitability(cfr_ctx *ctx, double *expl, double *br1, double *br2);
+
+/* Same for every game of the context: host arrays of n_games entries each
+ * (any may be NULL). */
+int cfr_exploitability_batch(cfr_ctx *ctx, double *host_expl, double *host_br1, double *host_br2);
+
+/* Checkpoint / resume of game g, player p: cumulative regrets r (S_p), the
+ * behavioural strategy to be played next b (S_p), the average sums xbar
+ * (S_p + 1, empty sequence first) in FP64, and the completed-iteration count t
+ * (shared by both players of a game).  cfr_set_state rebuilds the sequence-form
+ * strategy from b on the GPU. */
+int cfr_get_state(cfr_ctx *ctx, int64_t game, int player, double *host_r, double *host_b, double *host_xbar,
+                  int64_t *t);
+int cfr_set_state(cfr_ctx *ctx, int64_t game, int player, const double *host_r, const double *host_b,
+                  const double *host_xbar, int64_t t);
+
+/* Tracing: run n iterations without CUDA graphs, with a CUDA event recorded
+ * between consecutive kernel launches on the context's stream, and return the
+ * summed device time (ms) of each launch slot of an iteration in host_ms[4]:
+ * [player-1 up, player-1 down, player-2 up, player-2 down] (simultaneous
+ * schedule: [p1 up, p2 up, p1 down, p2 down]).  The iterations are real:
+ * state and counters advance as in cfr_iterate. */
+int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma,
+                           float *host_ms);
+
+/* Block until all work issued on the context's stream has finished
+ * (CFR_ERR_TIMEOUT if a bounded device wait gave up). */
+int cfr_sync(cfr_ctx *ctx);
+
+/* Release every resource of the context (NULL is allowed). */
+void cfr_free(cfr_ctx *ctx);
+
+/* Static description of a status code. */
+const char *cfr_strerror(int status);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *cfr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFR_B300_H */

@@ -1,0 +1,972 @@
+// C ABI of the B300 CFR library: context, device buffers, kernels, CUDA graphs.
+//
+// Declarations and contracts: include/cfr.h.  Layout: layout.h.  Device
+// building blocks: kernels.cuh (global-memory path, float-float arithmetic)
+// and staged.cuh (shared-memory staged work units).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/cfr.h"
+#include "kernels.cuh"
+#include "layout.h"
+#include "staged.cuh"
+
+using namespace cfrb;
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+namespace cfrb {
+
+// Best-response pass (MODE_BR, FP64) over every work unit from global memory;
+// the trunk of each game runs on the CTA that completes the game's last unit.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const void *xo, IterArgs ia) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    void *stage = smem;
+    __shared__ int s_item, s_last;
+    __shared__ ItemParams s_ip;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.work, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= P.n_items) break;
+        const int4 d = P.items[it];
+        const int g = d.x;
+        if (threadIdx.x == 0) item_params(gm, ia, g, &s_ip);
+        __syncthreads();
+        const ItemParams ip = s_ip;
+        if (!ip.active) continue;
+        run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const int prev = atomicAdd(&P.game_done[g], 1);
+            s_last = (prev == P.game_nitems[g] - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const int4 tr = P.trunks[g];
+            run_up<MODE>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
+            if (threadIdx.x == 0) {
+                if (MODE == MODE_BR) gm.br[g] = __ldcg(&P.ev64[g]);
+                P.game_done[g] = 0;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
+            *P.work = 0;
+            *P.exits = 0;
+        }
+    }
+}
+
+// trunk top-down into the staging vector xn (Alg. 2 NextStrategy above the cut)
+__device__ void trunk_topdown(const DevPlayer &P, int g) {
+    const int4 tr = P.trunks[g];
+    const int32_t *rng = P.ranges + tr.z;
+    if (threadIdx.x == 0) P.xn[g] = 1.f;
+    __syncthreads();
+    for (int k = 1; k < tr.y; k++) {
+        for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
+            const float xp = P.xn[P.inf_par[j]];
+            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) P.xn[s] = xp * P.b[s];
+        }
+        __syncthreads();
+    }
+}
+
+// Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
+// Alg. 3-5, and NextStrategy's regret matching): persistent CTAs take work
+// units from a queue, stage each unit in shared memory with bulk copies while
+// the previous one is computed, and the CTA completing a game's last unit
+// runs that game's trunk (bottom-up, then top-down into xn).
+__global__ void __launch_bounds__(kThreadsS, 1)
+    k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *bufs0 = smem, *bufs1 = smem + item_bytes;
+    float *stage = (float *)(smem + 2 * item_bytes);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ SLvl lv[2][kMaxStagedLevels];
+    __shared__ UpTab tab[2][kMaxStagedLevels];
+    __shared__ int s_next, s_last, s_err;
+    __shared__ ItemParams s_ip;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        s_next = atomicAdd(P.work, 1);
+    }
+    __syncthreads();
+    uint32_t ph[2] = {0u, 0u};
+    int cur = s_next, buf = 0;
+    if (tid == 0 && cur < P.n_items) {
+        const int4 h = P.items[cur];
+        if (h.w & kStaged) issue_up(P, h, bufs0, &bar[0], lv[0], tab[0]);
+    }
+    while (cur < P.n_items) {
+        if (tid == 0) s_next = atomicAdd(P.work, 1);
+        __syncthreads();
+        const int nxt = s_next;
+        const int4 h = P.items[cur];
+        const int g = h.x;
+        if (tid == 0) {
+            if (nxt < P.n_items) {
+                const int4 hn = P.items[nxt];
+                if (hn.w & kStaged) issue_up(P, hn, buf ? bufs0 : bufs1, &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+            }
+            item_params(gm, ia, g, &s_ip);
+            s_err = 0;
+        }
+        __syncthreads();
+        if (h.w & kStaged) {
+            if (!mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+            ph[buf] ^= 1u;
+        }
+        __syncthreads();
+        if (s_err) break;
+        const ItemParams ip = s_ip;
+        if (ip.active) {
+            if (h.w & kStaged) compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf]);
+            else run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, stage);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const int prev = atomicAdd(&P.game_done[g], 1);
+                s_last = (prev == P.game_nitems[g] - 1);
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const int4 tr = P.trunks[g];
+                run_up<MODE_CFR>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
+                trunk_topdown(P, g);
+                if (tid == 0) {
+                    P.game_done[g] = 0;
+                    if (ia.first_of_iter) gm.t_done[g] = ip.t;
+                }
+                __syncthreads();
+            }
+        }
+        cur = nxt;
+        buf ^= 1;
+    }
+    if (tid == 0) {
+        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
+            *P.work = 0;
+            *P.exits = 0;
+        }
+    }
+}
+
+// one unit top-down from global memory (units too large to stage)
+__device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nlvl, const int32_t *rng) {
+    const bool avg = ia.average != 0;
+    for (int k = 0; k < nlvl; k++) {
+        const float *xpar = (k == 0) ? P.xn : P.x;
+        for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
+            const float xp = xpar[P.inf_par[j]];
+            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) {
+                if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
+                P.x[s] = xp * P.b[s];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Down pass (Alg. 2 NextStrategy below the cut: y += L^T y, x = A^T y) and the
+// average xbar += t^gamma x; the first unit of each game also moves the
+// trunk's staged x into place.
+__global__ void __launch_bounds__(kThreadsS, 1) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *bufs0 = smem, *bufs1 = smem + item_bytes;
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ SLvl lv[2][kMaxStagedLevels];
+    __shared__ DownTab tab[2][kMaxStagedLevels];
+    __shared__ int s_next, s_err;
+    __shared__ ItemParams s_ip;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        s_next = atomicAdd(P.work, 1);
+    }
+    __syncthreads();
+    uint32_t ph[2] = {0u, 0u};
+    int cur = s_next, buf = 0;
+    if (tid == 0 && cur < P.n_items) {
+        const int4 h = P.items[cur];
+        if (h.w & kStaged) issue_down(P, h, bufs0, &bar[0], lv[0], tab[0]);
+    }
+    const bool avg = ia.average != 0;
+    while (cur < P.n_items) {
+        if (tid == 0) s_next = atomicAdd(P.work, 1);
+        __syncthreads();
+        const int nxt = s_next;
+        const int4 h = P.items[cur];
+        const int g = h.x;
+        if (tid == 0) {
+            if (nxt < P.n_items) {
+                const int4 hn = P.items[nxt];
+                if (hn.w & kStaged) issue_down(P, hn, buf ? bufs0 : bufs1, &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+            }
+            item_params(gm, ia, g, &s_ip);
+            s_err = 0;
+        }
+        __syncthreads();
+        const ItemParams ip = s_ip;
+        if (ip.active && P.item_first[cur]) {
+            const int4 tr = P.trunks[g];
+            const int32_t *rng = P.ranges + tr.z;
+            for (int k = 0; k < tr.y; k++) {
+                const int slo = rng[kLvl * k + 2], shi = rng[kLvl * k + 3];
+                for (int s = slo + tid; s < shi; s += blockDim.x) {
+                    if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
+                    P.x[s] = P.xn[s];
+                }
+            }
+        }
+        if (h.w & kStaged) {
+            if (!mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+            ph[buf] ^= 1u;
+        }
+        __syncthreads();
+        if (s_err) break;
+        if (ip.active) {
+            if (h.w & kStaged) compute_down(P, ia, ip, h.y, lv[buf], tab[buf]);
+            else run_down(P, ia, ip, h.y, P.ranges + h.z);
+        }
+        __syncthreads();
+        cur = nxt;
+        buf ^= 1;
+    }
+    if (tid == 0) {
+        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
+            *P.work = 0;
+            *P.exits = 0;
+        }
+    }
+}
+
+// trunk top-down, one CTA per game (when x is rebuilt from b outside an iteration)
+__global__ void k_trunk_topdown(DevPlayer P) { trunk_topdown(P, blockIdx.x); }
+
+// uniform behavioural strategy (regret matching of r = 0)
+__global__ void k_uniform(DevPlayer P, int64_t J) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
+        const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+        const float v = 1.0f / (float)(s1 - s0);
+        for (int s = s0; s < s1; s++) P.b[s] = v;
+    }
+}
+
+// normalised average (FP64) for the best-response pass; current x where no
+// iteration has been averaged yet
+__global__ void k_normalize(DevPlayer P, int64_t S) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        const int g = P.seq_game[s];
+        const float2 dn = P.xbar[g];
+        const double den = (double)dn.x + (double)dn.y;
+        const float2 v = P.xbar[s];
+        P.xnorm[s] = den > 0.0 ? ((double)v.x + (double)v.y) / den : (double)P.x[s];
+    }
+}
+
+// state of one game in caller order (FP64): r, b, xbar (empty first)
+__global__ void k_get_state(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
+                            double *out_r, double *out_b, double *out_xbar) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        const float2 v = P.xbar[g];
+        out_xbar[0] = (double)v.x + (double)v.y;
+    }
+    if (k >= Jg) return;
+    const int j = ext_inf[k];
+    const int base = ext_seq0[k];
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    for (int s = s0; s < s1; s++) {
+        const int o = base + (s - s0);
+        const float2 r = P.r[s];
+        out_r[o] = (double)r.x + (double)r.y;
+        out_b[o] = (double)P.b[s];
+        const float2 xb = P.xbar[s];
+        out_xbar[1 + o] = (double)xb.x + (double)xb.y;
+    }
+}
+
+__global__ void k_set_state(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
+                            const double *in_r, const double *in_b, const double *in_xbar) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) P.xbar[g] = ff_from_double(in_xbar[0]);
+    if (k >= Jg) return;
+    const int j = ext_inf[k];
+    const int base = ext_seq0[k];
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    for (int s = s0; s < s1; s++) {
+        const int o = base + (s - s0);
+        P.r[s] = ff_from_double(in_r[o]);
+        P.b[s] = (float)in_b[o];
+        P.xbar[s] = ff_from_double(in_xbar[1 + o]);
+    }
+}
+
+// average behavioural strategy of one game: xbar[(j,a)] / xbar[p_j] (FP64)
+__global__ void k_average(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int Jg, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Jg) return;
+    const int j = ext_inf[k];
+    const int base = ext_seq0[k];
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    const float2 dp = P.xbar[P.inf_par[j]];
+    const double den = (double)dp.x + (double)dp.y;
+    for (int s = s0; s < s1; s++) {
+        const float2 v = P.xbar[s];
+        out[base + (s - s0)] = den > 0.0 ? ((double)v.x + (double)v.y) / den : 1.0 / (double)(s1 - s0);
+    }
+}
+
+__global__ void k_set_t(int32_t *t_done, int g, int32_t t) { t_done[g] = t; }
+
+}  // namespace cfrb
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string &m) {
+    g_last_error = m;
+    return code;
+}
+
+struct PlayerBuf {
+    DevPlayer d{};
+    int32_t *ext_inf = nullptr, *ext_seq0 = nullptr;
+    int64_t S = 0, J = 0, n_items = 0;
+    int n_levels = 0;
+    int grid_up = 1, grid_up_br = 1, grid_down = 1;
+    size_t smem_br = 0;
+    std::vector<int32_t> game_J, game_S;
+    std::vector<int64_t> game_jbase;
+};
+
+struct GraphKey {
+    int variant, mode, k;
+    double a, b, g;
+    bool operator<(const GraphKey &o) const {
+        return std::tie(variant, mode, k, a, b, g) < std::tie(o.variant, o.mode, o.k, o.a, o.b, o.g);
+    }
+};
+
+}  // namespace
+
+struct cfr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t G = 0, Z = 0;
+    PlayerBuf pl[2];
+    int32_t *t_done = nullptr;
+    uint8_t *active = nullptr;
+    double *br[2] = {nullptr, nullptr};
+    double *scratch = nullptr;   // FP64 transfer area: 3 * (max S + 1)
+    int64_t scratch_n = 0;
+    int update_mode = CFR_UPDATES_DEFAULT;
+    int graph_k = 64;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::vector<void *> allocs;
+    std::vector<int64_t> game_nodes, game_nnz;
+    std::vector<uint8_t> active_host;
+    int64_t dev_bytes = 0, h2d_bytes = 0;
+    int item_bytes = 96 * 1024;     // one staged unit buffer (two per CTA)
+    size_t smem_staged = 0;
+    int32_t *err = nullptr;         // device error word (bounded waits)
+    bool poisoned = false;
+};
+
+namespace {
+
+#define CU(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return set_err(e_ == cudaErrorMemoryAllocation ? CFR_ERR_OOM : CFR_ERR_CUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+#define TRY(x)               \
+    do {                     \
+        int rc_ = (x);       \
+        if (rc_) return rc_; \
+    } while (0)
+
+template <class T>
+int dalloc(cfr_ctx *c, T **p, size_t n) {
+    void *q = nullptr;
+    // 32 bytes of tail padding: staged copies round their ranges out to 16 bytes
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T) + 32;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(CFR_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    c->dev_bytes += (int64_t)bytes;
+    *p = (T *)q;
+    return CFR_OK;
+}
+
+template <class T>
+int upload(cfr_ctx *c, T **p, const std::vector<T> &v) {
+    TRY(dalloc(c, p, v.size()));
+    if (!v.empty()) CU(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    c->h2d_bytes += (int64_t)(v.size() * sizeof(T));
+    return CFR_OK;
+}
+
+int launch_rebuild_x(cfr_ctx *c, int p) {
+    PlayerBuf &B = c->pl[p];
+    DevGames gm{c->t_done, c->active, nullptr};
+    IterArgs ia{};
+    ia.average = 0;
+    k_trunk_topdown<<<(unsigned)c->G, kThreads, 0, c->stream>>>(B.d);
+    k_down_staged<<<B.grid_down, kThreadsS, c->smem_staged, c->stream>>>(B.d, gm, ia, c->item_bytes);
+    CU(cudaGetLastError());
+    return CFR_OK;
+}
+
+// one iteration: NextStrategy/ObserveUtility for both players (Alg. 2), in the
+// alternating or simultaneous schedule (Sec. 3.5.1)
+int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double gamma, bool alternating,
+                     cudaEvent_t *ev = nullptr) {
+    DevGames gm{c->t_done, c->active, nullptr};
+    IterArgs up1{variant, 1, +1.f, alpha, beta, gamma, 1};
+    IterArgs up2{variant, 0, -1.f, alpha, beta, gamma, 1};
+    IterArgs dn{variant, 0, 0.f, alpha, beta, gamma, 1};
+    PlayerBuf &A = c->pl[0], &B = c->pl[1];
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], c->stream);
+    };
+    const size_t sm = c->smem_staged;
+    const int ib = c->item_bytes;
+    mark(0);
+    if (alternating) {
+        k_up_staged<<<A.grid_up, kThreadsS, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
+        mark(1);
+        k_down_staged<<<A.grid_down, kThreadsS, sm, c->stream>>>(A.d, gm, dn, ib);
+        mark(2);
+        k_up_staged<<<B.grid_up, kThreadsS, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
+        mark(3);
+        k_down_staged<<<B.grid_down, kThreadsS, sm, c->stream>>>(B.d, gm, dn, ib);
+    } else {
+        k_up_staged<<<A.grid_up, kThreadsS, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
+        mark(1);
+        k_up_staged<<<B.grid_up, kThreadsS, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
+        mark(2);
+        k_down_staged<<<A.grid_down, kThreadsS, sm, c->stream>>>(A.d, gm, dn, ib);
+        mark(3);
+        k_down_staged<<<B.grid_down, kThreadsS, sm, c->stream>>>(B.d, gm, dn, ib);
+    }
+    mark(4);
+    CU(cudaGetLastError());
+    return CFR_OK;
+}
+
+int occupancy_grid(const void *fn, int threads, size_t smem, int64_t n_items, int *grid) {
+    int dev = 0, sms = 0, per = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem));
+    if (per < 1) return set_err(CFR_ERR_CUDA, "kernel does not fit on an SM");
+    const int64_t full = (int64_t)sms * per;
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, n_items));
+    return CFR_OK;
+}
+
+int build_player(cfr_ctx *c, const Layout &L, int p) {
+    const PlayerLayout &H = L.pl[p];
+    PlayerBuf &B = c->pl[p];
+    DevPlayer &d = B.d;
+    B.S = H.S;
+    B.J = H.J;
+    B.n_items = (int64_t)H.items.size();
+    B.n_levels = H.n_levels;
+    B.game_J = H.game_J;
+    B.game_S = H.game_S;
+    B.game_jbase = H.game_jbase;
+    int32_t *p32;
+    TRY(upload(c, &p32, H.inf_seq));
+    d.inf_seq = p32;
+    TRY(upload(c, &p32, H.seq_child));
+    d.seq_child = p32;
+    TRY(upload(c, &p32, H.inf_par));
+    d.inf_par = p32;
+    TRY(upload(c, &p32, H.seq_game));
+    d.seq_game = p32;
+    TRY(upload(c, &p32, H.m_ptr));
+    d.m_ptr = p32;
+    TRY(upload(c, &p32, H.m_col));
+    d.m_col = p32;
+    float *pf;
+    TRY(upload(c, &pf, H.m_val));
+    d.m_val = pf;
+    double *pd;
+    TRY(upload(c, &pd, H.m_val64));
+    d.m_val64 = pd;
+    std::vector<int4> items(H.items.size()), trunks(H.trunks.size());
+    std::vector<int32_t> first(H.items.size(), 0);
+    std::vector<char> seen(L.G, 0);
+    for (size_t k = 0; k < H.items.size(); k++) {
+        const Item &it = H.items[k];
+        items[k] = make_int4(it.game, it.nlvl, it.rng, it.flags);
+        if (!seen[it.game]) {
+            first[k] = 1;
+            seen[it.game] = 1;
+        }
+    }
+    for (size_t g = 0; g < H.trunks.size(); g++) {
+        const Item &it = H.trunks[g];
+        trunks[g] = make_int4(it.game, it.nlvl, it.rng, 0);
+    }
+    int4 *p4;
+    TRY(upload(c, &p4, items));
+    d.items = p4;
+    TRY(upload(c, &p4, trunks));
+    d.trunks = p4;
+    TRY(upload(c, &p32, H.ranges));
+    d.ranges = p32;
+    TRY(upload(c, &p32, H.game_nitems));
+    d.game_nitems = p32;
+    TRY(upload(c, &p32, first));
+    d.item_first = p32;
+    TRY(upload(c, &B.ext_inf, H.ext_inf));
+    TRY(upload(c, &B.ext_seq0, H.ext_seq0));
+    d.n_items = (int32_t)H.items.size();
+    d.G = (int32_t)L.G;
+    TRY(dalloc(c, &d.r, H.S));
+    TRY(dalloc(c, &d.b, H.S));
+    TRY(dalloc(c, &d.x, H.S));
+    TRY(dalloc(c, &d.xn, H.S));
+    TRY(dalloc(c, &d.xbar, H.S));
+    TRY(dalloc(c, &d.u, H.S));
+    TRY(dalloc(c, &d.ev, H.J));
+    TRY(dalloc(c, &d.u64, H.S));
+    TRY(dalloc(c, &d.ev64, H.J));
+    TRY(dalloc(c, &d.xnorm, H.S));
+    int32_t *ctr;
+    TRY(dalloc(c, &ctr, L.G + 2));
+    CU(cudaMemsetAsync(ctr, 0, (L.G + 2) * sizeof(int32_t), c->stream));
+    d.game_done = ctr;
+    d.work = ctr + L.G;
+    d.exits = ctr + L.G + 1;
+    d.err = c->err;
+    CU(cudaMemsetAsync(d.r, 0, H.S * sizeof(float2), c->stream));
+    CU(cudaMemsetAsync(d.xbar, 0, H.S * sizeof(float2), c->stream));
+    CU(cudaMemsetAsync(d.ev, 0, H.J * sizeof(float), c->stream));
+    CU(cudaMemsetAsync(d.ev64, 0, H.J * sizeof(double), c->stream));
+    CU(cudaMemsetAsync(d.x, 0, H.S * sizeof(float), c->stream));
+    CU(cudaMemsetAsync(d.xn, 0, H.S * sizeof(float), c->stream));
+    B.smem_br = (size_t)(kThreads / 32) * 32 * kStage * sizeof(double);
+    CU(cudaFuncSetAttribute(k_up_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
+    CU(cudaFuncSetAttribute(k_down_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
+    TRY(occupancy_grid((const void *)k_up_staged, kThreadsS, c->smem_staged, B.n_items, &B.grid_up));
+    TRY(occupancy_grid((const void *)k_up<MODE_BR>, kThreads, B.smem_br, B.n_items, &B.grid_up_br));
+    TRY(occupancy_grid((const void *)k_down_staged, kThreadsS, c->smem_staged, B.n_items, &B.grid_down));
+    k_uniform<<<(unsigned)std::min<int64_t>((H.J + kThreads - 1) / kThreads, 65535), kThreads, 0, c->stream>>>(d,
+                                                                                                             H.J);
+    CU(cudaGetLastError());
+    return CFR_OK;
+}
+
+int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
+    if (!out) return set_err(CFR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!games || n < 1) return set_err(CFR_ERR_ARG, "no games");
+    std::vector<TreeView> tv(n);
+    for (int64_t g = 0; g < n; g++) {
+        const cfr_tree_desc &t = games[g];
+        if (t.n_nodes < 1 || !t.parent || !t.kind || !t.infoset || !t.action || !t.chance_prob || !t.payoff_p1)
+            return set_err(CFR_ERR_ARG, "game " + std::to_string(g) + ": NULL array or empty tree");
+        tv[g] = {t.n_nodes, t.parent, t.kind, t.infoset, t.action, t.chance_prob, t.payoff_p1};
+    }
+    Layout L;
+    std::string err;
+    int rc;
+    CompileOptions opt;
+    {
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        opt.slots = std::max(1, sms);
+        opt.item_bytes = 96 * 1024;
+    }
+    try {
+        rc = compile_forest(tv.data(), n, opt, &L, &err);
+    } catch (const std::bad_alloc &) {
+        return set_err(CFR_ERR_OOM, "host allocation failed while compiling");
+    } catch (const std::exception &e) {
+        return set_err(CFR_ERR_INVALID, e.what());
+    }
+    if (rc != ST_OK) return set_err(rc == ST_OOM ? CFR_ERR_OOM : CFR_ERR_INVALID, err);
+    cfr_ctx *c = new (std::nothrow) cfr_ctx();
+    if (!c) return set_err(CFR_ERR_OOM, "context allocation");
+    auto bail = [&](int code) {
+        cfr_free(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(set_err(CFR_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)));
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(set_err(CFR_ERR_CUDA, cudaGetErrorString(e)));
+        c->own_stream = true;
+    }
+    c->G = L.G;
+    c->Z = L.Z;
+    c->item_bytes = (int)opt.item_bytes;
+    c->smem_staged = 2 * (size_t)c->item_bytes + (size_t)(kThreadsS / 32) * 32 * kStage * sizeof(float);
+    if ((rc = dalloc(c, &c->err, 1))) return bail(rc);
+    if (cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream) != cudaSuccess)
+        return bail(set_err(CFR_ERR_CUDA, "memset"));
+    c->game_nodes = L.game_nodes;
+    c->game_nnz = L.game_nnz;
+    for (int p = 0; p < 2; p++)
+        if ((rc = build_player(c, L, p))) return bail(rc);
+    if ((rc = dalloc(c, &c->t_done, L.G))) return bail(rc);
+    if ((rc = dalloc(c, &c->active, L.G))) return bail(rc);
+    if ((rc = dalloc(c, &c->br[0], L.G))) return bail(rc);
+    if ((rc = dalloc(c, &c->br[1], L.G))) return bail(rc);
+    int64_t smax = 0;
+    for (int p = 0; p < 2; p++)
+        for (int64_t g = 0; g < L.G; g++) smax = std::max<int64_t>(smax, L.pl[p].game_S[g]);
+    c->scratch_n = smax + 1;
+    if ((rc = dalloc(c, &c->scratch, 3 * c->scratch_n))) return bail(rc);
+    c->active_host.assign(L.G, 1);
+    if (cudaMemsetAsync(c->t_done, 0, L.G * sizeof(int32_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->active, 1, L.G, c->stream) != cudaSuccess)
+        return bail(set_err(CFR_ERR_CUDA, "memset"));
+    for (int p = 0; p < 2; p++)
+        if ((rc = launch_rebuild_x(c, p))) return bail(rc);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(set_err(CFR_ERR_CUDA, cudaGetErrorString(e)));
+    *out = c;
+    return CFR_OK;
+}
+
+bool default_alternating(int variant) { return variant != CFR_VANILLA; }
+
+// read the device error word after the stream has drained; a bounded device
+// wait that gave up leaves the context unusable
+int check_err(cfr_ctx *c) {
+    if (c->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    int32_t e = 0;
+    CU(cudaMemcpyAsync(&e, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (e) {
+        c->poisoned = true;
+        return set_err(CFR_ERR_TIMEOUT, "a bounded device wait gave up (shared-memory staging did not complete)");
+    }
+    return CFR_OK;
+}
+
+int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, double gamma) {
+    if (!c) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (c->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    if (n < 0) return set_err(CFR_ERR_ARG, "negative iteration count");
+    if (variant < 0 || variant > 3) return set_err(CFR_ERR_ARG, "unknown variant");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(gamma))
+        return set_err(CFR_ERR_ARG, "alpha, beta, gamma must be finite");
+    const bool alt = c->update_mode == CFR_UPDATES_DEFAULT ? default_alternating(variant)
+                                                           : c->update_mode == CFR_UPDATES_ALTERNATING;
+    const int K = c->graph_k;
+    int64_t done = 0;
+    if (n >= K) {
+        GraphKey key{variant, alt ? 2 : 1, K, alpha, beta, gamma};
+        auto f = c->graphs.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (f == c->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = CFR_OK;
+            for (int k = 0; k < K && rc == CFR_OK; k++) rc = launch_iteration(c, variant, alpha, beta, gamma, alt);
+            cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ee != cudaSuccess) return set_err(CFR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+            ee = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ee != cudaSuccess)
+                return set_err(CFR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
+            c->graphs[key] = exec;
+        } else {
+            exec = f->second;
+        }
+        for (; done + K <= n; done += K) CU(cudaGraphLaunch(exec, c->stream));
+    }
+    for (; done < n; done++) TRY(launch_iteration(c, variant, alpha, beta, gamma, alt));
+    return CFR_OK;
+}
+
+int check_game(cfr_ctx *c, int64_t g, int player) {
+    if (!c) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (g < 0 || g >= c->G) return set_err(CFR_ERR_ARG, "game index out of range");
+    if (player != 1 && player != 2) return set_err(CFR_ERR_ARG, "player must be 1 or 2");
+    return CFR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int cfr_load_tree(const cfr_tree_desc *tree, void *cuda_stream, cfr_ctx **out) {
+    return load(tree, 1, cuda_stream, out);
+}
+
+int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream, cfr_ctx **out) {
+    return load(games, n_games, cuda_stream, out);
+}
+
+int cfr_iterate(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma) {
+    if (ctx && std::find(ctx->active_host.begin(), ctx->active_host.end(), 0) != ctx->active_host.end()) {
+        std::fill(ctx->active_host.begin(), ctx->active_host.end(), 1);
+        CU(cudaMemsetAsync(ctx->active, 1, ctx->G, ctx->stream));
+    }
+    return iterate(ctx, n, (int)v, alpha, beta, gamma);
+}
+
+int cfr_iterate_batch(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma,
+                      const uint8_t *host_active) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    std::vector<uint8_t> act(ctx->G, 1);
+    if (host_active)
+        for (int64_t g = 0; g < ctx->G; g++) act[g] = host_active[g] ? 1 : 0;
+    if (act != ctx->active_host) {
+        ctx->active_host = act;
+        // pageable source: the copy is staged before the call returns
+        CU(cudaMemcpyAsync(ctx->active, ctx->active_host.data(), ctx->G, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return iterate(ctx, n, (int)v, alpha, beta, gamma);
+}
+
+int cfr_set_update_mode(cfr_ctx *ctx, int mode) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (mode < 0 || mode > 2) return set_err(CFR_ERR_ARG, "unknown update mode");
+    ctx->update_mode = mode;
+    return CFR_OK;
+}
+
+int cfr_set_graph_iterations(cfr_ctx *ctx, int k) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (k < 1 || k > 4096) return set_err(CFR_ERR_ARG, "graph iterations must be in [1, 4096]");
+    ctx->graph_k = k;
+    return CFR_OK;
+}
+
+int cfr_sizes(cfr_ctx *ctx, int64_t game, int64_t *out) {
+    TRY(check_game(ctx, game, 1));
+    if (!out) return set_err(CFR_ERR_ARG, "out is NULL");
+    int32_t t = 0;
+    CU(cudaMemcpyAsync(&t, ctx->t_done + game, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    out[0] = ctx->pl[0].game_S[game];
+    out[1] = ctx->pl[1].game_S[game];
+    out[2] = ctx->pl[0].game_J[game];
+    out[3] = ctx->pl[1].game_J[game];
+    out[4] = ctx->game_nnz[game];
+    out[5] = ctx->game_nodes[game];
+    out[6] = t;
+    out[7] = ctx->G;
+    out[8] = ctx->dev_bytes;
+    out[9] = ctx->h2d_bytes;
+    return CFR_OK;
+}
+
+int cfr_get_average_strategy(cfr_ctx *ctx, int64_t game, int player, double *host_out, int64_t len) {
+    TRY(check_game(ctx, game, player));
+    PlayerBuf &B = ctx->pl[player - 1];
+    const int Jg = B.game_J[game];
+    if (!host_out || len != B.game_S[game]) return set_err(CFR_ERR_ARG, "output length must equal S_p");
+    if (Jg > 0) {
+        k_average<<<(Jg + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+            B.d, B.ext_inf + B.game_jbase[game], B.ext_seq0 + B.game_jbase[game], Jg, ctx->scratch);
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(host_out, ctx->scratch, len * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
+}
+
+int cfr_exploitability_batch(cfr_ctx *ctx, double *host_expl, double *host_br1, double *host_br2) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (ctx->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    DevGames gm{ctx->t_done, ctx->active, nullptr};
+    IterArgs ia{};
+    // the best response is computed for every game, whatever the active mask
+    const bool masked = std::find(ctx->active_host.begin(), ctx->active_host.end(), 0) != ctx->active_host.end();
+    if (masked) CU(cudaMemsetAsync(ctx->active, 1, ctx->G, ctx->stream));
+    for (int p = 0; p < 2; p++) {
+        PlayerBuf &B = ctx->pl[p];
+        k_normalize<<<(unsigned)std::min<int64_t>((B.S + kThreads - 1) / kThreads, 65535), kThreads, 0,
+                      ctx->stream>>>(B.d, B.S);
+    }
+    for (int p = 0; p < 2; p++) {
+        PlayerBuf &B = ctx->pl[p];
+        gm.br = ctx->br[p];
+        ia.sign = p == 0 ? 1.f : -1.f;
+        k_up<MODE_BR><<<B.grid_up_br, kThreads, B.smem_br, ctx->stream>>>(B.d, gm, ctx->pl[1 - p].d.xnorm, ia);
+    }
+    CU(cudaGetLastError());
+    if (masked)
+        CU(cudaMemcpyAsync(ctx->active, ctx->active_host.data(), ctx->G, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<double> b1(ctx->G), b2(ctx->G);
+    CU(cudaMemcpyAsync(b1.data(), ctx->br[0], ctx->G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(b2.data(), ctx->br[1], ctx->G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    TRY(check_err(ctx));
+    for (int64_t g = 0; g < ctx->G; g++) {
+        if (host_expl) host_expl[g] = 0.5 * (b1[g] + b2[g]);
+        if (host_br1) host_br1[g] = b1[g];
+        if (host_br2) host_br2[g] = b2[g];
+    }
+    return CFR_OK;
+}
+
+int cfr_exploitability(cfr_ctx *ctx, double *expl, double *br1, double *br2) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    std::vector<double> e(ctx->G), a(ctx->G), b(ctx->G);
+    TRY(cfr_exploitability_batch(ctx, e.data(), a.data(), b.data()));
+    if (expl) *expl = e[0];
+    if (br1) *br1 = a[0];
+    if (br2) *br2 = b[0];
+    return CFR_OK;
+}
+
+int cfr_get_state(cfr_ctx *ctx, int64_t game, int player, double *host_r, double *host_b, double *host_xbar,
+                  int64_t *t) {
+    TRY(check_game(ctx, game, player));
+    PlayerBuf &B = ctx->pl[player - 1];
+    const int Jg = B.game_J[game];
+    const int64_t Sg = B.game_S[game];
+    double *dr = ctx->scratch, *db = ctx->scratch + ctx->scratch_n, *dx = ctx->scratch + 2 * ctx->scratch_n;
+    k_get_state<<<(Jg + kThreads) / kThreads, kThreads, 0, ctx->stream>>>(
+        B.d, B.ext_inf + B.game_jbase[game], B.ext_seq0 + B.game_jbase[game], (int)game, Jg, dr, db, dx);
+    CU(cudaGetLastError());
+    if (host_r && Sg) CU(cudaMemcpyAsync(host_r, dr, Sg * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (host_b && Sg) CU(cudaMemcpyAsync(host_b, db, Sg * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (host_xbar) CU(cudaMemcpyAsync(host_xbar, dx, (Sg + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    int32_t tt = 0;
+    CU(cudaMemcpyAsync(&tt, ctx->t_done + game, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    TRY(check_err(ctx));
+    if (t) *t = tt;
+    return CFR_OK;
+}
+
+int cfr_set_state(cfr_ctx *ctx, int64_t game, int player, const double *host_r, const double *host_b,
+                  const double *host_xbar, int64_t t) {
+    TRY(check_game(ctx, game, player));
+    if (!host_r || !host_b || !host_xbar) return set_err(CFR_ERR_ARG, "state arrays must not be NULL");
+    if (t < 0 || t > INT32_MAX - 1) return set_err(CFR_ERR_ARG, "t out of range");
+    PlayerBuf &B = ctx->pl[player - 1];
+    const int Jg = B.game_J[game];
+    const int64_t Sg = B.game_S[game];
+    double *dr = ctx->scratch, *db = ctx->scratch + ctx->scratch_n, *dx = ctx->scratch + 2 * ctx->scratch_n;
+    if (Sg) {
+        CU(cudaMemcpyAsync(dr, host_r, Sg * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(db, host_b, Sg * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CU(cudaMemcpyAsync(dx, host_xbar, (Sg + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    k_set_state<<<(Jg + kThreads) / kThreads, kThreads, 0, ctx->stream>>>(
+        B.d, B.ext_inf + B.game_jbase[game], B.ext_seq0 + B.game_jbase[game], (int)game, Jg, dr, db, dx);
+    k_set_t<<<1, 1, 0, ctx->stream>>>(ctx->t_done, (int)game, (int32_t)t);
+    CU(cudaGetLastError());
+    TRY(launch_rebuild_x(ctx, player - 1));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
+}
+
+int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma,
+                           float *host_ms) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (!host_ms || n < 1) return set_err(CFR_ERR_ARG, "need n >= 1 and an output array");
+    if ((int)v < 0 || (int)v > 3) return set_err(CFR_ERR_ARG, "unknown variant");
+    const bool alt = ctx->update_mode == CFR_UPDATES_DEFAULT ? default_alternating((int)v)
+                                                             : ctx->update_mode == CFR_UPDATES_ALTERNATING;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; k++) CU(cudaEventCreate(&ev[k]));
+    double tot[4] = {0, 0, 0, 0};
+    int rc = CFR_OK;
+    for (int64_t i = 0; i < n && rc == CFR_OK; i++) {
+        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, ev);
+        if (rc) break;
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e != cudaSuccess) {
+            rc = set_err(CFR_ERR_CUDA, cudaGetErrorString(e));
+            break;
+        }
+        for (int k = 0; k < 4; k++) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            tot[k] += ms;
+        }
+    }
+    for (int k = 0; k < 5; k++) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 4; k++) host_ms[k] = (float)tot[k];
+    if (rc) return rc;
+    return check_err(ctx);
+}
+
+int cfr_sync(cfr_ctx *ctx) {
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
+}
+
+void cfr_free(cfr_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *cfr_strerror(int status) {
+    switch (status) {
+        case CFR_OK: return "ok";
+        case CFR_ERR_INVALID: return "invalid game tree";
+        case CFR_ERR_OOM: return "out of memory";
+        case CFR_ERR_CUDA: return "CUDA error";
+        case CFR_ERR_TIMEOUT: return "device wait timed out";
+        case CFR_ERR_STATE: return "invalid state for this call";
+        case CFR_ERR_ARG: return "invalid argument";
+        default: return "unknown status";
+    }
+}
+
+const char *cfr_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// Device building blocks of one sequence-form CFR iteration (sm_103a).
+//
+// One player's half-step is two launches over the forest layout (layout.h):
+//
+//   up   : per work item (a group of subtrees below the game's cut level),
+//          deepest level first:
+//            - payoff product rows u = sign * M x_other          (Sec. 2.1, two-player utilities)
+//            - V[s] = u[s] + sum of the child infosets' ev       (Alg. 2: v += L w + L v; q = B^T(w+v))
+//            - ev_j = sum_a b_j[a] V[(j,a)]                       (C (b . q))
+//            - r += V - ev_j, variant post-op, next strategy     (Alg. 2 regret update; Alg. 3-5)
+//          The last CTA to finish an item of a game runs that game's trunk
+//          (levels above the cut) the same way, then the trunk's top-down
+//          pass into a staging vector xn.
+//   down : per work item, top-down: x[(j,a)] = x[p_j] b_j[a]    (Alg. 2: y += L^T y; x = A^T y)
+//          and the average xbar += t^gamma x (for the x being replaced).
+//
+// No CTA ever waits for another CTA: completion is counted with one atomic
+// per item (threadfence-reduction pattern) and a game's trunk runs on
+// whichever CTA finishes that game's last item.  Cumulative regrets and
+// average sums are float-float pairs (Kahan-compensated FP32): B300's FP64
+// rate is far below its FP32 rate, so the hot path does no FP64 arithmetic.
+// The best-response pass (MODE_BR) runs in FP64.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "layout.h"
+
+namespace cfrb {
+
+constexpr int kThreads = 256;      // threads of a global-path CTA
+constexpr int kStage = 8;          // products staged per lane per pass of the payoff SpMV
+
+enum { VAR_CFR = 0, VAR_PLUS = 1, VAR_DCFR = 2, VAR_PCFR_PLUS = 3 };
+enum { MODE_CFR = 0, MODE_BR = 1 };
+
+struct DevPlayer {
+    // structure (read-only)
+    const int32_t *inf_seq, *seq_child, *inf_par, *seq_game;
+    const int32_t *m_ptr, *m_col;
+    const float *m_val;
+    const double *m_val64;
+    const int4 *items, *trunks;     // {game, nlvl, rng, flags}; ranges: kLvl ints per level
+    const int32_t *ranges, *game_nitems, *item_first;
+    int32_t n_items, G;
+    // state
+    float2 *r;       // cumulative regret, float-float (hi, lo)
+    float *b;        // behavioural strategy to be played next
+    float *x;        // sequence-form strategy of the last NextStrategy
+    float *xn;       // trunk staging of the next x
+    float2 *xbar;    // weighted sum of played x, float-float
+    // scratch
+    float *u, *ev;
+    double *u64, *ev64, *xnorm;
+    // work counters and the error word (nonzero: a bounded wait gave up)
+    int32_t *game_done, *work, *exits, *err;
+};
+
+struct DevGames {
+    int32_t *t_done;        // completed iterations per game
+    const uint8_t *active;  // 1 = advance this game
+    double *br;             // best-response value per game (BR pass output)
+};
+
+struct IterArgs {
+    int variant;
+    int first_of_iter;      // 1 for the first launch of an iteration (player 1's up pass)
+    float sign;             // +1: u1 = M y ; -1: u2 = -M^T x
+    double alpha, beta, gamma;
+    int average;            // down pass: accumulate xbar (0 when only rebuilding x)
+};
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (error-free transforms: Knuth two-sum, Dekker)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_add_f(float2 a, float b) {
+    float2 s = ff_two_sum(a.x, b);
+    return ff_fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float2 s = ff_two_sum(a.x, b.x);
+    return ff_fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
+    const float p = __fmul_rn(a.x, b);
+    const float e = fmaf(a.y, b, fmaf(a.x, b, -p));
+    return ff_fast_two_sum(p, e);
+}
+__host__ __device__ __forceinline__ float2 ff_from_double(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// ---------------------------------------------------------------------------
+// per-item parameters, computed once per item by thread 0
+// ---------------------------------------------------------------------------
+struct ItemParams {
+    float2 w;        // t^gamma
+    float2 fpos;     // DCFR: t^alpha / (t^alpha + 1)
+    float2 fneg;     // DCFR: t^beta / (t^beta + 1)
+    int32_t t;
+    int32_t active;
+};
+
+__device__ __forceinline__ void item_params(const DevGames &gm, const IterArgs &ia, int g, ItemParams *ip) {
+    const int32_t t = gm.t_done[g] + (ia.first_of_iter ? 1 : 0);
+    const double td = (double)t;
+    ip->t = t;
+    ip->active = gm.active[g];
+    ip->w = ff_from_double(pow(td, ia.gamma));
+    if (ia.variant == VAR_DCFR) {
+        const double ta = pow(td, ia.alpha), tb = pow(td, ia.beta);
+        ip->fpos = ff_from_double(ta / (ta + 1.0));
+        ip->fneg = ff_from_double(tb / (tb + 1.0));
+    } else {
+        ip->fpos = make_float2(1.f, 0.f);
+        ip->fneg = make_float2(1.f, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// payoff product rows: u[s] = sign * sum_k val[k] * xo[col[k]] for s in the
+// sequence ranges of the given unit levels (kLvl ints each).  Each warp owns
+// groups of 32 consecutive rows, reads their contiguous nonzeros with
+// coalesced loads, stages the products in shared memory and lets each lane
+// sum its own row in CSR order (deterministic).
+// ---------------------------------------------------------------------------
+template <typename T, typename TV>
+__device__ void spmv_ranges(const int32_t *__restrict__ m_ptr, const int32_t *__restrict__ m_col,
+                            const TV *__restrict__ m_val, const T *__restrict__ xo, T *__restrict__ u,
+                            const int32_t *lvls, int n_lvls, T sign, T *stage_all) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    T *stage = stage_all + warp * (32 * kStage);
+    int gbase = 0;
+    for (int q = 0; q < n_lvls; q++) {
+        const int slo = lvls[kLvl * q + 2], shi = lvls[kLvl * q + 3];
+        const int ng = (shi - slo + 31) >> 5;
+        // group k of this range is handled by warp (gbase + k) % nw
+        int k0 = (warp - gbase) % nw;
+        if (k0 < 0) k0 += nw;
+        for (int k = k0; k < ng; k += nw) {
+            const int row = slo + (k << 5) + lane;
+            const bool has = row < shi;
+            const int p0 = has ? __ldg(&m_ptr[row]) : 0;
+            const int p1 = has ? __ldg(&m_ptr[row + 1]) : 0;
+            const int last = min(31, shi - 1 - slo - (k << 5));
+            const int g0 = __shfl_sync(0xffffffffu, p0, 0);
+            const int g1 = __shfl_sync(0xffffffffu, p1, last);
+            T acc = T(0);
+            for (int base = g0; base < g1; base += 32 * kStage) {
+#pragma unroll
+                for (int e = 0; e < kStage; e++) {
+                    const int kk = base + e * 32 + lane;
+                    T prod = T(0);
+                    if (kk < g1) prod = T(__ldg(&m_val[kk])) * __ldg(&xo[__ldg(&m_col[kk])]);
+                    stage[e * 32 + lane] = prod;
+                }
+                __syncwarp();
+                const int lo = max(p0, base), hi = min(p1, base + 32 * kStage);
+                for (int kk = lo; kk < hi; kk++) acc += stage[kk - base];
+                __syncwarp();
+            }
+            if (has) u[row] = sign * acc;
+        }
+        gbase += ng;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bottom-up step for one infoset j (MODE_CFR, global memory): counterfactual
+// values, regret update, variant post-op and the next behavioural strategy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 post_op(float2 r, int variant, const ItemParams &ip) {
+    if (variant == VAR_PLUS || variant == VAR_PCFR_PLUS) {
+        if (r.x < 0.f) r = make_float2(0.f, 0.f);
+    } else if (variant == VAR_DCFR) {
+        if (r.x > 0.f) r = ff_mul(r, ip.fpos);
+        else if (r.x < 0.f) r = ff_mul(r, ip.fneg);
+    }
+    return r;
+}
+
+__device__ __forceinline__ float child_sum(const DevPlayer &P, int s) {
+    float v = 0.f;
+    const int c0 = P.seq_child[s], c1 = P.seq_child[s + 1];
+    for (int c = c0; c < c1; c++) v += __ldcg(&P.ev[c]);
+    return v;
+}
+
+__device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const ItemParams &ip) {
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    const int na = s1 - s0;
+    const bool pred = (variant == VAR_PCFR_PLUS);
+    float ev = 0.f;
+    for (int s = s0; s < s1; s++) {
+        const float v = P.u[s] + child_sum(P, s);
+        P.u[s] = v;   // u is scratch: keep V for the next passes
+        ev = fmaf(P.b[s], v, ev);
+    }
+    P.ev[j] = ev;
+    float pos = 0.f;
+    for (int s = s0; s < s1; s++) {
+        const float d = P.u[s] - ev;
+        float2 r = ff_add_f(P.r[s], d);
+        r = post_op(r, variant, ip);
+        P.r[s] = r;
+        const float rr = pred ? r.x + d : r.x;
+        const float q = rr > 0.f ? rr : 0.f;
+        P.u[s] = q;
+        pos += q;
+    }
+    const float inv = pos > 0.f ? 1.0f / pos : 0.f;
+    const float uni = 1.0f / (float)na;
+    for (int s = s0; s < s1; s++) P.b[s] = pos > 0.f ? P.u[s] * inv : uni;
+}
+
+// best-response step (MODE_BR, FP64): V = u + sum children, ev = max_a V
+__device__ void up_infoset_br(const DevPlayer &P, int j) {
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    double best = -INFINITY;
+    for (int s = s0; s < s1; s++) {
+        double v = P.u64[s];
+        const int c0 = P.seq_child[s], c1 = P.seq_child[s + 1];
+        for (int c = c0; c < c1; c++) v += __ldcg(&P.ev64[c]);
+        best = v > best ? v : best;
+    }
+    P.ev64[j] = best;
+}
+
+// Levels of one work unit bottom-up (deepest first), after its payoff rows,
+// straight from global memory (trunks, units too large to stage, and the
+// best-response pass).  rng: kLvl ints per level.
+template <int MODE>
+__device__ void run_up(const DevPlayer &P, const void *xo, const IterArgs &ia, const ItemParams &ip, int nlvl,
+                       const int32_t *rng, void *stage) {
+    if (MODE == MODE_CFR)
+        spmv_ranges<float, float>(P.m_ptr, P.m_col, P.m_val, (const float *)xo, P.u, rng, nlvl, ia.sign,
+                                  (float *)stage);
+    else
+        spmv_ranges<double, double>(P.m_ptr, P.m_col, P.m_val64, (const double *)xo, P.u64, rng, nlvl,
+                                    (double)ia.sign, (double *)stage);
+    __syncthreads();
+    for (int k = nlvl - 1; k >= 0; k--) {
+        const int jlo = rng[kLvl * k], jhi = rng[kLvl * k + 1];
+        for (int j = jlo + (int)threadIdx.x; j < jhi; j += blockDim.x) {
+            if (MODE == MODE_CFR) up_infoset_cfr(P, j, ia.variant, ip);
+            else up_infoset_br(P, j);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace cfrb
