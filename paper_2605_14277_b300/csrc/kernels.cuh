@@ -197,8 +197,9 @@ __device__ __forceinline__ float2 post_op(float2 r, int variant, const ItemParam
     return r;
 }
 
-__device__ __forceinline__ float child_sum(const DevPlayer &P, int s) {
-    float v = 0.f;
+// V[s] = u[s] + ev of each child infoset, added in child order
+__device__ __forceinline__ float value_of(const DevPlayer &P, int s) {
+    float v = P.u[s];
     const int c0 = P.seq_child[s], c1 = P.seq_child[s + 1];
     for (int c = c0; c < c1; c++) v += __ldcg(&P.ev[c]);
     return v;
@@ -210,7 +211,7 @@ __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const Ite
     const bool pred = (variant == VAR_PCFR_PLUS);
     float ev = 0.f;
     for (int s = s0; s < s1; s++) {
-        const float v = P.u[s] + child_sum(P, s);
+        const float v = value_of(P, s);
         P.u[s] = v;   // u is scratch: keep V for the next passes
         ev = fmaf(P.b[s], v, ev);
     }
