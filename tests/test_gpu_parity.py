@@ -150,10 +150,12 @@ def perturb(t, seed, eps=1e-12):
 
 
 def oracle_spread(tree, variant, T):
-    """Final exploitability of FP64 oracle runs that differ only below the
-    level of any meaningful change: the game itself, two relabellings of its
-    infosets (summation order) and three 1e-12 payoff perturbations."""
-    games = [tree, relabel(tree, 1), relabel(tree, 2), perturb(tree, 1), perturb(tree, 2), perturb(tree, 3)]
+    """Final exploitability of FP64 oracle runs that differ from the game only
+    at the level of the GPU's arithmetic: the game itself, two relabellings of
+    its infosets (summation order), three 1e-12 payoff perturbations and three
+    at FP32 rounding level (1e-7; the passes run in FP32)."""
+    games = [tree, relabel(tree, 1), relabel(tree, 2), perturb(tree, 1), perturb(tree, 2), perturb(tree, 3),
+             perturb(tree, 4, 1e-7), perturb(tree, 5, 1e-7), perturb(tree, 6, 1e-7)]
     runs = []
     for t in games:
         o = Oracle(t)
