@@ -95,26 +95,28 @@ __device__ void trunk_topdown(const DevPlayer &P, int g) {
 __global__ void __launch_bounds__(kThreadsS, 1)
     k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *bufs0 = smem, *bufs1 = smem + item_bytes;
+    unsigned char *bufs[2] = {smem, smem + item_bytes};
     float *stage = (float *)(smem + 2 * item_bytes);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ UpTab tab[2][kMaxStagedLevels];
     __shared__ int s_next, s_last, s_err;
     __shared__ ItemParams s_ip;
-    const int tid = threadIdx.x;
+    __shared__ ParamCache s_pc;
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         s_next = atomicAdd(P.work, 1);
+        s_pc.t = -1;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u};
     int cur = s_next, buf = 0;
-    if (tid == 0 && cur < P.n_items) {
+    if (warp == 0 && cur < P.n_items) {
         const int4 h = P.items[cur];
-        if (h.w & kStaged) issue_up(P, h, bufs0, &bar[0], lv[0], tab[0]);
+        if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0]);
     }
     while (cur < P.n_items) {
         if (tid == 0) s_next = atomicAdd(P.work, 1);
@@ -122,12 +124,13 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         const int nxt = s_next;
         const int4 h = P.items[cur];
         const int g = h.x;
-        if (tid == 0) {
-            if (nxt < P.n_items) {
-                const int4 hn = P.items[nxt];
-                if (hn.w & kStaged) issue_up(P, hn, buf ? bufs0 : bufs1, &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
-            }
-            item_params(gm, ia, g, &s_ip);
+        // warp 0 starts the next unit's copies while warp 1 fetches this unit's parameters
+        if (warp == 0 && nxt < P.n_items) {
+            const int4 hn = P.items[nxt];
+            if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+        }
+        if (tid == 32) {
+            cached_params(gm, ia, g, &s_pc, &s_ip);
             s_err = 0;
         }
         __syncthreads();
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
         if (s_err) break;
         const ItemParams ip = s_ip;
         if (ip.active) {
-            if (h.w & kStaged) compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf]);
+            if (h.w & kStaged) compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], false);
             else run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, stage);
             __syncthreads();
             if (tid == 0) {
@@ -149,9 +152,21 @@ __global__ void __launch_bounds__(kThreadsS, 1)
             }
             __syncthreads();
             if (s_last) {
+                // this game's trunk, in the buffer the unit just released
                 __threadfence();
                 const int4 tr = P.trunks[g];
-                run_up<MODE_CFR>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
+                if (tr.w & kStaged) {
+                    if (warp == 0) issue_up(P, tr, bufs[buf], &bar[buf], lv[buf], tab[buf]);
+                    __syncthreads();
+                    if (!mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+                    ph[buf] ^= 1u;
+                    __syncthreads();
+                    if (s_err) break;
+                    compute_up(P, xo, ia, ip, tr.y, lv[buf], tab[buf], true);
+                    __syncthreads();
+                } else {
+                    run_up<MODE_CFR>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
+                }
                 trunk_topdown(P, g);
                 if (tid == 0) {
                     P.game_done[g] = 0;
@@ -192,25 +207,27 @@ __device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParam
 // trunk's staged x into place.
 __global__ void __launch_bounds__(kThreadsS, 1) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *bufs0 = smem, *bufs1 = smem + item_bytes;
+    unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ DownTab tab[2][kMaxStagedLevels];
     __shared__ int s_next, s_err;
     __shared__ ItemParams s_ip;
-    const int tid = threadIdx.x;
+    __shared__ ParamCache s_pc;
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         s_next = atomicAdd(P.work, 1);
+        s_pc.t = -1;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u};
     int cur = s_next, buf = 0;
-    if (tid == 0 && cur < P.n_items) {
+    if (warp == 0 && cur < P.n_items) {
         const int4 h = P.items[cur];
-        if (h.w & kStaged) issue_down(P, h, bufs0, &bar[0], lv[0], tab[0]);
+        if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0]);
     }
     const bool avg = ia.average != 0;
     while (cur < P.n_items) {
@@ -219,12 +236,12 @@ __global__ void __launch_bounds__(kThreadsS, 1) k_down_staged(DevPlayer P, DevGa
         const int nxt = s_next;
         const int4 h = P.items[cur];
         const int g = h.x;
-        if (tid == 0) {
-            if (nxt < P.n_items) {
-                const int4 hn = P.items[nxt];
-                if (hn.w & kStaged) issue_down(P, hn, buf ? bufs0 : bufs1, &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
-            }
-            item_params(gm, ia, g, &s_ip);
+        if (warp == 0 && nxt < P.n_items) {
+            const int4 hn = P.items[nxt];
+            if (hn.w & kStaged) issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+        }
+        if (tid == 32) {
+            cached_params(gm, ia, g, &s_pc, &s_ip);
             s_err = 0;
         }
         __syncthreads();
@@ -542,7 +559,7 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     }
     for (size_t g = 0; g < H.trunks.size(); g++) {
         const Item &it = H.trunks[g];
-        trunks[g] = make_int4(it.game, it.nlvl, it.rng, 0);
+        trunks[g] = make_int4(it.game, it.nlvl, it.rng, it.flags);
     }
     int4 *p4;
     TRY(upload(c, &p4, items));

@@ -442,7 +442,15 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             c = std::min(c, std::max(1, nl));
             P.game_cut[g] = c;
             P.trunks[g] = {(int32_t)g, 0, std::min(c, nl), (int32_t)P.ranges.size(), 0};
-            for (int32_t d = 0; d < std::min(c, nl); d++) push_level(lv[d].first, lv[d].second);
+            {
+                int64_t fu = 0;
+                for (int32_t d = 0; d < std::min(c, nl); d++) {
+                    push_level(lv[d].first, lv[d].second);
+                    const int32_t s0 = P.inf_seq[lv[d].first], s1 = P.inf_seq[lv[d].second];
+                    fu += up_level_bytes(s1 - s0, lv[d].second - lv[d].first, P.m_ptr[s1] - P.m_ptr[s0]);
+                }
+                if (std::min(c, nl) <= kMaxStagedLevels && fu <= opt.item_bytes) P.trunks[g].flags |= kStaged;
+            }
             auto emit = [&](int32_t a, int32_t b) {
                 Item it{(int32_t)g, c, 0, (int32_t)P.ranges.size(), 0};
                 int32_t lo = a, hi = b;

@@ -55,6 +55,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_
     return false;
 }
 
+// Per-iteration parameters depend on the game only through its iteration
+// counter t, so a CTA keeps the last set it computed (FP64 pow on B300 is slow).
+struct ParamCache {
+    int32_t t;
+    ItemParams p;
+};
+__device__ __forceinline__ void cached_params(const DevGames &gm, const IterArgs &ia, int g, ParamCache *c,
+                                              ItemParams *out) {
+    const int32_t t = gm.t_done[g] + (ia.first_of_iter ? 1 : 0);
+    if (t != c->t) {
+        item_params(gm, ia, g, &c->p);
+        c->t = t;
+    }
+    *out = c->p;
+    out->t = t;
+    out->active = gm.active[g];
+}
+
 // one unit level as staged in shared memory
 struct SLvl {
     int32_t j0, j1, s0, s1, n0, n1;
@@ -90,92 +108,131 @@ __device__ __forceinline__ unsigned char *place(unsigned char *&cur, const void 
     return dst + (g0 - A);
 }
 
-// Thread 0 only: lay out a unit in buffer `buf` and start its copies.  The
-// shared tables are filled and the bytes counted first, then the barrier is
-// armed and the copies issued.
+// Warp 0 (all 32 lanes): lay out a unit in buffer `buf` and start its copies.
+// Lane k owns level k: it sizes the level (the same formula the host packer
+// used), a warp scan places the levels one after another, lane 0 arms the
+// barrier with the total byte count, then every lane issues its level's copies.
 __device__ void issue_up(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
                          UpTab *tab) {
+    const int lane = threadIdx.x & 31;
     const int32_t *rng = P.ranges + hdr.z;
     const int nl = hdr.y;
-    const void *src[kMaxStagedLevels][7];
-    uint32_t nb[kMaxStagedLevels][7];
-    uint32_t total = 0;
-    unsigned char *cur = buf;
-    for (int k = 0; k < nl; k++) {
-        const int32_t *d = rng + kLvl * k;
-        const SLvl L{d[0], d[1], d[2], d[3], d[4], d[5]};
-        lv[k] = L;
-        UpTab &t = tab[k];
-        t.r = (float2 *)place(cur, P.r, L.s0, L.s1, 8, &src[k][0], &nb[k][0]);
-        t.b = (float *)place(cur, P.b, L.s0, L.s1, 4, &src[k][1], &nb[k][1]);
-        t.sch = (const int32_t *)place(cur, P.seq_child, L.s0, L.s1 + 1, 4, &src[k][2], &nb[k][2]);
-        t.mptr = (const int32_t *)place(cur, P.m_ptr, L.s0, L.s1 + 1, 4, &src[k][3], &nb[k][3]);
-        t.iseq = (const int32_t *)place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &src[k][4], &nb[k][4]);
-        t.col = (const int32_t *)place(cur, P.m_col, L.n0, L.n1, 4, &src[k][5], &nb[k][5]);
-        t.val = (float *)place(cur, P.m_val, L.n0, L.n1, 4, &src[k][6], &nb[k][6]);
+    SLvl L{0, 0, 0, 0, 0, 0};
+    int64_t bytes = 0;
+    if (lane < nl) {
+        const int32_t *d = rng + kLvl * lane;
+        L = SLvl{d[0], d[1], d[2], d[3], d[4], d[5]};
+        bytes = up_level_bytes(L.s1 - L.s0, L.j1 - L.j0, L.n1 - L.n0);
+    }
+    int64_t off = bytes;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+    }
+    off -= bytes;   // exclusive prefix: this level's start
+    const void *src[7];
+    uint32_t nb[7] = {0, 0, 0, 0, 0, 0, 0};
+    uint32_t mine = 0;
+    if (lane < nl) {
+        unsigned char *cur = buf + off;
+        lv[lane] = L;
+        UpTab t;
+        t.r = (float2 *)place(cur, P.r, L.s0, L.s1, 8, &src[0], &nb[0]);
+        t.b = (float *)place(cur, P.b, L.s0, L.s1, 4, &src[1], &nb[1]);
+        t.sch = (const int32_t *)place(cur, P.seq_child, L.s0, L.s1 + 1, 4, &src[2], &nb[2]);
+        t.mptr = (const int32_t *)place(cur, P.m_ptr, L.s0, L.s1 + 1, 4, &src[3], &nb[3]);
+        t.iseq = (const int32_t *)place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &src[4], &nb[4]);
+        t.col = (const int32_t *)place(cur, P.m_col, L.n0, L.n1, 4, &src[5], &nb[5]);
+        t.val = (float *)place(cur, P.m_val, L.n0, L.n1, 4, &src[6], &nb[6]);
         t.V = (float *)cur;
         cur += work16(L.s1 - L.s0, 4);
         t.ev = (float *)cur;
-        cur += work16(L.j1 - L.j0, 4);
-        for (int f = 0; f < 7; f++) total += nb[k][f];
+        tab[lane] = t;
+        for (int f = 0; f < 7; f++) mine += nb[f];
     }
+    uint32_t total = mine;
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
     fence_proxy_async();
-    mbar_arrive_expect_tx(bar, total);
-    for (int k = 0; k < nl; k++) {
-        const void *dsts[7] = {tab[k].r, tab[k].b, tab[k].sch, tab[k].mptr, tab[k].iseq, tab[k].col, tab[k].val};
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    __syncwarp();
+    if (lane < nl) {
+        const UpTab &t = tab[lane];
+        const void *dsts[7] = {t.r, t.b, t.sch, t.mptr, t.iseq, t.col, t.val};
         for (int f = 0; f < 7; f++)
-            if (nb[k][f]) {
-                // the reserved span starts 16-aligned; the element pointer sits
-                // at the same offset from it as the source element from A
-                void *d0 = (void *)(((uintptr_t)dsts[f]) & ~(uintptr_t)15);
-                bulk_g2s(d0, src[k][f], nb[k][f], bar);
-            }
+            if (nb[f]) bulk_g2s((void *)(((uintptr_t)dsts[f]) & ~(uintptr_t)15), src[f], nb[f], bar);
     }
 }
 
 __device__ void issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
                            DownTab *tab) {
+    const int lane = threadIdx.x & 31;
     const int32_t *rng = P.ranges + hdr.z;
     const int nl = hdr.y;
-    const void *src[kMaxStagedLevels][5];
-    uint32_t nb[kMaxStagedLevels][5];
-    uint32_t total = 0;
-    unsigned char *cur = buf;
-    for (int k = 0; k < nl; k++) {
-        const int32_t *d = rng + kLvl * k;
-        const SLvl L{d[0], d[1], d[2], d[3], d[4], d[5]};
-        lv[k] = L;
-        DownTab &t = tab[k];
-        t.b = (float *)place(cur, P.b, L.s0, L.s1, 4, &src[k][0], &nb[k][0]);
-        t.x = (float *)place(cur, P.x, L.s0, L.s1, 4, &src[k][1], &nb[k][1]);
-        t.xbar = (float2 *)place(cur, P.xbar, L.s0, L.s1, 8, &src[k][2], &nb[k][2]);
-        t.ipar = (const int32_t *)place(cur, P.inf_par, L.j0, L.j1, 4, &src[k][3], &nb[k][3]);
-        t.iseq = (const int32_t *)place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &src[k][4], &nb[k][4]);
-        for (int f = 0; f < 5; f++) total += nb[k][f];
+    SLvl L{0, 0, 0, 0, 0, 0};
+    int64_t bytes = 0;
+    if (lane < nl) {
+        const int32_t *d = rng + kLvl * lane;
+        L = SLvl{d[0], d[1], d[2], d[3], d[4], d[5]};
+        bytes = down_level_bytes(L.s1 - L.s0, L.j1 - L.j0);
     }
+    int64_t off = bytes;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+    }
+    off -= bytes;
+    const void *src[5];
+    uint32_t nb[5] = {0, 0, 0, 0, 0};
+    uint32_t mine = 0;
+    if (lane < nl) {
+        unsigned char *cur = buf + off;
+        lv[lane] = L;
+        DownTab t;
+        t.b = (float *)place(cur, P.b, L.s0, L.s1, 4, &src[0], &nb[0]);
+        t.x = (float *)place(cur, P.x, L.s0, L.s1, 4, &src[1], &nb[1]);
+        t.xbar = (float2 *)place(cur, P.xbar, L.s0, L.s1, 8, &src[2], &nb[2]);
+        t.ipar = (const int32_t *)place(cur, P.inf_par, L.j0, L.j1, 4, &src[3], &nb[3]);
+        t.iseq = (const int32_t *)place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &src[4], &nb[4]);
+        tab[lane] = t;
+        for (int f = 0; f < 5; f++) mine += nb[f];
+    }
+    uint32_t total = mine;
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
     fence_proxy_async();
-    mbar_arrive_expect_tx(bar, total);
-    for (int k = 0; k < nl; k++) {
-        const void *dsts[5] = {tab[k].b, tab[k].x, tab[k].xbar, tab[k].ipar, tab[k].iseq};
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    __syncwarp();
+    if (lane < nl) {
+        const DownTab &t = tab[lane];
+        const void *dsts[5] = {t.b, t.x, t.xbar, t.ipar, t.iseq};
         for (int f = 0; f < 5; f++)
-            if (nb[k][f]) {
-                void *d0 = (void *)(((uintptr_t)dsts[f]) & ~(uintptr_t)15);
-                bulk_g2s(d0, src[k][f], nb[k][f], bar);
-            }
+            if (nb[f]) bulk_g2s((void *)(((uintptr_t)dsts[f]) & ~(uintptr_t)15), src[f], nb[f], bar);
     }
 }
 
 // Up pass of a staged unit: payoff rows, bottom-up values, regret update,
 // variant post-op and next strategy, all in shared memory; then write-back.
 __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, const IterArgs &ia,
-                           const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab) {
+                           const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab, bool trunk) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    // products val * xo[col], in place (gathers of the other player's x)
+    // products val * xo[col], in place (gathers of the other player's x),
+    // four independent gathers in flight per thread
     for (int k = 0; k < nl; k++) {
         const int nz = lv[k].n1 - lv[k].n0;
         float *val = tab[k].val;
         const int32_t *col = tab[k].col;
-        for (int q = tid; q < nz; q += nt) val[q] *= __ldg(&xo[col[q]]);
+        for (int q = tid; q < nz; q += 4 * nt) {
+            float g[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int e = q + u * nt;
+                g[u] = e < nz ? __ldg(&xo[col[e]]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int e = q + u * nt;
+                if (e < nz) val[e] *= g[u];
+            }
+        }
     }
     __syncthreads();
     // row sums in CSR order
@@ -196,14 +253,17 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
         const SLvl L = lv[k];
         const UpTab t = tab[k];
         const int ni = L.j1 - L.j0;
-        const int cj0 = (k + 1 < nl) ? lv[k + 1].j0 : 0;
-        const float *evc = (k + 1 < nl) ? tab[k + 1].ev : nullptr;
+        // children of this level: the unit's next level in shared memory, or
+        // (a trunk's deepest level) the work items' top levels in global memory
+        const bool glob = (k + 1 == nl) && trunk;
+        const int cj0 = glob ? 0 : ((k + 1 < nl) ? lv[k + 1].j0 : 0);
+        const float *evc = glob ? P.ev : ((k + 1 < nl) ? tab[k + 1].ev : nullptr);
         for (int i = tid; i < ni; i += nt) {
             const int q0 = t.iseq[i] - L.s0, q1 = t.iseq[i + 1] - L.s0;
             float ev = 0.f;
             for (int q = q0; q < q1; q++) {
                 float v = t.V[q];
-                for (int c = t.sch[q] - cj0; c < t.sch[q + 1] - cj0; c++) v += evc[c];
+                for (int c = t.sch[q] - cj0; c < t.sch[q + 1] - cj0; c++) v += glob ? __ldcg(&evc[c]) : evc[c];
                 t.V[q] = v;
                 ev = fmaf(t.b[q], v, ev);
             }

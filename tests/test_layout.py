@@ -82,6 +82,11 @@ def test_staged_units_fit_their_buffer():
                     n_staged += 1
                     assert fu <= item_bytes and fd <= item_bytes and nlvl <= 24
             assert n_staged > 0
+            for (g, lvl0, nlvl, r0, flags) in d["trunks"]:
+                rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
+                fu = sum(up_bytes(s1 - s0, j1 - j0, n1 - n0) for j0, j1, s0, s1, n0, n1 in rng)
+                if flags & 1:
+                    assert fu <= item_bytes and nlvl <= 24
 
 
 def test_payoff_matrix_matches_sequence_form():
