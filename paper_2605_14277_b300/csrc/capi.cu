@@ -88,10 +88,11 @@ __device__ void trunk_topdown(const DevPlayer &P, int g) {
 }
 
 // Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
-// Alg. 3-5, and NextStrategy's regret matching): persistent CTAs take work
-// units from a queue, stage each unit in shared memory with bulk copies while
-// the previous one is computed, and the CTA completing a game's last unit
-// runs that game's trunk (bottom-up, then top-down into xn).
+// Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take work
+// units from a queue.  Warp 0 is the producer: while warps 1.. compute the
+// current unit out of shared memory, it fetches the next unit and starts that
+// unit's bulk copies into the other buffer.  The CTA completing a game's last
+// unit runs that game's trunk (bottom-up, then top-down into xn).
 __global__ void __launch_bounds__(kThreadsS, 1)
     k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -100,51 +101,60 @@ __global__ void __launch_bounds__(kThreadsS, 1)
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ UpTab tab[2][kMaxStagedLevels];
-    __shared__ int s_next, s_last, s_err;
+    __shared__ int s_cur, s_nxt, s_last, s_err;
     __shared__ ItemParams s_ip;
     __shared__ ParamCache s_pc;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = P.n_items;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        s_next = atomicAdd(P.work, 1);
+        s_cur = atomicAdd(P.work, 1);
         s_pc.t = -1;
+        s_err = 0;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u};
-    int cur = s_next, buf = 0;
-    if (warp == 0 && cur < P.n_items) {
-        const int4 h = P.items[cur];
-        if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+    int cur = s_cur, buf = 0;
+    if (warp == 0) {
+        if (cur < n) {
+            const int4 h = P.items[cur];
+            if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+        }
+        if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
     }
-    while (cur < P.n_items) {
-        if (tid == 0) s_next = atomicAdd(P.work, 1);
-        __syncthreads();
-        const int nxt = s_next;
+    __syncthreads();
+    int nxt = s_nxt;
+    while (cur < n) {
         const int4 h = P.items[cur];
         const int g = h.x;
-        // warp 0 starts the next unit's copies while warp 1 fetches this unit's parameters
-        if (warp == 0 && nxt < P.n_items) {
-            const int4 hn = P.items[nxt];
-            if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
-        }
-        if (tid == 32) {
-            cached_params(gm, ia, g, &s_pc, &s_ip);
-            s_err = 0;
-        }
-        __syncthreads();
-        if (h.w & kStaged) {
-            if (!mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+        const bool staged = (h.w & kStaged) != 0;
+        if (tid == 32) cached_params(gm, ia, g, &s_pc, &s_ip);
+        if (staged) {
+            if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
             ph[buf] ^= 1u;
         }
         __syncthreads();
         if (s_err) break;
         const ItemParams ip = s_ip;
+        if (warp == 0) {
+            // producer: next unit's copies, then the unit after it from the queue
+            if (nxt < n) {
+                const int4 hn = P.items[nxt];
+                if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+            }
+            if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
+        } else if (ip.active && staged) {
+            compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], false);
+        }
+        __syncthreads();
+        const int nxt2 = s_nxt;
         if (ip.active) {
-            if (h.w & kStaged) compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], false);
-            else run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, stage);
-            __syncthreads();
+            if (!staged) {
+                run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, stage);
+                __syncthreads();
+            }
             if (tid == 0) {
                 __threadfence();
                 const int prev = atomicAdd(&P.game_done[g], 1);
@@ -158,11 +168,11 @@ __global__ void __launch_bounds__(kThreadsS, 1)
                 if (tr.w & kStaged) {
                     if (warp == 0) issue_up(P, tr, bufs[buf], &bar[buf], lv[buf], tab[buf]);
                     __syncthreads();
-                    if (!mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+                    if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
                     ph[buf] ^= 1u;
                     __syncthreads();
                     if (s_err) break;
-                    compute_up(P, xo, ia, ip, tr.y, lv[buf], tab[buf], true);
+                    if (warp != 0) compute_up(P, xo, ia, ip, tr.y, lv[buf], tab[buf], true);
                     __syncthreads();
                 } else {
                     run_up<MODE_CFR>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
@@ -176,6 +186,7 @@ __global__ void __launch_bounds__(kThreadsS, 1)
             }
         }
         cur = nxt;
+        nxt = nxt2;
         buf ^= 1;
     }
     if (tid == 0) {
@@ -204,71 +215,79 @@ __device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParam
 
 // Down pass (Alg. 2 NextStrategy below the cut: y += L^T y, x = A^T y) and the
 // average xbar += t^gamma x; the first unit of each game also moves the
-// trunk's staged x into place.
+// trunk's staged x into place.  Same producer / consumer split as the up pass.
 __global__ void __launch_bounds__(kThreadsS, 1) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ DownTab tab[2][kMaxStagedLevels];
-    __shared__ int s_next, s_err;
+    __shared__ int s_cur, s_nxt, s_err;
     __shared__ ItemParams s_ip;
     __shared__ ParamCache s_pc;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = P.n_items;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        s_next = atomicAdd(P.work, 1);
+        s_cur = atomicAdd(P.work, 1);
         s_pc.t = -1;
+        s_err = 0;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u};
-    int cur = s_next, buf = 0;
-    if (warp == 0 && cur < P.n_items) {
-        const int4 h = P.items[cur];
-        if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+    int cur = s_cur, buf = 0;
+    if (warp == 0) {
+        if (cur < n) {
+            const int4 h = P.items[cur];
+            if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+        }
+        if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
     }
+    __syncthreads();
+    int nxt = s_nxt;
     const bool avg = ia.average != 0;
-    while (cur < P.n_items) {
-        if (tid == 0) s_next = atomicAdd(P.work, 1);
-        __syncthreads();
-        const int nxt = s_next;
+    while (cur < n) {
         const int4 h = P.items[cur];
         const int g = h.x;
-        if (warp == 0 && nxt < P.n_items) {
-            const int4 hn = P.items[nxt];
-            if (hn.w & kStaged) issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
-        }
-        if (tid == 32) {
-            cached_params(gm, ia, g, &s_pc, &s_ip);
-            s_err = 0;
-        }
-        __syncthreads();
-        const ItemParams ip = s_ip;
-        if (ip.active && P.item_first[cur]) {
-            const int4 tr = P.trunks[g];
-            const int32_t *rng = P.ranges + tr.z;
-            for (int k = 0; k < tr.y; k++) {
-                const int slo = rng[kLvl * k + 2], shi = rng[kLvl * k + 3];
-                for (int s = slo + tid; s < shi; s += blockDim.x) {
-                    if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
-                    P.x[s] = P.xn[s];
-                }
-            }
-        }
-        if (h.w & kStaged) {
-            if (!mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+        const bool staged = (h.w & kStaged) != 0;
+        if (tid == 32) cached_params(gm, ia, g, &s_pc, &s_ip);
+        if (staged) {
+            if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
             ph[buf] ^= 1u;
         }
         __syncthreads();
         if (s_err) break;
-        if (ip.active) {
-            if (h.w & kStaged) compute_down(P, ia, ip, h.y, lv[buf], tab[buf]);
-            else run_down(P, ia, ip, h.y, P.ranges + h.z);
+        const ItemParams ip = s_ip;
+        if (warp == 0) {
+            if (nxt < n) {
+                const int4 hn = P.items[nxt];
+                if (hn.w & kStaged) issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+            }
+            if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
+        } else if (ip.active) {
+            if (P.item_first[cur]) {
+                const int4 tr = P.trunks[g];
+                const int32_t *rng = P.ranges + tr.z;
+                for (int k = 0; k < tr.y; k++) {
+                    const int slo = rng[kLvl * k + 2], shi = rng[kLvl * k + 3];
+                    for (int s = slo + tid - kProducerThreads; s < shi; s += blockDim.x - kProducerThreads) {
+                        if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
+                        P.x[s] = P.xn[s];
+                    }
+                }
+            }
+            if (staged) compute_down(P, ia, ip, h.y, lv[buf], tab[buf]);
         }
         __syncthreads();
+        const int nxt2 = s_nxt;
+        if (ip.active && !staged) {
+            run_down(P, ia, ip, h.y, P.ranges + h.z);
+            __syncthreads();
+        }
         cur = nxt;
+        nxt = nxt2;
         buf ^= 1;
     }
     if (tid == 0) {

@@ -55,6 +55,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_
     return false;
 }
 
+// Warp 0 of a staged CTA is the producer (queue fetches, bulk-copy issue);
+// warps 1.. compute, synchronising among themselves on named barrier 1.
+constexpr int kProducerThreads = 32;
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x - kProducerThreads) : "memory");
+}
+
 // Per-iteration parameters depend on the game only through its iteration
 // counter t, so a CTA keeps the last set it computed (FP64 pow on B300 is slow).
 struct ParamCache {
@@ -209,11 +216,59 @@ __device__ void issue_down(const DevPlayer &P, const int4 hdr, unsigned char *bu
     }
 }
 
-// Up pass of a staged unit: payoff rows, bottom-up values, regret update,
-// variant post-op and next strategy, all in shared memory; then write-back.
+// Up pass of a staged unit (consumer warps only): payoff rows, bottom-up
+// values, regret update, variant post-op and next strategy, all in shared
+// memory; then write-back.  For a trunk, the deepest level's children are the
+// work items' top-level infosets, read from global memory.
+constexpr int kRegA = 4;   // infosets with at most kRegA actions keep their values in registers
+
+__device__ __forceinline__ void up_step_reg(const UpTab &t, const SLvl &L, int i, int q0, int na, int cj0,
+                                            const float *evc, bool glob, int variant, bool pred,
+                                            const ItemParams &ip) {
+    float V[kRegA], bb[kRegA], qv[kRegA];
+    int cc[kRegA + 1];
+    float2 rr[kRegA];
+#pragma unroll
+    for (int a = 0; a < kRegA; a++)
+        if (a < na) {
+            V[a] = t.V[q0 + a];
+            bb[a] = t.b[q0 + a];
+            rr[a] = t.r[q0 + a];
+        }
+#pragma unroll
+    for (int a = 0; a <= kRegA; a++)
+        if (a <= na) cc[a] = t.sch[q0 + a] - cj0;
+#pragma unroll
+    for (int a = 0; a < kRegA; a++)
+        if (a < na)
+            for (int c = cc[a]; c < cc[a + 1]; c++) V[a] += glob ? __ldcg(&evc[c]) : evc[c];
+    float ev = 0.f;
+#pragma unroll
+    for (int a = 0; a < kRegA; a++)
+        if (a < na) ev = fmaf(bb[a], V[a], ev);
+    t.ev[i] = ev;
+    float pos = 0.f;
+#pragma unroll
+    for (int a = 0; a < kRegA; a++)
+        if (a < na) {
+            const float d = V[a] - ev;
+            float2 r = ff_add_f(rr[a], d);
+            r = post_op(r, variant, ip);
+            t.r[q0 + a] = r;
+            const float x = pred ? r.x + d : r.x;
+            qv[a] = x > 0.f ? x : 0.f;
+            pos += qv[a];
+        }
+    const float inv = pos > 0.f ? 1.0f / pos : 0.f;
+    const float uni = 1.0f / (float)na;
+#pragma unroll
+    for (int a = 0; a < kRegA; a++)
+        if (a < na) t.b[q0 + a] = pos > 0.f ? qv[a] * inv : uni;
+}
+
 __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, const IterArgs &ia,
                            const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab, bool trunk) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     // products val * xo[col], in place (gathers of the other player's x),
     // four independent gathers in flight per thread
     for (int k = 0; k < nl; k++) {
@@ -234,7 +289,7 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
             }
         }
     }
-    __syncthreads();
+    consumer_sync();
     // row sums in CSR order
     for (int k = 0; k < nl; k++) {
         const int ns = lv[k].s1 - lv[k].s0, n0 = lv[k].n0;
@@ -247,7 +302,7 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
             V[q] = ia.sign * acc;
         }
     }
-    __syncthreads();
+    consumer_sync();
     const bool pred = (ia.variant == VAR_PCFR_PLUS);
     for (int k = nl - 1; k >= 0; k--) {
         const SLvl L = lv[k];
@@ -260,6 +315,10 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
         const float *evc = glob ? P.ev : ((k + 1 < nl) ? tab[k + 1].ev : nullptr);
         for (int i = tid; i < ni; i += nt) {
             const int q0 = t.iseq[i] - L.s0, q1 = t.iseq[i + 1] - L.s0;
+            if (q1 - q0 <= kRegA) {
+                up_step_reg(t, L, i, q0, q1 - q0, cj0, evc, glob, ia.variant, pred, ip);
+                continue;
+            }
             float ev = 0.f;
             for (int q = q0; q < q1; q++) {
                 float v = t.V[q];
@@ -283,7 +342,7 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
             const float uni = 1.0f / (float)(q1 - q0);
             for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? t.V[q] * inv : uni;
         }
-        __syncthreads();
+        consumer_sync();
     }
     // write-back (coalesced)
     for (int k = 0; k < nl; k++) {
@@ -305,7 +364,7 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
 // xbar += w x for the strategy being replaced.
 __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv,
                              const DownTab *tab) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     const bool avg = ia.average != 0;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
@@ -321,7 +380,7 @@ __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemP
                 t.x[q] = xp * t.b[q];
             }
         }
-        __syncthreads();
+        consumer_sync();
     }
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
