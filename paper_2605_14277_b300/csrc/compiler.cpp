@@ -394,12 +394,7 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             }
             raw_up[j] = u;
         }
-        int64_t total_raw = 0;
-        for (int64_t g = 0; g < G; g++) total_raw += raw_up[g];
-        // item size: enough items for ~2 per resident CTA, within the buffer
         const int64_t slack_per_level = 8 * 48;
-        int64_t target = total_raw / std::max<int64_t>(1, 2 * opt.slots);
-        target = std::max(opt.min_item_bytes, std::min(target, opt.item_bytes));
         P.game_nitems.assign(G, 0);
         P.game_cut.assign(G, 1);
         P.trunks.resize(G);
@@ -417,6 +412,11 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
         for (int64_t g = 0; g < G; g++) {
             const auto &lv = glv[g];
             const int32_t nl = (int32_t)lv.size();   // levels 0..nl-1
+            // item size: enough items for ~2 per resident CTA if this game were
+            // alone, within the buffer.  It depends on this game only, so a game
+            // is cut into the same units alone and inside a batch.
+            int64_t target = raw_up[g] / std::max<int64_t>(1, 2 * opt.slots);
+            target = std::max(opt.min_item_bytes, std::min(target, opt.item_bytes));
             // the shallowest cut whose subtrees all fit the item target with a
             // trunk of at most trunk_max sequences; otherwise the cut with the
             // smallest largest subtree among those with a small trunk

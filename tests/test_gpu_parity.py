@@ -232,7 +232,8 @@ def test_batch_game_is_identical_alone_and_in_mix(cfr):
         for p in (1, 2):
             a = alone.get_state(p)
             b = batch.get_state(p, game=g)
-            assert rel(b["r"], a["r"]) <= ONE_STEP_RTOL and rel(b["xbar"], a["xbar"]) <= ONE_STEP_RTOL
+            assert np.array_equal(a["r"], b["r"]) and np.array_equal(a["xbar"], b["xbar"])
+            assert np.array_equal(a["b"], b["b"])
 
 
 def test_active_mask_freezes_games(cfr):
