@@ -13,8 +13,8 @@
  *   - All functions return an int status: CFR_OK (0) or a negative CFR_ERR_*.
  *     No call aborts the process and no C++ exception crosses this boundary.
  *   - The library copies every input it is given; output buffers belong to the
- *     caller.  Buffers named host_* are host memory; nothing in this ABI takes a
- *     device pointer.
+ *     caller.  Buffers named host_* are host memory; the only device pointer in
+ *     this ABI is the output of cfr_exploitability_batch_noalloc.
  *   - All device work of a context is issued on the CUDA stream passed at load
  *     time (a cudaStream_t given as void*; NULL = a non-blocking stream the
  *     context creates and owns).  Calls that return data synchronise that
@@ -128,6 +128,30 @@ int cfr_exploitability(cfr_ctx *ctx, double *expl, double *br1, double *br2);
 /* Same for every game of the context: host arrays of n_games entries each
  * (any may be NULL). */
 int cfr_exploitability_batch(cfr_ctx *ctx, double *host_expl, double *host_br1, double *host_br2);
+
+/* Exploitability of every game, like cfr_exploitability_batch, for callers
+ * that cannot allocate memory at the point of the call: code running under a
+ * memory manager that owns the whole device pool (a framework's caching
+ * allocator, an embedded runtime with a fixed budget), or loops where the
+ * device-wide synchronisation of cudaMalloc/cudaFree is not acceptable.  The
+ * paper has no counterpart; this is an interface variant of the FP64
+ * best-response pass.
+ *   - dev_expl: caller-owned DEVICE buffer of n_games doubles (the one device
+ *     pointer of this ABI); expl[g] = (BR1 + BR2) / 2 as in
+ *     cfr_exploitability_batch.
+ *   - Allocates nothing (no cudaMalloc/cudaFree, no host heap): the per-game
+ *     best-response values live in a fixed device array of the library that
+ *     holds at most 65536 games (1 MiB, kept on every GPU that loads the
+ *     library until the process exits).  Contexts with more games get
+ *     CFR_ERR_ARG.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the context's device current; make that
+ *     first call before any stream capture.
+ *   - Asynchronous on the context's stream: dev_expl is valid once the stream
+ *     has reached this point (e.g. after cfr_sync).  All calls share the one
+ *     array, so calls whose work overlaps on the GPU (different streams or
+ *     contexts) race; calls on one stream are ordered. */
+int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl);
 
 /* Checkpoint / resume of game g, player p: cumulative regrets r (S_p), the
  * behavioural strategy to be played next b (S_p), the average sums xbar

@@ -57,6 +57,7 @@ def lib():
         L.cfr_get_state.argtypes = [P, i64, i, P, P, P, P]
         L.cfr_set_state.argtypes = [P, i64, i, P, P, P, i64]
         L.cfr_profile_iterations.argtypes = [P, i64, i, d, d, d, P]
+        L.cfr_exploitability_batch_noalloc.argtypes = [P, P]
         L.cfr_sync.argtypes = [P]
         L.cfr_free.argtypes = [P]
         L.cfr_free.restype = None
@@ -175,6 +176,13 @@ class Solver:
         e, b1, b2 = (np.zeros(self.n_games) for _ in range(3))
         _check(lib().cfr_exploitability_batch(self._h, _ptr(e), _ptr(b1), _ptr(b2)), "cfr_exploitability_batch")
         return e, b1, b2
+
+    def exploitability_into(self, dev_ptr: int):
+        """Exploitability of every game written to a caller-owned device buffer
+        of n_games doubles (a device address, e.g. torch's tensor.data_ptr()),
+        without any allocation; asynchronous on the solver's stream."""
+        _check(lib().cfr_exploitability_batch_noalloc(self._h, ctypes.c_void_p(int(dev_ptr))),
+               "cfr_exploitability_batch_noalloc")
 
     def average_strategy(self, player: int, game: int = 0):
         S = self._sizes[game]["S1" if player == 1 else "S2"]

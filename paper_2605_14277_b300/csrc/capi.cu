@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <tuple>
@@ -385,9 +386,17 @@ __global__ void k_set_t(int32_t *t_done, int g, int32_t t) { t_done[g] = t; }
 namespace {
 
 thread_local std::string g_last_error;
+thread_local const char *g_last_error_static = nullptr;
 
 int set_err(int code, const std::string &m) {
     g_last_error = m;
+    g_last_error_static = nullptr;
+    return code;
+}
+
+// error with a static message: no allocation on this path
+int set_err_static(int code, const char *m) {
+    g_last_error_static = m;
     return code;
 }
 
@@ -775,7 +784,84 @@ int check_game(cfr_ctx *c, int64_t g, int player) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// exploitability without allocating: scratch in a fixed device array
+// ---------------------------------------------------------------------------
+namespace {
+
+// Best-response values of both players for up to kNoAllocMaxGames games.  Every
+// GPU that loads this library holds the array (1 MiB) until the process exits.
+constexpr int64_t kNoAllocMaxGames = 1 << 16;
+static __device__ __align__(256) double g_noalloc_br[2 * kNoAllocMaxGames];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per
+// device.  In host code the array's name is only a host-side stand-in.
+int noalloc_scratch(int dev, double **out) {
+    if (dev < 0 || dev >= kMaxDevices) return set_err_static(CFR_ERR_ARG, "device ordinal out of range for the scratch table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_br) != cudaSuccess)
+            return set_err_static(CFR_ERR_CUDA, "cudaGetSymbolAddress of the exploitability scratch failed");
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CFR_OK;
+}
+
+__global__ void k_expl_combine(const double *br1, const double *br2, int64_t G, double *expl) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x)
+        expl[g] = 0.5 * (br1[g] + br2[g]);
+}
+
+}  // namespace
+
 extern "C" {
+
+int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl) {
+    if (!ctx) return set_err_static(CFR_ERR_ARG, "ctx is NULL");
+    if (!dev_expl) return set_err_static(CFR_ERR_ARG, "dev_expl is NULL");
+    if (ctx->poisoned) return set_err_static(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    if (ctx->G > kNoAllocMaxGames)
+        return set_err_static(CFR_ERR_ARG, "too many games: the no-allocation exploitability handles at most 65536");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_err_static(CFR_ERR_CUDA, "cudaGetDevice failed");
+    if (dev != ctx->device) return set_err_static(CFR_ERR_ARG, "the context's device must be current");
+    double *br = nullptr;
+    TRY(noalloc_scratch(dev, &br));
+    double *br1 = br, *br2 = br + kNoAllocMaxGames;
+    // the scratch keeps the previous call's values: start every game from zero
+    if (cudaMemsetAsync(br1, 0, ctx->G * sizeof(double), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(br2, 0, ctx->G * sizeof(double), ctx->stream) != cudaSuccess)
+        return set_err_static(CFR_ERR_CUDA, "clearing the exploitability scratch failed");
+    const bool masked = std::find(ctx->active_host.begin(), ctx->active_host.end(), 0) != ctx->active_host.end();
+    if (masked && cudaMemsetAsync(ctx->active, 1, ctx->G, ctx->stream) != cudaSuccess)
+        return set_err_static(CFR_ERR_CUDA, "cudaMemsetAsync failed");
+    DevGames gm{ctx->t_done, ctx->active, nullptr};
+    IterArgs ia{};
+    for (int p = 0; p < 2; p++) {
+        PlayerBuf &B = ctx->pl[p];
+        k_normalize<<<(unsigned)std::min<int64_t>((B.S + kThreads - 1) / kThreads, 65535), kThreads, 0,
+                      ctx->stream>>>(B.d, B.S);
+    }
+    for (int p = 0; p < 2; p++) {
+        PlayerBuf &B = ctx->pl[p];
+        gm.br = p == 0 ? br1 : br2;
+        ia.sign = p == 0 ? 1.f : -1.f;
+        k_up<MODE_BR><<<B.grid_up_br, kThreads, B.smem_br, ctx->stream>>>(B.d, gm, ctx->pl[1 - p].d.xnorm, ia);
+    }
+    k_expl_combine<<<(unsigned)std::min<int64_t>((ctx->G + 255) / 256, 65535), 256, 0, ctx->stream>>>(br1, br2,
+                                                                                                    ctx->G, dev_expl);
+    if (cudaGetLastError() != cudaSuccess) return set_err_static(CFR_ERR_CUDA, "kernel launch failed");
+    if (masked && cudaMemcpyAsync(ctx->active, ctx->active_host.data(), ctx->G, cudaMemcpyHostToDevice,
+                                  ctx->stream) != cudaSuccess)
+        return set_err_static(CFR_ERR_CUDA, "cudaMemcpyAsync failed");
+    return CFR_OK;
+}
 
 int cfr_load_tree(const cfr_tree_desc *tree, void *cuda_stream, cfr_ctx **out) {
     return load(tree, 1, cuda_stream, out);
@@ -1003,6 +1089,6 @@ const char *cfr_strerror(int status) {
     }
 }
 
-const char *cfr_last_error(void) { return g_last_error.c_str(); }
+const char *cfr_last_error(void) { return g_last_error_static ? g_last_error_static : g_last_error.c_str(); }
 
 }  // extern "C"
