@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -28,8 +29,74 @@ using namespace cfrb;
 // ---------------------------------------------------------------------------
 namespace cfrb {
 
-// Best-response pass (MODE_BR, FP64) over every work unit from global memory;
-// the trunk of each game runs on the CTA that completes the game's last unit.
+// the last CTA to leave a launch resets the queue for the next launch and
+// advances the epoch
+__device__ __forceinline__ void launch_exit(const DevPlayer &P) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
+            *P.work = 0;
+            *P.exits = 0;
+            atomicAdd(P.epoch, 1);
+        }
+    }
+}
+
+// Bottom-up completion: unit v of the current game is done.  Returns the
+// parent unit if this CTA completed the parent's last child (the caller runs
+// it next), else -1; -2 when v is the game's root.
+__device__ __forceinline__ int climb(const DevPlayer &P, int v, int *s_last) {
+    const int par = P.unit_tree[v].x;
+    if (par < 0) return -2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int prev = atomicAdd(&P.unit_cnt[par], 1);
+        const int last = (prev == P.unit_tree[par].y - 1);
+        if (last) P.unit_cnt[par] = 0;
+        *s_last = last;
+    }
+    __syncthreads();
+    if (!*s_last) return -1;
+    __threadfence();
+    return par;
+}
+
+// the root unit's next x, top-down from global memory, into xn (level 0's
+// parent is the empty sequence, x = 1)
+__device__ void root_topdown_global(const DevPlayer &P, int nlvl, const int32_t *rng) {
+    for (int k = 0; k < nlvl; k++) {
+        for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
+            const int par = P.inf_par[j];
+            const float xp = par < 0 ? 1.f : P.xn[par];
+            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) P.xn[s] = xp * P.b[s];
+        }
+        __syncthreads();
+    }
+}
+
+// xn of every game's root unit from the current b (one CTA per game), when x
+// is rebuilt outside an iteration
+__global__ void k_root_topdown(DevPlayer P) {
+    const int4 h = P.units[P.game_root[blockIdx.x]];
+    root_topdown_global(P, h.y, P.ranges + h.z);
+}
+
+// Per-game parameters of iterations t = t_done + k, k = 0..kParamSpan, for the
+// passes that follow (one thread per entry).
+__global__ void k_params(DevGames gm, IterArgs ia, int G) {
+    const int64_t n = (int64_t)G * (kParamSpan + 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e / (kParamSpan + 1)), k = (int)(e % (kParamSpan + 1));
+        const int32_t t0 = gm.t_done[g];
+        params_of_t(gm, ia, g, t0 + k, &gm.par[e]);
+        if (k == 0) gm.pbase[g] = t0;
+    }
+}
+
+// Best-response pass (MODE_BR, FP64) over every unit from global memory:
+// leaves from the queue, each internal unit on the CTA completing its last
+// child; the root's ev is the game's best-response value.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const void *xo, IterArgs ia) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -40,171 +107,142 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         if (threadIdx.x == 0) s_item = atomicAdd(P.work, 1);
         __syncthreads();
         const int it = s_item;
-        if (it >= P.n_items) break;
-        const int4 d = P.items[it];
-        const int g = d.x;
+        __syncthreads();
+        if (it >= P.n_up) break;
+        int u = P.up_queue[it];
+        const int g = P.units[u].x;
         if (threadIdx.x == 0) item_params(gm, ia, g, &s_ip);
         __syncthreads();
         const ItemParams ip = s_ip;
         if (!ip.active) continue;
-        run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage);
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const int prev = atomicAdd(&P.game_done[g], 1);
-            s_last = (prev == P.game_nitems[g] - 1);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            const int4 tr = P.trunks[g];
-            run_up<MODE>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
-            if (threadIdx.x == 0) {
-                if (MODE == MODE_BR) gm.br[g] = __ldcg(&P.ev64[g]);
-                P.game_done[g] = 0;
+        for (;;) {
+            const int4 d = P.units[u];
+            run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage);
+            const int par = climb(P, u, &s_last);
+            if (par == -2) {
+                if (threadIdx.x == 0 && MODE == MODE_BR) gm.br[g] = __ldcg(&P.ev64[g]);
+                break;
             }
-            __syncthreads();
+            if (par < 0) break;
+            u = par;
         }
     }
-    if (threadIdx.x == 0) {
-        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
-            *P.work = 0;
-            *P.exits = 0;
-        }
-    }
-}
-
-// trunk top-down into the staging vector xn (Alg. 2 NextStrategy above the cut)
-__device__ void trunk_topdown(const DevPlayer &P, int g) {
-    const int4 tr = P.trunks[g];
-    const int32_t *rng = P.ranges + tr.z;
-    if (threadIdx.x == 0) P.xn[g] = 1.f;
-    __syncthreads();
-    for (int k = 1; k < tr.y; k++) {
-        for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
-            const float xp = P.xn[P.inf_par[j]];
-            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) P.xn[s] = xp * P.b[s];
-        }
-        __syncthreads();
-    }
+    launch_exit(P);
 }
 
 // Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
-// Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take work
+// Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take leaf
 // units from a queue.  Warp 0 is the producer: while warps 1.. compute the
-// current unit out of shared memory, it fetches the next unit and starts that
-// unit's bulk copies into the other buffer.  The CTA completing a game's last
-// unit runs that game's trunk (bottom-up, then top-down into xn).
-__global__ void __launch_bounds__(kThreadsS, 1)
+// current unit out of shared memory, it fetches the next unit, loads its
+// parameters and starts its bulk copies into the other buffer.  The CTA
+// completing the last child of an internal unit runs that unit next, in the
+// buffer just released; the game's root unit also publishes its next x (xn).
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *bufs[2] = {smem, smem + item_bytes};
-    float *stage = (float *)(smem + 2 * item_bytes);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ UpTab tab[2][kMaxStagedLevels];
+    __shared__ ChildEv cev[2];
     __shared__ int s_cur, s_nxt, s_last, s_err;
-    __shared__ ItemParams s_ip;
-    __shared__ ParamCache s_pc;
+    __shared__ ItemParams s_ip[2];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int n = P.n_items;
+    const int n = P.n_up;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         s_cur = atomicAdd(P.work, 1);
-        s_pc.t = -1;
         s_err = 0;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u};
+    auto stage = [&](const int4 h, int b) { issue_up(P, h, bufs[b], &bar[b], lv[b], tab[b], &cev[b]); };
     int cur = s_cur, buf = 0;
     if (warp == 0) {
         if (cur < n) {
-            const int4 h = P.items[cur];
-            if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+            const int4 h = P.units[P.up_queue[cur]];
+            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x, P.err);
+            if (h.w & kStaged) stage(h, 0);
         }
         if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
     }
     __syncthreads();
-    int nxt = s_nxt;
+    int ahead = s_nxt;   // next queue entry, not yet issued
     while (cur < n) {
-        const int4 h = P.items[cur];
-        const int g = h.x;
-        const bool staged = (h.w & kStaged) != 0;
-        if (tid == 32) cached_params(gm, ia, g, &s_pc, &s_ip);
-        if (staged) {
-            if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
-            ph[buf] ^= 1u;
-        }
-        __syncthreads();
-        if (s_err) break;
-        const ItemParams ip = s_ip;
-        if (warp == 0) {
-            // producer: next unit's copies, then the unit after it from the queue
-            if (nxt < n) {
-                const int4 hn = P.items[nxt];
-                if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
-            }
-            if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
-        } else if (ip.active && staged) {
-            compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], false);
-        }
-        __syncthreads();
-        const int nxt2 = s_nxt;
-        if (ip.active) {
-            if (!staged) {
-                run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, stage);
-                __syncthreads();
-            }
-            if (tid == 0) {
-                __threadfence();
-                const int prev = atomicAdd(&P.game_done[g], 1);
-                s_last = (prev == P.game_nitems[g] - 1);
+        // a unit from the queue, then every parent whose last child it completes
+        int u = P.up_queue[cur];
+        bool from_queue = true;
+        int pend = n;    // queue entry staged in the other buffer
+        for (;;) {
+            const int4 h = P.units[u];
+            const bool staged = (h.w & kStaged) != 0;
+            if (staged) {
+                if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+                ph[buf] ^= 1u;
             }
             __syncthreads();
-            if (s_last) {
-                // this game's trunk, in the buffer the unit just released
-                __threadfence();
-                const int4 tr = P.trunks[g];
-                if (tr.w & kStaged) {
-                    if (warp == 0) issue_up(P, tr, bufs[buf], &bar[buf], lv[buf], tab[buf]);
-                    __syncthreads();
-                    if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
-                    ph[buf] ^= 1u;
-                    __syncthreads();
-                    if (s_err) break;
-                    if (warp != 0) compute_up(P, xo, ia, ip, tr.y, lv[buf], tab[buf], true);
-                    __syncthreads();
-                } else {
-                    run_up<MODE_CFR>(P, xo, ia, ip, tr.y, P.ranges + tr.z, stage);
-                }
-                trunk_topdown(P, g);
-                if (tid == 0) {
-                    P.game_done[g] = 0;
-                    if (ia.first_of_iter) gm.t_done[g] = ip.t;
-                }
-                __syncthreads();
+            if (s_err) {
+                cur = n;
+                break;
             }
+            const ItemParams ip = s_ip[buf];   // a parent belongs to the same game
+            const bool root = P.unit_tree[u].x < 0;
+            if (warp == 0) {
+                // producer: the next queue entry's parameters and copies into
+                // the other buffer, then the entry after it
+                if (from_queue) {
+                    if (tid == 0) s_nxt = ahead < n ? atomicAdd(P.work, 1) : n;
+                    if (ahead < n) {
+                        const int4 hn = P.units[P.up_queue[ahead]];
+                        if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
+                        if (hn.w & kStaged) stage(hn, buf ^ 1);
+                    }
+                }
+            } else if (ip.active && staged) {
+                compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], &cev[buf], (h.w & kInternal) != 0, root);
+            }
+            __syncthreads();
+            if (from_queue) {
+                pend = ahead;
+                ahead = s_nxt;
+            }
+            if (!ip.active) break;
+            if (!staged) {
+                run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
+                if (root) root_topdown_global(P, h.y, P.ranges + h.z);
+            }
+            const int par = climb(P, u, &s_last);
+            if (par == -2) {
+                if (tid == 0 && ia.first_of_iter) gm.t_done[h.x] = ip.t;
+                break;
+            }
+            if (par < 0) break;
+            // this CTA completed the parent's last child: the parent next, in
+            // the buffer just released
+            u = par;
+            from_queue = false;
+            const int4 hp = P.units[u];
+            if ((hp.w & kStaged) && warp == 0) stage(hp, buf);
         }
-        cur = nxt;
-        nxt = nxt2;
+        if (cur >= n) break;
+        cur = pend;
         buf ^= 1;
     }
-    if (tid == 0) {
-        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
-            *P.work = 0;
-            *P.exits = 0;
-        }
-    }
+    launch_exit(P);
 }
 
 // one unit top-down from global memory (units too large to stage)
-__device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nlvl, const int32_t *rng) {
+__device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nlvl, const int32_t *rng,
+                         bool child_of_root) {
     const bool avg = ia.average != 0;
     for (int k = 0; k < nlvl; k++) {
-        const float *xpar = (k == 0) ? P.xn : P.x;
+        const float *xpar = (k == 0 && child_of_root) ? P.xn : P.x;
         for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
-            const float xp = xpar[P.inf_par[j]];
+            const int par = P.inf_par[j];
+            const float xp = par < 0 ? 1.f : __ldcg(&xpar[par]);
             for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) {
                 if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
                 P.x[s] = xp * P.b[s];
@@ -214,93 +252,101 @@ __device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParam
     }
 }
 
-// Down pass (Alg. 2 NextStrategy below the cut: y += L^T y, x = A^T y) and the
-// average xbar += t^gamma x; the first unit of each game also moves the
-// trunk's staged x into place.  Same producer / consumer split as the up pass.
-__global__ void __launch_bounds__(kThreadsS, 1) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
+// Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y) and the average
+// xbar += t^gamma x.  Units come from the queue in unit-tree depth order, so a
+// unit's parent was taken earlier by a running CTA.  A unit's copies start at
+// once; its computation waits until the parent has published its x (flag =
+// epoch + 1), except below the root, whose next x the up pass published in xn.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ DownTab tab[2][kMaxStagedLevels];
-    __shared__ int s_cur, s_nxt, s_err;
-    __shared__ ItemParams s_ip;
-    __shared__ ParamCache s_pc;
+    __shared__ int s_cur, s_nxt, s_err, s_epoch;
+    __shared__ ItemParams s_ip[2];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int n = P.n_items;
+    const int n = P.n_units;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
+        s_epoch = __ldcg(P.epoch);
         s_cur = atomicAdd(P.work, 1);
-        s_pc.t = -1;
         s_err = 0;
     }
     __syncthreads();
+    const int done_flag = s_epoch + 1;
     uint32_t ph[2] = {0u, 0u};
     int cur = s_cur, buf = 0;
     if (warp == 0) {
         if (cur < n) {
-            const int4 h = P.items[cur];
+            const int4 h = P.units[P.down_queue[cur]];
             if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x, P.err);
         }
         if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
     }
     __syncthreads();
     int nxt = s_nxt;
-    const bool avg = ia.average != 0;
     while (cur < n) {
-        const int4 h = P.items[cur];
-        const int g = h.x;
+        const int u = P.down_queue[cur];
+        const int4 h = P.units[u];
+        const int2 tr = P.unit_tree[u];
         const bool staged = (h.w & kStaged) != 0;
-        if (tid == 32) cached_params(gm, ia, g, &s_pc, &s_ip);
+        const bool below_root = (h.w & kChildOfRoot) != 0;
         if (staged) {
             if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
             ph[buf] ^= 1u;
         }
         __syncthreads();
         if (s_err) break;
-        const ItemParams ip = s_ip;
+        const ItemParams ip = s_ip[buf];
+        const bool wait = ip.active && tr.x >= 0 && !below_root;
         if (warp == 0) {
             if (nxt < n) {
-                const int4 hn = P.items[nxt];
+                const int4 hn = P.units[P.down_queue[nxt]];
                 if (hn.w & kStaged) issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
             }
             if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
-        } else if (ip.active) {
-            if (P.item_first[cur]) {
-                const int4 tr = P.trunks[g];
-                const int32_t *rng = P.ranges + tr.z;
-                for (int k = 0; k < tr.y; k++) {
-                    const int slo = rng[kLvl * k + 2], shi = rng[kLvl * k + 3];
-                    for (int s = slo + tid - kProducerThreads; s < shi; s += blockDim.x - kProducerThreads) {
-                        if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
-                        P.x[s] = P.xn[s];
-                    }
+        } else if (ip.active && staged) {
+            if (wait) {
+                if (tid == 32 && !flag_wait(&P.unit_flag[tr.x], done_flag, P.err)) s_err = 1;
+                consumer_sync();
+            }
+            if (!s_err) {
+                compute_down(P, ia, ip, h.y, lv[buf], tab[buf], below_root);
+                if (tr.y > 0 && tr.x >= 0) {
+                    __threadfence();
+                    consumer_sync();
+                    if (tid == 32) st_release(&P.unit_flag[u], done_flag);
                 }
             }
-            if (staged) compute_down(P, ia, ip, h.y, lv[buf], tab[buf]);
         }
         __syncthreads();
+        if (s_err) break;
         const int nxt2 = s_nxt;
         if (ip.active && !staged) {
-            run_down(P, ia, ip, h.y, P.ranges + h.z);
-            __syncthreads();
+            if (wait) {
+                if (tid == 0 && !flag_wait(&P.unit_flag[tr.x], done_flag, P.err)) s_err = 1;
+                __syncthreads();
+                if (s_err) break;
+            }
+            run_down(P, ia, ip, h.y, P.ranges + h.z, below_root);
+            if (tr.y > 0 && tr.x >= 0) {
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) st_release(&P.unit_flag[u], done_flag);
+            }
         }
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
     }
-    if (tid == 0) {
-        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
-            *P.work = 0;
-            *P.exits = 0;
-        }
-    }
+    launch_exit(P);
 }
-
-// trunk top-down, one CTA per game (when x is rebuilt from b outside an iteration)
-__global__ void k_trunk_topdown(DevPlayer P) { trunk_topdown(P, blockIdx.x); }
 
 // uniform behavioural strategy (regret matching of r = 0)
 __global__ void k_uniform(DevPlayer P, int64_t J) {
@@ -400,10 +446,40 @@ int set_err_static(int code, const char *m) {
     return code;
 }
 
+// Launch shapes of the staged passes: threads per CTA, CTAs per SM and the
+// unit buffer (two per CTA).  More, smaller CTAs per SM overlap one CTA's
+// barrier waits and copy latency with another's compute.
+using UpFn = void (*)(DevPlayer, DevGames, const float *, IterArgs, int);
+using DownFn = void (*)(DevPlayer, DevGames, IterArgs, int);
+struct StagedConfig {
+    int threads, ctas_per_sm, item_bytes;
+    UpFn up;
+    DownFn down;
+};
+const StagedConfig kConfigs[] = {
+    {512, 1, 96 * 1024, k_up_staged<512, 1>, k_down_staged<512, 1>},
+    {256, 2, 48 * 1024, k_up_staged<256, 2>, k_down_staged<256, 2>},
+    {256, 3, 32 * 1024, k_up_staged<256, 3>, k_down_staged<256, 3>},
+    {512, 2, 48 * 1024, k_up_staged<512, 2>, k_down_staged<512, 2>},
+    {256, 4, 24 * 1024, k_up_staged<256, 4>, k_down_staged<256, 4>},
+};
+constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
+constexpr int kDefaultConfig = 1;
+
+// the launch shape: CFR_B300_STAGED_CONFIG (an index into kConfigs) if set
+int staged_config() {
+    const char *e = std::getenv("CFR_B300_STAGED_CONFIG");
+    if (e && *e) {
+        const int k = std::atoi(e);
+        if (k >= 0 && k < kNumConfigs) return k;
+    }
+    return kDefaultConfig;
+}
+
 struct PlayerBuf {
     DevPlayer d{};
     int32_t *ext_inf = nullptr, *ext_seq0 = nullptr;
-    int64_t S = 0, J = 0, n_items = 0;
+    int64_t S = 0, J = 0, n_units = 0, n_up = 0;
     int n_levels = 0;
     int grid_up = 1, grid_up_br = 1, grid_down = 1;
     size_t smem_br = 0;
@@ -429,6 +505,8 @@ struct cfr_ctx {
     PlayerBuf pl[2];
     int32_t *t_done = nullptr;
     uint8_t *active = nullptr;
+    ItemParams *par = nullptr;      // per-game parameter table (kParamSpan + 1 entries)
+    int32_t *pbase = nullptr;
     double *br[2] = {nullptr, nullptr};
     double *scratch = nullptr;   // FP64 transfer area: 3 * (max S + 1)
     int64_t scratch_n = 0;
@@ -439,7 +517,9 @@ struct cfr_ctx {
     std::vector<int64_t> game_nodes, game_nnz;
     std::vector<uint8_t> active_host;
     int64_t dev_bytes = 0, h2d_bytes = 0;
-    int item_bytes = 96 * 1024;     // one staged unit buffer (two per CTA)
+    int cfg = kDefaultConfig;       // staged launch shape (kConfigs)
+    int threads = 256;              // threads of a staged CTA
+    int item_bytes = 48 * 1024;     // one staged unit buffer (two per CTA)
     size_t smem_staged = 0;
     int32_t *err = nullptr;         // device error word (bounded waits)
     bool poisoned = false;
@@ -485,13 +565,27 @@ int upload(cfr_ctx *c, T **p, const std::vector<T> &v) {
     return CFR_OK;
 }
 
+DevGames dev_games(const cfr_ctx *c) { return DevGames{c->t_done, c->active, nullptr, c->par, c->pbase}; }
+
+// the parameter table for the next kParamSpan iterations of every game
+int launch_params(cfr_ctx *c, int variant, double alpha, double beta, double gamma) {
+    IterArgs ia{variant, 0, 0.f, alpha, beta, gamma, 0};
+    const int64_t n = c->G * (kParamSpan + 1);
+    k_params<<<(unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096), kThreads, 0, c->stream>>>(
+        dev_games(c), ia, (int)c->G);
+    CU(cudaGetLastError());
+    return CFR_OK;
+}
+
+// x of player p from the current b (top-down, no averaging)
 int launch_rebuild_x(cfr_ctx *c, int p) {
     PlayerBuf &B = c->pl[p];
-    DevGames gm{c->t_done, c->active, nullptr};
+    TRY(launch_params(c, 0, 0.0, 0.0, 0.0));
     IterArgs ia{};
     ia.average = 0;
-    k_trunk_topdown<<<(unsigned)c->G, kThreads, 0, c->stream>>>(B.d);
-    k_down_staged<<<B.grid_down, kThreadsS, c->smem_staged, c->stream>>>(B.d, gm, ia, c->item_bytes);
+    k_root_topdown<<<(unsigned)c->G, kThreads, 0, c->stream>>>(B.d);
+    kConfigs[c->cfg].down<<<B.grid_down, c->threads, c->smem_staged, c->stream>>>(B.d, dev_games(c), ia,
+                                                                                   c->item_bytes);
     CU(cudaGetLastError());
     return CFR_OK;
 }
@@ -499,8 +593,9 @@ int launch_rebuild_x(cfr_ctx *c, int p) {
 // one iteration: NextStrategy/ObserveUtility for both players (Alg. 2), in the
 // alternating or simultaneous schedule (Sec. 3.5.1)
 int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double gamma, bool alternating,
-                     cudaEvent_t *ev = nullptr) {
-    DevGames gm{c->t_done, c->active, nullptr};
+                     bool params, cudaEvent_t *ev = nullptr) {
+    if (params) TRY(launch_params(c, variant, alpha, beta, gamma));
+    const DevGames gm = dev_games(c);
     IterArgs up1{variant, 1, +1.f, alpha, beta, gamma, 1};
     IterArgs up2{variant, 0, -1.f, alpha, beta, gamma, 1};
     IterArgs dn{variant, 0, 0.f, alpha, beta, gamma, 1};
@@ -509,38 +604,40 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
         if (ev) cudaEventRecord(ev[k], c->stream);
     };
     const size_t sm = c->smem_staged;
-    const int ib = c->item_bytes;
+    const int ib = c->item_bytes, nt = c->threads;
+    const UpFn up = kConfigs[c->cfg].up;
+    const DownFn down = kConfigs[c->cfg].down;
     mark(0);
     if (alternating) {
-        k_up_staged<<<A.grid_up, kThreadsS, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
+        up<<<A.grid_up, nt, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
         mark(1);
-        k_down_staged<<<A.grid_down, kThreadsS, sm, c->stream>>>(A.d, gm, dn, ib);
+        down<<<A.grid_down, nt, sm, c->stream>>>(A.d, gm, dn, ib);
         mark(2);
-        k_up_staged<<<B.grid_up, kThreadsS, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
+        up<<<B.grid_up, nt, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
         mark(3);
-        k_down_staged<<<B.grid_down, kThreadsS, sm, c->stream>>>(B.d, gm, dn, ib);
+        down<<<B.grid_down, nt, sm, c->stream>>>(B.d, gm, dn, ib);
     } else {
-        k_up_staged<<<A.grid_up, kThreadsS, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
+        up<<<A.grid_up, nt, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
         mark(1);
-        k_up_staged<<<B.grid_up, kThreadsS, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
+        up<<<B.grid_up, nt, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
         mark(2);
-        k_down_staged<<<A.grid_down, kThreadsS, sm, c->stream>>>(A.d, gm, dn, ib);
+        down<<<A.grid_down, nt, sm, c->stream>>>(A.d, gm, dn, ib);
         mark(3);
-        k_down_staged<<<B.grid_down, kThreadsS, sm, c->stream>>>(B.d, gm, dn, ib);
+        down<<<B.grid_down, nt, sm, c->stream>>>(B.d, gm, dn, ib);
     }
     mark(4);
     CU(cudaGetLastError());
     return CFR_OK;
 }
 
-int occupancy_grid(const void *fn, int threads, size_t smem, int64_t n_items, int *grid) {
+int occupancy_grid(const void *fn, int threads, size_t smem, int64_t n_work, int *grid) {
     int dev = 0, sms = 0, per = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem));
     if (per < 1) return set_err(CFR_ERR_CUDA, "kernel does not fit on an SM");
     const int64_t full = (int64_t)sms * per;
-    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, n_items));
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(full, n_work));
     return CFR_OK;
 }
 
@@ -550,7 +647,8 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     DevPlayer &d = B.d;
     B.S = H.S;
     B.J = H.J;
-    B.n_items = (int64_t)H.items.size();
+    B.n_units = (int64_t)H.units.size();
+    B.n_up = (int64_t)H.up_queue.size();
     B.n_levels = H.n_levels;
     B.game_J = H.game_J;
     B.game_S = H.game_S;
@@ -574,35 +672,31 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     double *pd;
     TRY(upload(c, &pd, H.m_val64));
     d.m_val64 = pd;
-    std::vector<int4> items(H.items.size()), trunks(H.trunks.size());
-    std::vector<int32_t> first(H.items.size(), 0);
-    std::vector<char> seen(L.G, 0);
-    for (size_t k = 0; k < H.items.size(); k++) {
-        const Item &it = H.items[k];
-        items[k] = make_int4(it.game, it.nlvl, it.rng, it.flags);
-        if (!seen[it.game]) {
-            first[k] = 1;
-            seen[it.game] = 1;
-        }
-    }
-    for (size_t g = 0; g < H.trunks.size(); g++) {
-        const Item &it = H.trunks[g];
-        trunks[g] = make_int4(it.game, it.nlvl, it.rng, it.flags);
+    std::vector<int4> units(H.units.size());
+    std::vector<int2> tree(H.units.size());
+    for (size_t k = 0; k < H.units.size(); k++) {
+        const Unit &u = H.units[k];
+        units[k] = make_int4(u.game, u.nlvl, u.rng, u.flags);
+        tree[k] = make_int2(u.parent, u.nchild);
     }
     int4 *p4;
-    TRY(upload(c, &p4, items));
-    d.items = p4;
-    TRY(upload(c, &p4, trunks));
-    d.trunks = p4;
+    TRY(upload(c, &p4, units));
+    d.units = p4;
+    int2 *p2;
+    TRY(upload(c, &p2, tree));
+    d.unit_tree = p2;
     TRY(upload(c, &p32, H.ranges));
     d.ranges = p32;
-    TRY(upload(c, &p32, H.game_nitems));
-    d.game_nitems = p32;
-    TRY(upload(c, &p32, first));
-    d.item_first = p32;
+    TRY(upload(c, &p32, H.up_queue));
+    d.up_queue = p32;
+    TRY(upload(c, &p32, H.down_queue));
+    d.down_queue = p32;
+    TRY(upload(c, &p32, H.game_root));
+    d.game_root = p32;
     TRY(upload(c, &B.ext_inf, H.ext_inf));
     TRY(upload(c, &B.ext_seq0, H.ext_seq0));
-    d.n_items = (int32_t)H.items.size();
+    d.n_units = (int32_t)H.units.size();
+    d.n_up = (int32_t)H.up_queue.size();
     d.G = (int32_t)L.G;
     TRY(dalloc(c, &d.r, H.S));
     TRY(dalloc(c, &d.b, H.S));
@@ -615,11 +709,14 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.ev64, H.J));
     TRY(dalloc(c, &d.xnorm, H.S));
     int32_t *ctr;
-    TRY(dalloc(c, &ctr, L.G + 2));
-    CU(cudaMemsetAsync(ctr, 0, (L.G + 2) * sizeof(int32_t), c->stream));
-    d.game_done = ctr;
-    d.work = ctr + L.G;
-    d.exits = ctr + L.G + 1;
+    const int64_t nu = (int64_t)H.units.size();
+    TRY(dalloc(c, &ctr, 2 * nu + 3));
+    CU(cudaMemsetAsync(ctr, 0, (2 * nu + 3) * sizeof(int32_t), c->stream));
+    d.unit_cnt = ctr;
+    d.unit_flag = ctr + nu;
+    d.work = ctr + 2 * nu;
+    d.exits = ctr + 2 * nu + 1;
+    d.epoch = ctr + 2 * nu + 2;
     d.err = c->err;
     CU(cudaMemsetAsync(d.r, 0, H.S * sizeof(float2), c->stream));
     CU(cudaMemsetAsync(d.xbar, 0, H.S * sizeof(float2), c->stream));
@@ -628,11 +725,13 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     CU(cudaMemsetAsync(d.x, 0, H.S * sizeof(float), c->stream));
     CU(cudaMemsetAsync(d.xn, 0, H.S * sizeof(float), c->stream));
     B.smem_br = (size_t)(kThreads / 32) * 32 * kStage * sizeof(double);
-    CU(cudaFuncSetAttribute(k_up_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
-    CU(cudaFuncSetAttribute(k_down_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
-    TRY(occupancy_grid((const void *)k_up_staged, kThreadsS, c->smem_staged, B.n_items, &B.grid_up));
-    TRY(occupancy_grid((const void *)k_up<MODE_BR>, kThreads, B.smem_br, B.n_items, &B.grid_up_br));
-    TRY(occupancy_grid((const void *)k_down_staged, kThreadsS, c->smem_staged, B.n_items, &B.grid_down));
+    const StagedConfig &cf = kConfigs[c->cfg];
+    CU(cudaFuncSetAttribute((const void *)cf.up, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
+    CU(cudaFuncSetAttribute((const void *)cf.down, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->smem_staged));
+    TRY(occupancy_grid((const void *)cf.up, c->threads, c->smem_staged, B.n_up, &B.grid_up));
+    TRY(occupancy_grid((const void *)k_up<MODE_BR>, kThreads, B.smem_br, B.n_up, &B.grid_up_br));
+    TRY(occupancy_grid((const void *)cf.down, c->threads, c->smem_staged, B.n_units, &B.grid_down));
     k_uniform<<<(unsigned)std::min<int64_t>((H.J + kThreads - 1) / kThreads, 65535), kThreads, 0, c->stream>>>(d,
                                                                                                              H.J);
     CU(cudaGetLastError());
@@ -658,8 +757,9 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
         int dev = 0, sms = 148;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaGetLastError();
-        opt.slots = std::max(1, sms);
-        opt.item_bytes = 96 * 1024;
+        const StagedConfig &cf = kConfigs[staged_config()];
+        opt.slots = std::max(1, sms) * cf.ctas_per_sm;
+        opt.item_bytes = cf.item_bytes;
     }
     try {
         rc = compile_forest(tv.data(), n, opt, &L, &err);
@@ -686,8 +786,12 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
     }
     c->G = L.G;
     c->Z = L.Z;
+    c->cfg = staged_config();
+    c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
-    c->smem_staged = 2 * (size_t)c->item_bytes + (size_t)(kThreadsS / 32) * 32 * kStage * sizeof(float);
+    // two unit buffers; a unit too large to stage uses its buffer as the
+    // payoff-product stage of the global-memory path
+    c->smem_staged = 2 * (size_t)c->item_bytes;
     if ((rc = dalloc(c, &c->err, 1))) return bail(rc);
     if (cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream) != cudaSuccess)
         return bail(set_err(CFR_ERR_CUDA, "memset"));
@@ -697,6 +801,8 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
         if ((rc = build_player(c, L, p))) return bail(rc);
     if ((rc = dalloc(c, &c->t_done, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->active, L.G))) return bail(rc);
+    if ((rc = dalloc(c, &c->par, L.G * (kParamSpan + 1)))) return bail(rc);
+    if ((rc = dalloc(c, &c->pbase, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->br[0], L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->br[1], L.G))) return bail(rc);
     int64_t smax = 0;
@@ -727,7 +833,9 @@ int check_err(cfr_ctx *c) {
     CU(cudaStreamSynchronize(c->stream));
     if (e) {
         c->poisoned = true;
-        return set_err(CFR_ERR_TIMEOUT, "a bounded device wait gave up (shared-memory staging did not complete)");
+        if (e == kErrParams)
+            return set_err(CFR_ERR_STATE, "internal: a pass ran outside its parameter table (context unusable)");
+        return set_err(CFR_ERR_TIMEOUT, "a bounded device wait gave up (a copy or a parent unit did not complete)");
     }
     return CFR_OK;
 }
@@ -751,7 +859,8 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = CFR_OK;
-            for (int k = 0; k < K && rc == CFR_OK; k++) rc = launch_iteration(c, variant, alpha, beta, gamma, alt);
+            for (int k = 0; k < K && rc == CFR_OK; k++)
+                rc = launch_iteration(c, variant, alpha, beta, gamma, alt, k % kParamSpan == 0);
             cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
@@ -768,7 +877,8 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
         }
         for (; done + K <= n; done += K) CU(cudaGraphLaunch(exec, c->stream));
     }
-    for (; done < n; done++) TRY(launch_iteration(c, variant, alpha, beta, gamma, alt));
+    for (int64_t k = 0; done < n; done++, k++)
+        TRY(launch_iteration(c, variant, alpha, beta, gamma, alt, k % kParamSpan == 0));
     return CFR_OK;
 }
 
@@ -1042,7 +1152,7 @@ int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha,
     double tot[4] = {0, 0, 0, 0};
     int rc = CFR_OK;
     for (int64_t i = 0; i < n && rc == CFR_OK; i++) {
-        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, ev);
+        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, i % kParamSpan == 0, ev);
         if (rc) break;
         cudaError_t e = cudaEventSynchronize(ev[4]);
         if (e != cudaSuccess) {

@@ -8,8 +8,8 @@
 // matrices A, B, C and the level graphs L^(d) of Sec. 3.1-3.2 are not stored
 // as matrices: each has at most one nonzero per column, so each becomes an
 // index array (inf_seq, seq_child, inf_par) over the breadth-first order.
-// Finally each player's levels are cut into work items that fit one
-// shared-memory buffer of the CUDA passes.
+// Finally each player's levels are cut into a tree of units that each fit
+// one shared-memory buffer of the CUDA passes.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -377,29 +377,32 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 B.m_val[q] = A.m_val[k];
             }
     }
-    // ---- work items: a cut level per game and player, subtrees below it packed
-    // into units that fit one shared-memory buffer -------------------------
+    // ---- units: per game and player, a tree of units, each of which fits one
+    // shared-memory buffer ----------------------------------------------------
     for (int p = 0; p < 2; p++) {
         PlayerLayout &P = L.pl[p];
         const auto &glv = glvs[p];
         const int64_t J = P.J;
-        // per-infoset subtree footprint (raw bytes, without per-level slack)
-        std::vector<int64_t> raw_up(J, 0);
+        // own footprint of each infoset (raw bytes, without per-level slack)
+        // and the footprint of its whole subtree
+        std::vector<int64_t> own(J, 0), raw_up(J, 0);
         for (int64_t j = J - 1; j >= 0; j--) {
             int64_t u = 8 + 8;   // infoset: segment pointer + ev
+            int64_t sub = 0;
             for (int32_t q = P.inf_seq[j]; q < P.inf_seq[j + 1]; q++) {
                 const int64_t nz = P.m_ptr[q + 1] - P.m_ptr[q];
-                u += 24 + 8 * nz;
-                for (int32_t c = P.seq_child[q]; c < P.seq_child[q + 1]; c++) u += raw_up[c];
+                u += 24 + 12 * nz;   // r, b, child and row pointers, V; payoff column, value, gathered x
+                for (int32_t c = P.seq_child[q]; c < P.seq_child[q + 1]; c++) sub += raw_up[c];
             }
-            raw_up[j] = u;
+            own[j] = u;
+            raw_up[j] = u + sub;
         }
         const int64_t slack_per_level = 8 * 48;
-        P.game_nitems.assign(G, 0);
-        P.game_cut.assign(G, 1);
-        P.trunks.resize(G);
-        P.items.clear();
+        std::vector<int64_t> f(J, 0);   // subtree footprint truncated at a tier's bottom
+        P.units.clear();
         P.ranges.clear();
+        P.game_root.assign(G, -1);
+        P.game_tiers.assign(G, 0);
         auto push_level = [&](int32_t j0, int32_t j1) {
             const int32_t s0 = P.inf_seq[j0], s1 = P.inf_seq[j1];
             P.ranges.push_back(j0);
@@ -409,99 +412,133 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             P.ranges.push_back(P.m_ptr[s0]);
             P.ranges.push_back(P.m_ptr[s1]);
         };
+        // footprints of the levels [0, below) truncated at `below` (the
+        // deepest level also stages one ev per child infoset)
+        auto truncated = [&](const std::vector<std::pair<int32_t, int32_t>> &lv, int32_t below) {
+            for (int32_t d = below - 1; d >= 0; d--)
+                for (int32_t j = lv[d].first; j < lv[d].second; j++) {
+                    int64_t u = own[j];
+                    if (d + 1 < below) {
+                        for (int32_t q = P.inf_seq[j]; q < P.inf_seq[j + 1]; q++)
+                            for (int32_t c = P.seq_child[q]; c < P.seq_child[q + 1]; c++) u += f[c];
+                    } else {
+                        u += 4 * (int64_t)(P.seq_child[P.inf_seq[j + 1]] - P.seq_child[P.inf_seq[j]]);
+                    }
+                    f[j] = u;
+                }
+        };
         for (int64_t g = 0; g < G; g++) {
             const auto &lv = glv[g];
-            const int32_t nl = (int32_t)lv.size();   // levels 0..nl-1
-            // item size: enough items for ~2 per resident CTA if this game were
+            const int32_t nl = (int32_t)lv.size();   // levels 0..nl-1; level 0 = the root pseudo-infoset
+            // unit size: enough units for ~2 per resident CTA if this game were
             // alone, within the buffer.  It depends on this game only, so a game
             // is cut into the same units alone and inside a batch.
             int64_t target = raw_up[g] / std::max<int64_t>(1, 2 * opt.slots);
             target = std::max(opt.min_item_bytes, std::min(target, opt.item_bytes));
-            // the shallowest cut whose subtrees all fit the item target with a
-            // trunk of at most trunk_max sequences; otherwise the cut with the
-            // smallest largest subtree among those with a small trunk
-            int32_t c = 1;
-            if (nl > 1) {
-                int64_t trunk = 0;
-                int32_t best = -1, fallback = 1;
-                int64_t fb_mx = INT64_MAX;
-                for (int32_t cc = 1; cc < nl; cc++) {
-                    trunk += P.inf_seq[lv[cc - 1].second] - P.inf_seq[lv[cc - 1].first];
-                    if (cc > 1 && trunk > opt.trunk_max) break;
+            // tiers, bottom up: each tier starts at the shallowest level whose
+            // subtrees, truncated at the tier below, fit the target
+            std::vector<int32_t> tops;
+            std::vector<std::vector<int64_t>> top_f;   // truncated footprints of each tier's top level
+            for (int32_t below = nl; below > 0;) {
+                truncated(lv, below);
+                int32_t c = -1;
+                for (int32_t d = 0; d < below && c < 0; d++) {
                     int64_t mx = 0;
-                    for (int32_t j = lv[cc].first; j < lv[cc].second; j++) mx = std::max(mx, raw_up[j]);
-                    const int64_t need = mx + slack_per_level * (nl - cc);
-                    if (need <= target && best < 0) best = cc;
-                    if (mx < fb_mx) {
-                        fb_mx = mx;
-                        fallback = cc;
-                    }
+                    for (int32_t j = lv[d].first; j < lv[d].second; j++) mx = std::max(mx, f[j]);
+                    if (mx + slack_per_level * (below - d) <= target) c = d;
                 }
-                c = best > 0 ? best : fallback;
+                if (c < 0) c = below - 1;   // a single level per tier; wider units run unstaged
+                tops.push_back(c);
+                top_f.emplace_back(f.begin() + lv[c].first, f.begin() + lv[c].second);
+                below = c;
             }
-            c = std::min(c, std::max(1, nl));
-            P.game_cut[g] = c;
-            P.trunks[g] = {(int32_t)g, 0, std::min(c, nl), (int32_t)P.ranges.size(), 0};
-            {
-                int64_t fu = 0;
-                for (int32_t d = 0; d < std::min(c, nl); d++) {
-                    push_level(lv[d].first, lv[d].second);
-                    const int32_t s0 = P.inf_seq[lv[d].first], s1 = P.inf_seq[lv[d].second];
-                    fu += up_level_bytes(s1 - s0, lv[d].second - lv[d].first, P.m_ptr[s1] - P.m_ptr[s0]);
-                }
-                if (std::min(c, nl) <= kMaxStagedLevels && fu <= opt.item_bytes) P.trunks[g].flags |= kStaged;
-            }
-            auto emit = [&](int32_t a, int32_t b) {
-                Item it{(int32_t)g, c, 0, (int32_t)P.ranges.size(), 0};
-                int32_t lo = a, hi = b;
-                int64_t fu = 0, fd = 0;
-                while (lo < hi) {
-                    push_level(lo, hi);
-                    const int32_t slo = P.inf_seq[lo], shi = P.inf_seq[hi];
-                    fu += up_level_bytes(shi - slo, hi - lo, P.m_ptr[shi] - P.m_ptr[slo]);
-                    fd += down_level_bytes(shi - slo, hi - lo);
-                    it.nlvl++;
-                    lo = P.seq_child[slo];
-                    hi = P.seq_child[shi];
-                }
-                if (it.nlvl <= kMaxStagedLevels && fu <= opt.item_bytes && fd <= opt.item_bytes) it.flags |= kStaged;
-                P.items.push_back(it);
-                P.game_nitems[g]++;
+            std::reverse(tops.begin(), tops.end());
+            std::reverse(top_f.begin(), top_f.end());
+            const int32_t m = (int32_t)tops.size();
+            P.game_tiers[g] = m;
+            // units, top down: each tier packs, per parent unit, the parent's
+            // child infosets at the tier's top level into consecutive groups
+            struct Span {
+                int32_t parent, a, b;
             };
-            if (c >= nl) {
-                emit(0, 0);   // nothing below the cut: an empty item still triggers the trunk
-            } else {
-                const int64_t cap = std::max<int64_t>(target - slack_per_level * (nl - c), 1);
-                int32_t a = lv[c].first;
-                int64_t acc = 0;
-                for (int32_t j = lv[c].first; j < lv[c].second; j++) {
-                    if (acc > 0 && acc + raw_up[j] > cap) {
-                        emit(a, j);
-                        a = j;
-                        acc = 0;
+            std::vector<Span> spans{{-1, lv[0].first, lv[0].second}}, next;
+            for (int32_t i = 0; i < m; i++) {
+                const int32_t top = tops[i], bot = (i + 1 < m) ? tops[i + 1] : nl;
+                const int64_t cap = std::max<int64_t>(target - slack_per_level * (bot - top), 1);
+                const std::vector<int64_t> &ft = top_f[i];
+                next.clear();
+                auto emit = [&](int32_t par, int32_t a, int32_t b) {
+                    Unit u{(int32_t)g, top, 0, (int32_t)P.ranges.size(), 0, par, 0, i};
+                    int32_t lo = a, hi = b;
+                    int64_t fu = 0, fd = 0;
+                    for (int32_t d = top; d < bot && lo < hi; d++) {
+                        push_level(lo, hi);
+                        const int32_t slo = P.inf_seq[lo], shi = P.inf_seq[hi];
+                        fu += up_level_bytes(shi - slo, hi - lo, P.m_ptr[shi] - P.m_ptr[slo]);
+                        fd += down_level_bytes(shi - slo, hi - lo);
+                        u.nlvl++;
+                        lo = P.seq_child[slo];
+                        hi = P.seq_child[shi];
                     }
-                    acc += raw_up[j];
+                    const int32_t id = (int32_t)P.units.size();
+                    if (lo < hi && top + u.nlvl == bot) {
+                        // the child units' top levels: staged ev of [lo, hi)
+                        u.flags |= kInternal;
+                        next.push_back({id, lo, hi});
+                        for (int32_t v : {lo, hi, 0, 0, 0, 0}) P.ranges.push_back(v);
+                        fu += span16(hi - lo, 4);
+                    }
+                    if (u.nlvl < kMaxStagedLevels && fu <= opt.item_bytes && fd <= opt.item_bytes)
+                        u.flags |= kStaged;
+                    if (par >= 0) {
+                        P.units[par].nchild++;
+                        if (P.units[par].parent < 0) u.flags |= kChildOfRoot;
+                    } else {
+                        P.game_root[g] = id;
+                    }
+                    P.units.push_back(u);
+                };
+                for (const Span &sp : spans) {
+                    int32_t a = sp.a;
+                    int64_t acc = 0;
+                    for (int32_t j = sp.a; j < sp.b; j++) {
+                        const int64_t fj = ft[j - lv[top].first];
+                        if (acc > 0 && acc + fj > cap) {
+                            emit(sp.parent, a, j);
+                            a = j;
+                            acc = 0;
+                        }
+                        acc += fj;
+                    }
+                    emit(sp.parent, a, sp.b);
                 }
-                emit(a, lv[c].second);
+                spans.swap(next);
             }
         }
-        // largest items first: a dynamic queue then finishes with small ones
-        std::vector<int64_t> isz(P.items.size());
-        for (size_t k = 0; k < P.items.size(); k++) {
-            const Item &it = P.items[k];
+        // queues: leaves largest first for the bottom-up passes (a dynamic
+        // queue then finishes with small units); every unit by tree depth for
+        // the top-down pass, so a unit's parent always comes first
+        const int64_t nu = (int64_t)P.units.size();
+        std::vector<int64_t> usz(nu);
+        for (int64_t k = 0; k < nu; k++) {
+            const Unit &u = P.units[k];
             int64_t s = 0;
-            for (int32_t d = 0; d < it.nlvl; d++)
-                s += P.ranges[it.rng + kLvl * d + 3] - P.ranges[it.rng + kLvl * d + 2] +
-                     P.ranges[it.rng + kLvl * d + 5] - P.ranges[it.rng + kLvl * d + 4];
-            isz[k] = s;
+            for (int32_t d = 0; d < u.nlvl; d++)
+                s += P.ranges[u.rng + kLvl * d + 3] - P.ranges[u.rng + kLvl * d + 2] +
+                     P.ranges[u.rng + kLvl * d + 5] - P.ranges[u.rng + kLvl * d + 4];
+            usz[k] = s;
         }
-        std::vector<size_t> ord(P.items.size());
-        std::iota(ord.begin(), ord.end(), 0);
-        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return isz[a] > isz[b]; });
-        std::vector<Item> sorted;
-        sorted.reserve(ord.size());
-        for (size_t k : ord) sorted.push_back(P.items[k]);
-        P.items.swap(sorted);
+        P.up_queue.clear();
+        P.down_queue.resize(nu);
+        std::iota(P.down_queue.begin(), P.down_queue.end(), 0);
+        for (int64_t k = 0; k < nu; k++)
+            if (P.units[k].nchild == 0) P.up_queue.push_back((int32_t)k);
+        std::stable_sort(P.up_queue.begin(), P.up_queue.end(),
+                         [&](int32_t a, int32_t b) { return usz[a] > usz[b]; });
+        std::stable_sort(P.down_queue.begin(), P.down_queue.end(), [&](int32_t a, int32_t b) {
+            if (P.units[a].depth != P.units[b].depth) return P.units[a].depth < P.units[b].depth;
+            return usz[a] > usz[b];
+        });
     }
     L.game_nnz.assign(G, 0);
     for (int64_t r = 0; r < L.pl[0].S; r++)

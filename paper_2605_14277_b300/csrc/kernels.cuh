@@ -2,21 +2,24 @@
 //
 // One player's half-step is two launches over the forest layout (layout.h):
 //
-//   up   : per work item (a group of subtrees below the game's cut level),
-//          deepest level first:
+//   up   : per unit (a range of subtrees, a few levels deep), deepest level
+//          first:
 //            - payoff product rows u = sign * M x_other          (Sec. 2.1, two-player utilities)
 //            - V[s] = u[s] + sum of the child infosets' ev       (Alg. 2: v += L w + L v; q = B^T(w+v))
 //            - ev_j = sum_a b_j[a] V[(j,a)]                       (C (b . q))
 //            - r += V - ev_j, variant post-op, next strategy     (Alg. 2 regret update; Alg. 3-5)
-//          The last CTA to finish an item of a game runs that game's trunk
-//          (levels above the cut) the same way, then the trunk's top-down
-//          pass into a staging vector xn.
-//   down : per work item, top-down: x[(j,a)] = x[p_j] b_j[a]    (Alg. 2: y += L^T y; x = A^T y)
+//          Leaf units come from a queue; the CTA that completes the last
+//          child of an internal unit runs that unit next, up to the game's
+//          root unit.
+//   down : per unit, top-down: x[(j,a)] = x[p_j] b_j[a]          (Alg. 2: y += L^T y; x = A^T y)
 //          and the average xbar += t^gamma x (for the x being replaced).
+//          Units come from a queue in unit-tree depth order; a unit starts
+//          its top level once its parent unit has published its x.
 //
-// No CTA ever waits for another CTA: completion is counted with one atomic
-// per item (threadfence-reduction pattern) and a game's trunk runs on
-// whichever CTA finishes that game's last item.  Cumulative regrets and
+// The bottom-up pass never waits for another CTA: completion is counted with
+// one atomic per unit (threadfence-reduction pattern).  In the top-down pass
+// a unit's parent always comes earlier in the queue, so the CTA holding it is
+// running; that wait is bounded in time all the same.  Cumulative regrets and
 // average sums are float-float pairs (Kahan-compensated FP32): B300's FP64
 // rate is far below its FP32 rate, so the hot path does no FP64 arithmetic.
 // The best-response pass (MODE_BR) runs in FP64.
@@ -40,27 +43,36 @@ struct DevPlayer {
     const int32_t *m_ptr, *m_col;
     const float *m_val;
     const double *m_val64;
-    const int4 *items, *trunks;     // {game, nlvl, rng, flags}; ranges: kLvl ints per level
-    const int32_t *ranges, *game_nitems, *item_first;
-    int32_t n_items, G;
+    const int4 *units;              // {game, nlvl, rng, flags}; ranges: kLvl ints per level
+    const int2 *unit_tree;          // {parent unit (-1: root), child units}
+    const int32_t *ranges, *up_queue, *down_queue, *game_root;
+    int32_t n_units, n_up, G;
     // state
     float2 *r;       // cumulative regret, float-float (hi, lo)
     float *b;        // behavioural strategy to be played next
     float *x;        // sequence-form strategy of the last NextStrategy
-    float *xn;       // trunk staging of the next x
+    float *xn;       // next x of each root unit's sequences (written by the up pass)
     float2 *xbar;    // weighted sum of played x, float-float
     // scratch
     float *u, *ev;
     double *u64, *ev64, *xnorm;
-    // work counters and the error word (nonzero: a bounded wait gave up)
-    int32_t *game_done, *work, *exits, *err;
+    // unit_cnt: children completed in the current bottom-up pass (reset by
+    // the CTA that completes the last one); unit_flag: epoch + 1 once a unit's
+    // top-down x is final; work / exits: queue head and exit count of the
+    // current launch (reset by the last CTA to exit, which also advances the
+    // epoch); err: nonzero once a bounded wait gave up
+    int32_t *unit_cnt, *unit_flag, *work, *exits, *epoch, *err;
 };
 
+struct ItemParams;
 struct DevGames {
     int32_t *t_done;        // completed iterations per game
     const uint8_t *active;  // 1 = advance this game
     double *br;             // best-response value per game (BR pass output)
+    ItemParams *par;        // [G][kParamSpan + 1] parameters of t = pbase[g] + k
+    int32_t *pbase;         // [G]
 };
+constexpr int kParamSpan = 64;   // iterations covered by one parameter table
 
 struct IterArgs {
     int variant;
@@ -108,7 +120,7 @@ __host__ __device__ __forceinline__ float2 ff_from_double(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// per-item parameters, computed once per item by thread 0
+// per-unit parameters (they depend on the game's iteration counter only)
 // ---------------------------------------------------------------------------
 struct ItemParams {
     float2 w;        // t^gamma
@@ -118,8 +130,8 @@ struct ItemParams {
     int32_t active;
 };
 
-__device__ __forceinline__ void item_params(const DevGames &gm, const IterArgs &ia, int g, ItemParams *ip) {
-    const int32_t t = gm.t_done[g] + (ia.first_of_iter ? 1 : 0);
+__device__ __forceinline__ void params_of_t(const DevGames &gm, const IterArgs &ia, int g, int32_t t,
+                                            ItemParams *ip) {
     const double td = (double)t;
     ip->t = t;
     ip->active = gm.active[g];
@@ -132,6 +144,23 @@ __device__ __forceinline__ void item_params(const DevGames &gm, const IterArgs &
         ip->fpos = make_float2(1.f, 0.f);
         ip->fneg = make_float2(1.f, 0.f);
     }
+}
+__device__ __forceinline__ void item_params(const DevGames &gm, const IterArgs &ia, int g, ItemParams *ip) {
+    params_of_t(gm, ia, g, gm.t_done[g] + (ia.first_of_iter ? 1 : 0), ip);
+}
+// The parameters of game g for this pass, from the table filled ahead of the
+// iterations (FP64 pow is slow on this part and costs registers: the table
+// keeps it out of the passes).  The host refreshes the table at least every
+// kParamSpan iterations; a t outside it sets the error word.
+constexpr int kErrParams = 2;
+__device__ __forceinline__ ItemParams unit_params(const DevGames &gm, const IterArgs &ia, int g, int32_t *err) {
+    const int32_t t = __ldcg(&gm.t_done[g]) + (ia.first_of_iter ? 1 : 0);
+    int32_t k = t - __ldcg(&gm.pbase[g]);
+    if (k < 0 || k > kParamSpan) {
+        atomicExch(err, kErrParams);
+        k = 0;
+    }
+    return gm.par[(int64_t)g * (kParamSpan + 1) + k];
 }
 
 // ---------------------------------------------------------------------------
@@ -245,8 +274,8 @@ __device__ void up_infoset_br(const DevPlayer &P, int j) {
     P.ev64[j] = best;
 }
 
-// Levels of one work unit bottom-up (deepest first), after its payoff rows,
-// straight from global memory (trunks, units too large to stage, and the
+// Levels of one unit bottom-up (deepest first), after its payoff rows,
+// straight from global memory (units too large to stage, and the
 // best-response pass).  rng: kLvl ints per level.
 template <int MODE>
 __device__ void run_up(const DevPlayer &P, const void *xo, const IterArgs &ia, const ItemParams &ip, int nlvl,

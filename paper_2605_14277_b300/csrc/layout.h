@@ -7,8 +7,9 @@
 // sequence.  Sequences are numbered in infoset order.  With that order:
 //   * the sequences of infoset j are [inf_seq[j], inf_seq[j+1])            (logic matrix C, Sec. 3.1)
 //   * the child infosets of sequence s are [seq_child[s], seq_child[s+1])  (level graphs L^(d), Sec. 3.2)
-//   * within one level, each game's infosets are contiguous, and so is each
-//     subtree below a cut level: a work item is one contiguous range per level.
+//   * within one level, each game's infosets are contiguous, and so are the
+//     descendants of any contiguous range: a unit of work is one contiguous
+//     range per level.
 #pragma once
 #include <cstdint>
 #ifndef __CUDACC__
@@ -30,17 +31,33 @@ struct TreeView {
     const double *payoff;
 };
 
-// one unit of work: levels [lvl0, lvl0 + nlvl) of one game.  Level k of the
-// unit is described by kLvl ints at ranges[rng + kLvl * k]:
+// One unit of work: levels [lvl0, lvl0 + nlvl) of one game below one
+// contiguous range of infosets at level lvl0.  Level k of the unit is
+// described by kLvl ints at ranges[rng + kLvl * k]:
 //   infosets [j0, j1), sequences [s0, s1), payoff nonzeros [n0, n1)
 // (rows s0..s1 of this player's payoff CSR), so a kernel can issue every copy
 // of the unit without first reading index arrays.
+//
+// The units of a game form a tree.  A unit's parent is the unit whose deepest
+// level holds the parent sequences of this unit's top-level infosets; the
+// game's root unit starts at level 0.  A unit with children ("internal") finds
+// the child infosets of its deepest level at the top levels of its child
+// units.  Bottom-up passes take the leaves from a queue and run each internal
+// unit on the CTA that completes its last child; top-down passes take every
+// unit in tree-depth order and start a unit once its parent is done.
 constexpr int kLvl = 6;
-struct Item {
+struct Unit {
     int32_t game, lvl0, nlvl, rng;
-    int32_t flags;   // kStaged: the unit fits a shared-memory buffer
+    int32_t flags;    // kStaged | kInternal
+    int32_t parent;   // -1: the game's root unit
+    int32_t nchild;   // child units
+    int32_t depth;    // in the unit tree (root = 0)
 };
-constexpr int kStaged = 1;
+constexpr int kStaged = 1;       // the unit fits one shared-memory buffer in both passes
+constexpr int kInternal = 2;     // the deepest level's child infosets are other units' top levels;
+                                 // their range [c0, c1) follows the unit's levels as one more
+                                 // kLvl record {c0, c1, 0, 0, 0, 0}
+constexpr int kChildOfRoot = 4;  // the parent is the game's root unit
 constexpr int kMaxStagedLevels = 24;
 
 // Shared-memory bytes a staged unit level needs (host and device agree on
@@ -49,9 +66,10 @@ __host__ __device__ inline int64_t span16(int64_t n, int e) { return (n * e + 32
 __host__ __device__ inline int64_t work16(int64_t n, int e) { return (n * e + 15) / 16 * 16; }
 __host__ __device__ inline int64_t up_level_bytes(int64_t ns, int64_t ni, int64_t nz) {
     // r (float2), b, seq_child, payoff row pointers, infoset segments, payoff
-    // columns, payoff values; work: V per sequence, ev per infoset
+    // columns, payoff values; work: the gathered x of the other player per
+    // payoff entry, V per sequence, ev per infoset
     return span16(ns, 8) + span16(ns, 4) + 2 * span16(ns + 1, 4) + span16(ni + 1, 4) + 2 * span16(nz, 4) +
-           work16(ns, 4) + work16(ni, 4);
+           work16(nz, 4) + work16(ns, 4) + work16(ni, 4);
 }
 __host__ __device__ inline int64_t down_level_bytes(int64_t ns, int64_t ni) {
     // b, x, xbar (float2), infoset parents, infoset segments
@@ -69,11 +87,12 @@ struct PlayerLayout {
     std::vector<int32_t> m_col;         // [Z]     other player's sequence
     std::vector<float> m_val;           // [Z]     sum over terminals of chance reach * u1
     std::vector<double> m_val64;        // [Z]
-    std::vector<Item> items;            // bulk work items (levels >= cut)
-    std::vector<Item> trunks;           // per game: levels [0, cut)
-    std::vector<int32_t> ranges;        // kLvl ints per level of every item and trunk
-    std::vector<int32_t> game_nitems;   // [G]
-    std::vector<int32_t> game_cut;      // [G]
+    std::vector<Unit> units;            // every unit of every game
+    std::vector<int32_t> ranges;        // kLvl ints per level of every unit
+    std::vector<int32_t> up_queue;      // leaf units, largest first
+    std::vector<int32_t> down_queue;    // all units by tree depth, then largest first
+    std::vector<int32_t> game_root;     // [G] root unit of each game
+    std::vector<int32_t> game_tiers;    // [G] depth of the game's unit tree + 1
     // caller order: game g's caller infoset k is ext_inf[game_jbase[g] + k]; its
     // sequences start at caller index ext_seq0[game_jbase[g] + k]
     std::vector<int32_t> ext_inf, ext_seq0;
@@ -91,10 +110,9 @@ struct Layout {
 };
 
 struct CompileOptions {
-    int64_t item_bytes = 96 * 1024;    // shared-memory buffer of one staged work item
-    int64_t min_item_bytes = 8 * 1024; // smallest item the packer aims for
-    int64_t slots = 148;               // CTAs resident at once (items are sized to give each ~2)
-    int64_t trunk_max = 8192;          // most sequences a trunk may hold when a deeper cut is possible
+    int64_t item_bytes = 48 * 1024;    // shared-memory buffer of one staged unit
+    int64_t min_item_bytes = 8 * 1024; // smallest unit the packer aims for
+    int64_t slots = 296;               // CTAs resident at once (units are sized to give each ~2)
 };
 
 // status codes shared with the C ABI

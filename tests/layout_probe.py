@@ -56,7 +56,7 @@ class Layout:
         for p in (0, 1):
             d = {}
             for name in ("inf_seq", "seq_child", "inf_par", "seq_game", "m_ptr", "m_col", "ranges",
-                         "game_nitems", "ext_inf", "ext_seq0", "items", "trunks"):
+                         "up_queue", "down_queue", "game_root", "game_tiers", "ext_inf", "ext_seq0", "units"):
                 m = L.probe_i32(h, p, name.encode(), None)
                 a = np.zeros(m, np.int32)
                 L.probe_i32(h, p, name.encode(), a.ctypes.data)
@@ -70,8 +70,7 @@ class Layout:
                 a = np.zeros(m, np.int64)
                 L.probe_i64(h, p, name.encode(), a.ctypes.data)
                 d[name] = a
-            d["items"] = d["items"].reshape(-1, 5)
-            d["trunks"] = d["trunks"].reshape(-1, 5)
+            d["units"] = d["units"].reshape(-1, 8)   # game, lvl0, nlvl, rng, flags, parent, nchild, depth
             self.pl[p] = d
 
     def __del__(self):
@@ -105,7 +104,7 @@ def work16(n, e):
 def up_bytes(ns, ni, nz):
     """shared-memory bytes of one staged level of the up pass (layout.h)"""
     return (span16(ns, 8) + span16(ns, 4) + 2 * span16(ns + 1, 4) + span16(ni + 1, 4) + 2 * span16(nz, 4)
-            + work16(ns, 4) + work16(ni, 4))
+            + work16(nz, 4) + work16(ns, 4) + work16(ni, 4))
 
 
 def down_bytes(ns, ni):

@@ -49,17 +49,21 @@ int64_t probe_i32(void *h, int p, const char *name, void *out) {
     if (s == "m_ptr") return copy_out(P.m_ptr, out);
     if (s == "m_col") return copy_out(P.m_col, out);
     if (s == "ranges") return copy_out(P.ranges, out);
-    if (s == "game_nitems") return copy_out(P.game_nitems, out);
+    if (s == "up_queue") return copy_out(P.up_queue, out);
+    if (s == "down_queue") return copy_out(P.down_queue, out);
+    if (s == "game_root") return copy_out(P.game_root, out);
+    if (s == "game_tiers") return copy_out(P.game_tiers, out);
     if (s == "ext_inf") return copy_out(P.ext_inf, out);
     if (s == "ext_seq0") return copy_out(P.ext_seq0, out);
-    if (s == "items" || s == "trunks") {
-        const std::vector<Item> &v = s == "items" ? P.items : P.trunks;
+    if (s == "units") {
+        const std::vector<Unit> &v = P.units;
         if (out)
             for (size_t k = 0; k < v.size(); k++) {
-                int32_t *o = (int32_t *)out + 5 * k;
-                o[0] = v[k].game; o[1] = v[k].lvl0; o[2] = v[k].nlvl; o[3] = v[k].rng; o[4] = v[k].flags;
+                int32_t *o = (int32_t *)out + 8 * k;
+                o[0] = v[k].game; o[1] = v[k].lvl0; o[2] = v[k].nlvl; o[3] = v[k].rng;
+                o[4] = v[k].flags; o[5] = v[k].parent; o[6] = v[k].nchild; o[7] = v[k].depth;
             }
-        return (int64_t)v.size() * 5;
+        return (int64_t)v.size() * 8;
     }
     return -1;
 }

@@ -1,6 +1,7 @@
 """Host game compiler: layout invariants and an FP64 replay of the kernels'
-schedule (units deepest level first, then each game's trunk, then top-down)
-over the compiled index arrays, checked against the oracle.  CPU only."""
+schedule (leaf units from the queue deepest level first, each internal unit
+once its last child is done; then every unit top-down in queue order) over
+the compiled index arrays, checked against the oracle.  CPU only."""
 import numpy as np
 import pytest
 
@@ -27,35 +28,67 @@ def check_invariants(lay, G_):
         for j in range(G_, J):
             q = inf_par[j]
             assert seq_child[q] <= j < seq_child[q + 1]
-        # every infoset covered exactly once by trunks + items
+        # every infoset covered exactly once by the units
         cover = np.zeros(J, np.int64)
         rng = d["ranges"]
+        units = d["units"]
         unit_of = {}
-        for kind, units in (("trunk", d["trunks"]), ("item", d["items"])):
-            for ui, (g, lvl0, nlvl, r0, flags) in enumerate(units):
-                prev = None
-                for k in range(nlvl):
-                    lo, hi, s0, s1, n0, n1 = rng[r0 + 6 * k: r0 + 6 * k + 6]
-                    assert s0 == inf_seq[lo] and s1 == inf_seq[hi]
-                    assert n0 == d["m_ptr"][s0] and n1 == d["m_ptr"][s1]
-                    cover[lo:hi] += 1
-                    for j in range(lo, hi):
-                        unit_of[j] = (kind, ui, k)
-                    if prev is not None and hi > lo:
-                        ps = inf_par[lo:hi]
-                        assert (ps >= inf_seq[prev[0]]).all() and (ps < inf_seq[prev[1]]).all()
-                    prev = (lo, hi)
+        for ui, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(units):
+            assert nlvl >= 1
+            prev = None
+            for k in range(nlvl):
+                lo, hi, s0, s1, n0, n1 = rng[r0 + 6 * k: r0 + 6 * k + 6]
+                assert hi > lo
+                assert s0 == inf_seq[lo] and s1 == inf_seq[hi]
+                assert n0 == d["m_ptr"][s0] and n1 == d["m_ptr"][s1]
+                cover[lo:hi] += 1
+                for j in range(lo, hi):
+                    unit_of[j] = (ui, k)
+                if prev is not None:
+                    # level k holds exactly the children of level k-1
+                    assert lo == seq_child[inf_seq[prev[0]]] and hi == seq_child[inf_seq[prev[1]]]
+                prev = (lo, hi)
         assert (cover == 1).all()
-        # an item's top level hangs below trunk sequences of the same game
-        for ui, (g, lvl0, nlvl, r0, flags) in enumerate(d["items"]):
-            if nlvl == 0:
-                continue
+        # tree structure: a unit's top level hangs below its parent's deepest
+        # level; roots are level 0; child counts and depths agree
+        nchild = np.zeros(len(units), np.int64)
+        for ui, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(units):
             lo, hi = rng[r0], rng[r0 + 1]
+            if par < 0:
+                assert lvl0 == 0 and depth == 0 and d["game_root"][g] == ui and hi - lo == 1
+                continue
+            nchild[par] += 1
+            pg, plvl0, pnlvl = units[par][0], units[par][1], units[par][2]
+            assert pg == g and plvl0 + pnlvl == lvl0 and units[par][7] + 1 == depth
+            assert units[par][4] & 2
             for j in range(lo, hi):
-                pj = inf_par[j]
-                pinf = np.searchsorted(inf_seq, pj, side="right") - 1
-                assert unit_of[pinf][0] == "trunk" and d["trunks"][unit_of[pinf][1]][0] == g
-        assert np.bincount(d["items"][:, 0], minlength=G_).tolist() == d["game_nitems"].tolist()
+                pinf = np.searchsorted(inf_seq, inf_par[j], side="right") - 1
+                assert unit_of[pinf] == (par, pnlvl - 1)
+        assert nchild.tolist() == units[:, 6].tolist()
+        # internal units have children; their deepest level's children are
+        # exactly the children units' top levels, and that range follows the
+        # unit's levels as one more record
+        for ui, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(units):
+            lo, hi = rng[r0 + 6 * (nlvl - 1)], rng[r0 + 6 * (nlvl - 1) + 1]
+            c0, c1 = seq_child[inf_seq[lo]], seq_child[inf_seq[hi]]
+            assert bool(flags & 2) == (nch > 0) == (c1 > c0)
+            if flags & 2:
+                assert rng[r0 + 6 * nlvl: r0 + 6 * nlvl + 6].tolist() == [c0, c1, 0, 0, 0, 0]
+                kids = [v for v in range(len(units)) if units[v][5] == ui]
+                assert min(rng[units[v][3]] for v in kids) == c0
+                assert max(rng[units[v][3] + 1] for v in kids) == c1
+            # below-the-root flag
+            assert bool(flags & 4) == (par >= 0 and units[par][5] < 0)
+        # queues: leaves for the bottom-up pass; all units, parents first, for
+        # the top-down pass
+        assert sorted(d["up_queue"].tolist()) == [u for u in range(len(units)) if units[u][6] == 0]
+        assert sorted(d["down_queue"].tolist()) == list(range(len(units)))
+        pos = np.empty(len(units), np.int64)
+        pos[d["down_queue"]] = np.arange(len(units))
+        for ui in range(len(units)):
+            if units[ui][5] >= 0:
+                assert pos[units[ui][5]] < pos[ui]
+        assert (np.diff(units[d["down_queue"], 7]) >= 0).all()
 
 
 @pytest.mark.parametrize("item_bytes", [0, 600, 4000])
@@ -74,19 +107,29 @@ def test_staged_units_fit_their_buffer():
         for p in (0, 1):
             d = lay.pl[p]
             n_staged = 0
-            for (g, lvl0, nlvl, r0, flags) in d["items"]:
+            for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["units"]:
                 rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
                 fu = sum(up_bytes(s1 - s0, j1 - j0, n1 - n0) for j0, j1, s0, s1, n0, n1 in rng)
                 fd = sum(down_bytes(s1 - s0, j1 - j0) for j0, j1, s0, s1, n0, n1 in rng)
+                if flags & 2:
+                    c0, c1 = d["ranges"][r0 + 6 * nlvl: r0 + 6 * nlvl + 2]
+                    fu += 16 * ((4 * (c1 - c0) + 32 + 15) // 16)
                 if flags & 1:
                     n_staged += 1
                     assert fu <= item_bytes and fd <= item_bytes and nlvl <= 24
             assert n_staged > 0
-            for (g, lvl0, nlvl, r0, flags) in d["trunks"]:
-                rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
-                fu = sum(up_bytes(s1 - s0, j1 - j0, n1 - n0) for j0, j1, s0, s1, n0, n1 in rng)
-                if flags & 1:
-                    assert fu <= item_bytes and nlvl <= 24
+
+
+def test_deep_games_get_several_tiers():
+    """a game far larger than one unit is cut into a tree several tiers deep,
+    with every unit staged"""
+    t = G.random_game(11, depth=9, chance={0: 4, 4: 3}, actions=(3, 4), payoff="normal")
+    lay = Layout([t], item_bytes=3000)
+    for p in (0, 1):
+        d = lay.pl[p]
+        assert d["game_tiers"][0] >= 3
+        assert d["units"][:, 7].max() + 1 == d["game_tiers"][0]
+        assert (d["units"][:, 4] & 1).all()
 
 
 def test_payoff_matrix_matches_sequence_form():
@@ -153,42 +196,43 @@ class Sim:
             q = np.maximum(q, 0)
             b[s0:s1] = q / q.sum() if q.sum() > 0 else 1.0 / (s1 - s0)
 
-        def run(unit):
-            g, lvl0, nlvl, r0, flags = unit
+        units = d["units"]
+
+        def run(ui):
+            g, lvl0, nlvl, r0 = units[ui][:4]
             for k in range(nlvl - 1, -1, -1):
                 for j in range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]):
                     step(j, t[g])
 
-        for it in d["items"]:
-            run(it)
-        xn = np.zeros_like(st[p]["x"])
-        for g in range(self.G):
-            tr = d["trunks"][g]
-            run(tr)
-            xn[g] = 1.0
-            for k in range(1, tr[2]):
-                for j in range(rng[tr[3] + 6 * k], rng[tr[3] + 6 * k + 1]):
-                    for s in range(inf_seq[j], inf_seq[j + 1]):
-                        xn[s] = xn[d["inf_par"][j]] * b[s]
-        st[p]["xn"] = xn
+        # leaves in queue order; an internal unit runs when its last child is done
+        done = np.zeros(len(units), np.int64)
+        for ui in d["up_queue"]:
+            run(ui)
+            v = ui
+            while units[v][5] >= 0:
+                par = units[v][5]
+                done[par] += 1
+                if done[par] < units[par][6]:
+                    break
+                run(par)
+                v = par
 
     def down(self, p, st, w):
         d = self.lay.pl[p]
         inf_seq, rng, inf_par = d["inf_seq"], d["ranges"], d["inf_par"]
-        x, xn, xbar, b = st[p]["x"], st[p]["xn"], st[p]["xbar"], st[p]["b"]
-        for g in range(self.G):
-            tr = d["trunks"][g]
-            for k in range(tr[2]):
-                for s in range(inf_seq[rng[tr[3] + 6 * k]], inf_seq[rng[tr[3] + 6 * k + 1]]):
-                    xbar[s] += w[g] * x[s]
-                    x[s] = xn[s]
-        for (g, lvl0, nlvl, r0, flags) in d["items"]:
+        x, xbar, b = st[p]["x"], st[p]["xbar"], st[p]["b"]
+        units = d["units"]
+        finished = np.zeros(len(units), bool)
+        for ui in d["down_queue"]:
+            g, lvl0, nlvl, r0, flags, par = units[ui][:6]
+            assert par < 0 or finished[par]
             for k in range(nlvl):
-                src = xn if k == 0 else x
                 for j in range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]):
+                    xp = 1.0 if inf_par[j] < 0 else x[inf_par[j]]
                     for s in range(inf_seq[j], inf_seq[j + 1]):
                         xbar[s] += w[g] * x[s]
-                        x[s] = src[inf_par[j]] * b[s]
+                        x[s] = xp * b[s]
+            finished[ui] = True
 
     def iteration(self, st, variant, alpha, beta, gamma, alternating, t_done):
         t = t_done + 1.0
