@@ -42,24 +42,17 @@ __device__ __forceinline__ void launch_exit(const DevPlayer &P) {
     }
 }
 
-// Bottom-up completion: unit v of the current game is done.  Returns the
-// parent unit if this CTA completed the parent's last child (the caller runs
-// it next), else -1; -2 when v is the game's root.
-__device__ __forceinline__ int climb(const DevPlayer &P, int v, int *s_last) {
-    const int par = P.unit_tree[v].x;
-    if (par < 0) return -2;
+// Bottom-up completion of unit u (every thread of the CTA, after its
+// results are written): count it at its parent.
+__device__ __forceinline__ void unit_done(const DevPlayer &P, int u) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const int prev = atomicAdd(&P.unit_cnt[par], 1);
-        const int last = (prev == P.unit_tree[par].y - 1);
-        if (last) P.unit_cnt[par] = 0;
-        *s_last = last;
+        const int par = P.unit_tree[u].x;
+        if (par >= 0) {
+            __threadfence();
+            atomicAdd(&P.unit_cnt[par], 1);
+        }
     }
-    __syncthreads();
-    if (!*s_last) return -1;
-    __threadfence();
-    return par;
 }
 
 // the root unit's next x, top-down from global memory, into xn (level 0's
@@ -94,141 +87,142 @@ __global__ void k_params(DevGames gm, IterArgs ia, int G) {
     }
 }
 
-// Best-response pass (MODE_BR, FP64) over every unit from global memory:
-// leaves from the queue, each internal unit on the CTA completing its last
-// child; the root's ev is the game's best-response value.
+// Best-response pass (MODE_BR, FP64) over every unit from global memory, in
+// bottom-up queue order: an internal unit waits (bounded) until its children
+// are done; the root's ev is the game's best-response value.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const void *xo, IterArgs ia) {
     extern __shared__ __align__(128) unsigned char smem[];
     void *stage = smem;
-    __shared__ int s_item, s_last;
+    __shared__ int s_item, s_err;
     __shared__ ItemParams s_ip;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(P.work, 1);
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(P.work, 1);
+            s_err = 0;
+        }
         __syncthreads();
         const int it = s_item;
-        __syncthreads();
         if (it >= P.n_up) break;
-        int u = P.up_queue[it];
-        const int g = P.units[u].x;
-        if (threadIdx.x == 0) item_params(gm, ia, g, &s_ip);
+        const int u = P.up_queue[it];
+        const int4 d = P.units[u];
+        const int2 tr = P.unit_tree[u];
+        if (threadIdx.x == 0) {
+            item_params(gm, ia, d.x, &s_ip);
+            if (s_ip.active && tr.y > 0) {
+                if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) s_err = 1;
+                P.unit_cnt[u] = 0;
+                __threadfence();
+            }
+        }
         __syncthreads();
         const ItemParams ip = s_ip;
+        if (s_err) break;
         if (!ip.active) continue;
-        for (;;) {
-            const int4 d = P.units[u];
-            run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage);
-            const int par = climb(P, u, &s_last);
-            if (par == -2) {
-                if (threadIdx.x == 0 && MODE == MODE_BR) gm.br[g] = __ldcg(&P.ev64[g]);
-                break;
-            }
-            if (par < 0) break;
-            u = par;
-        }
+        run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage);
+        unit_done(P, u);
+        if (threadIdx.x == 0 && tr.x < 0 && MODE == MODE_BR) gm.br[d.x] = __ldcg(&P.ev64[d.x]);
     }
     launch_exit(P);
 }
 
 // Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
-// Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take leaf
-// units from a queue.  Warp 0 is the producer: while warps 1.. compute the
-// current unit out of shared memory, it fetches the next unit, loads its
-// parameters and starts its bulk copies into the other buffer.  The CTA
-// completing the last child of an internal unit runs that unit next, in the
-// buffer just released; the game's root unit also publishes its next x (xn).
+// Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take units
+// from the bottom-up queue: every leaf, then the internal units deepest first.
+// Warp 0 is the producer: while warps 1.. compute the current unit out of
+// shared memory, it fetches the next unit, loads its parameters and starts its
+// bulk copies into the other buffer.  An internal unit's own arrays are
+// staged at once; its children's ev is copied in when its completion count
+// shows all children done (a bounded wait: the children were taken earlier by
+// running CTAs and never wait themselves).  The game's root unit also
+// publishes its next x (xn).
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *bufs[2] = {smem, smem + item_bytes};
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[2];    // a buffer's own arrays
+    __shared__ __align__(8) uint64_t cbar[2];   // an internal unit's child ev
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ UpTab tab[2][kMaxStagedLevels];
     __shared__ ChildEv cev[2];
-    __shared__ int s_cur, s_nxt, s_last, s_err;
+    __shared__ int s_cur, s_nxt, s_err;
     __shared__ ItemParams s_ip[2];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_up;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&cbar[0], 1);
+        mbar_init(&cbar[1], 1);
         fence_mbar_init();
         s_cur = atomicAdd(P.work, 1);
         s_err = 0;
     }
     __syncthreads();
-    uint32_t ph[2] = {0u, 0u};
-    auto stage = [&](const int4 h, int b) { issue_up(P, h, bufs[b], &bar[b], lv[b], tab[b], &cev[b]); };
+    uint32_t ph[2] = {0u, 0u}, cph[2] = {0u, 0u};
     int cur = s_cur, buf = 0;
     if (warp == 0) {
         if (cur < n) {
             const int4 h = P.units[P.up_queue[cur]];
             if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x, P.err);
-            if (h.w & kStaged) stage(h, 0);
+            if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0], &cev[0]);
         }
         if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
     }
     __syncthreads();
-    int ahead = s_nxt;   // next queue entry, not yet issued
+    int nxt = s_nxt;
     while (cur < n) {
-        // a unit from the queue, then every parent whose last child it completes
-        int u = P.up_queue[cur];
-        bool from_queue = true;
-        int pend = n;    // queue entry staged in the other buffer
-        for (;;) {
-            const int4 h = P.units[u];
-            const bool staged = (h.w & kStaged) != 0;
-            if (staged) {
-                if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
-                ph[buf] ^= 1u;
+        const int u = P.up_queue[cur];
+        const int4 h = P.units[u];
+        const int2 tr = P.unit_tree[u];
+        const bool staged = (h.w & kStaged) != 0, internal = tr.y > 0, root = tr.x < 0;
+        if (staged) {
+            if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+            ph[buf] ^= 1u;
+        }
+        __syncthreads();
+        if (s_err) break;
+        const ItemParams ip = s_ip[buf];
+        if (warp == 0) {
+            // producer: the next unit's parameters and copies into the other
+            // buffer, then the unit after it from the queue
+            if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
+            if (nxt < n) {
+                const int4 hn = P.units[P.up_queue[nxt]];
+                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
+                if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1], &cev[buf ^ 1]);
             }
-            __syncthreads();
-            if (s_err) {
-                cur = n;
-                break;
-            }
-            const ItemParams ip = s_ip[buf];   // a parent belongs to the same game
-            const bool root = P.unit_tree[u].x < 0;
-            if (warp == 0) {
-                // producer: the next queue entry's parameters and copies into
-                // the other buffer, then the entry after it
-                if (from_queue) {
-                    if (tid == 0) s_nxt = ahead < n ? atomicAdd(P.work, 1) : n;
-                    if (ahead < n) {
-                        const int4 hn = P.units[P.up_queue[ahead]];
-                        if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
-                        if (hn.w & kStaged) stage(hn, buf ^ 1);
-                    }
+        } else if (ip.active) {
+            if (internal) {
+                // all children done, then their ev
+                if (tid == 32) {
+                    if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) s_err = 1;
+                    P.unit_cnt[u] = 0;
+                    if (staged) issue_child_ev(cev[buf], &cbar[buf]);
                 }
-            } else if (ip.active && staged) {
-                compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], &cev[buf], (h.w & kInternal) != 0, root);
+                consumer_sync();
+                if (staged && !s_err) {
+                    if (!mbar_wait(&cbar[buf], cph[buf], P.err)) s_err = 1;
+                }
+                if (staged) cph[buf] ^= 1u;
+                consumer_sync();
             }
-            __syncthreads();
-            if (from_queue) {
-                pend = ahead;
-                ahead = s_nxt;
-            }
-            if (!ip.active) break;
+            if (staged && !s_err) compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], &cev[buf], internal, root);
+        }
+        __syncthreads();
+        if (s_err) break;
+        const int nxt2 = s_nxt;
+        if (ip.active) {
             if (!staged) {
                 run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
                 if (root) root_topdown_global(P, h.y, P.ranges + h.z);
             }
-            const int par = climb(P, u, &s_last);
-            if (par == -2) {
-                if (tid == 0 && ia.first_of_iter) gm.t_done[h.x] = ip.t;
-                break;
-            }
-            if (par < 0) break;
-            // this CTA completed the parent's last child: the parent next, in
-            // the buffer just released
-            u = par;
-            from_queue = false;
-            const int4 hp = P.units[u];
-            if ((hp.w & kStaged) && warp == 0) stage(hp, buf);
+            unit_done(P, u);
+            if (tid == 0 && root && ia.first_of_iter) gm.t_done[h.x] = ip.t;
         }
-        if (cur >= n) break;
-        cur = pend;
+        cur = nxt;
+        nxt = nxt2;
         buf ^= 1;
     }
     launch_exit(P);
@@ -760,6 +754,8 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
         const StagedConfig &cf = kConfigs[staged_config()];
         opt.slots = std::max(1, sms) * cf.ctas_per_sm;
         opt.item_bytes = cf.item_bytes;
+        if (const char *e = std::getenv("CFR_B300_INTERNAL_DIV")) opt.internal_div = std::max(1, std::atoi(e));
+        if (const char *e = std::getenv("CFR_B300_LEAF_ORDER")) opt.leaf_order = std::atoi(e);
     }
     try {
         rc = compile_forest(tv.data(), n, opt, &L, &err);

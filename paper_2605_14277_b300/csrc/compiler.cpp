@@ -441,11 +441,13 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             std::vector<std::vector<int64_t>> top_f;   // truncated footprints of each tier's top level
             for (int32_t below = nl; below > 0;) {
                 truncated(lv, below);
+                const int64_t tier_target =
+                    below == nl ? target : std::max<int64_t>(1024, target / std::max<int64_t>(1, opt.internal_div));
                 int32_t c = -1;
                 for (int32_t d = 0; d < below && c < 0; d++) {
                     int64_t mx = 0;
                     for (int32_t j = lv[d].first; j < lv[d].second; j++) mx = std::max(mx, f[j]);
-                    if (mx + slack_per_level * (below - d) <= target) c = d;
+                    if (mx + slack_per_level * (below - d) <= tier_target) c = d;
                 }
                 if (c < 0) c = below - 1;   // a single level per tier; wider units run unstaged
                 tops.push_back(c);
@@ -464,7 +466,9 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             std::vector<Span> spans{{-1, lv[0].first, lv[0].second}}, next;
             for (int32_t i = 0; i < m; i++) {
                 const int32_t top = tops[i], bot = (i + 1 < m) ? tops[i + 1] : nl;
-                const int64_t cap = std::max<int64_t>(target - slack_per_level * (bot - top), 1);
+                const int64_t tier_target =
+                    bot == nl ? target : std::max<int64_t>(1024, target / std::max<int64_t>(1, opt.internal_div));
+                const int64_t cap = std::max<int64_t>(tier_target - slack_per_level * (bot - top), 1);
                 const std::vector<int64_t> &ft = top_f[i];
                 next.clear();
                 auto emit = [&](int32_t par, int32_t a, int32_t b) {
@@ -528,13 +532,22 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                      P.ranges[u.rng + kLvl * d + 5] - P.ranges[u.rng + kLvl * d + 4];
             usz[k] = s;
         }
+        // bottom-up queue: every leaf, largest first, then the internal units
+        // deepest first, so a unit is always taken after all its children
         P.up_queue.clear();
         P.down_queue.resize(nu);
         std::iota(P.down_queue.begin(), P.down_queue.end(), 0);
+        std::vector<int32_t> internal;
         for (int64_t k = 0; k < nu; k++)
-            if (P.units[k].nchild == 0) P.up_queue.push_back((int32_t)k);
-        std::stable_sort(P.up_queue.begin(), P.up_queue.end(),
-                         [&](int32_t a, int32_t b) { return usz[a] > usz[b]; });
+            (P.units[k].nchild == 0 ? P.up_queue : internal).push_back((int32_t)k);
+        if (opt.leaf_order == 0)
+            std::stable_sort(P.up_queue.begin(), P.up_queue.end(),
+                             [&](int32_t a, int32_t b) { return usz[a] > usz[b]; });
+        std::stable_sort(internal.begin(), internal.end(), [&](int32_t a, int32_t b) {
+            if (P.units[a].depth != P.units[b].depth) return P.units[a].depth > P.units[b].depth;
+            return usz[a] > usz[b];
+        });
+        P.up_queue.insert(P.up_queue.end(), internal.begin(), internal.end());
         std::stable_sort(P.down_queue.begin(), P.down_queue.end(), [&](int32_t a, int32_t b) {
             if (P.units[a].depth != P.units[b].depth) return P.units[a].depth < P.units[b].depth;
             return usz[a] > usz[b];

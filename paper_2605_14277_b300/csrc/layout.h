@@ -42,9 +42,10 @@ struct TreeView {
 // level holds the parent sequences of this unit's top-level infosets; the
 // game's root unit starts at level 0.  A unit with children ("internal") finds
 // the child infosets of its deepest level at the top levels of its child
-// units.  Bottom-up passes take the leaves from a queue and run each internal
-// unit on the CTA that completes its last child; top-down passes take every
-// unit in tree-depth order and start a unit once its parent is done.
+// units.  Bottom-up passes take every leaf, then the internal units deepest
+// first, from one queue; an internal unit stages its own arrays at once and
+// starts computing when all its children are done.  Top-down passes take
+// every unit in tree-depth order and start a unit once its parent is done.
 constexpr int kLvl = 6;
 struct Unit {
     int32_t game, lvl0, nlvl, rng;
@@ -89,7 +90,7 @@ struct PlayerLayout {
     std::vector<double> m_val64;        // [Z]
     std::vector<Unit> units;            // every unit of every game
     std::vector<int32_t> ranges;        // kLvl ints per level of every unit
-    std::vector<int32_t> up_queue;      // leaf units, largest first
+    std::vector<int32_t> up_queue;      // leaves largest first, then internal units deepest first
     std::vector<int32_t> down_queue;    // all units by tree depth, then largest first
     std::vector<int32_t> game_root;     // [G] root unit of each game
     std::vector<int32_t> game_tiers;    // [G] depth of the game's unit tree + 1
@@ -113,6 +114,8 @@ struct CompileOptions {
     int64_t item_bytes = 48 * 1024;    // shared-memory buffer of one staged unit
     int64_t min_item_bytes = 8 * 1024; // smallest unit the packer aims for
     int64_t slots = 296;               // CTAs resident at once (units are sized to give each ~2)
+    int64_t internal_div = 1;          // internal units aim for target / internal_div
+    int leaf_order = 0;                // 0: largest first; 1: tree order (children of one parent together)
 };
 
 // status codes shared with the C ABI

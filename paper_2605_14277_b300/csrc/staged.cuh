@@ -128,10 +128,13 @@ struct DownTab {
     uint32_t xbar;  // float2
     uint32_t ipar, iseq;
 };
-// an internal unit's staged child values: ev of infosets [c0, c1)
+// an internal unit's staged child values: ev of infosets [c0, c1), brought in
+// by one bulk copy (dst, src, bytes) once all its children are done
 struct ChildEv {
     uint32_t ev;
     int32_t c0;
+    uint32_t dst, bytes;
+    const void *src;
 };
 
 // Shared-memory placement of the copied range [a, b) of an array with element
@@ -233,8 +236,13 @@ __device__ void issue_up(const DevPlayer &P, const int4 hdr, unsigned char *buf,
             default: t.val = sh_off(place(cur, P.m_val, L.n0, L.n1, 4, &dst, &src, &nb)); break;
             }
         } else if (f == 0 && internal && lane == nl) {
+            // placed now, copied once the children are done (issue_child_ev)
             cev->ev = sh_off(place(cur, P.ev, L.j0, L.j1, 4, &dst, &src, &nb));
             cev->c0 = L.j0;
+            cev->dst = sh_off((const void *)dst);
+            cev->bytes = nb;
+            cev->src = (const void *)src;
+            nb = 0;
         }
         mine += issue_copy(dst, src, nb, bar);
     }
@@ -246,6 +254,14 @@ __device__ void issue_up(const DevPlayer &P, const int4 hdr, unsigned char *buf,
         tab[lane].ev = sh_off(cur);
     }
     arm(bar, mine);
+}
+
+// One thread, once an internal unit's children are all done (acquired through
+// their completion count): copy their top-level ev into the unit's buffer.
+__device__ __forceinline__ void issue_child_ev(const ChildEv &c, uint64_t *bar) {
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, c.bytes);
+    if (c.bytes) bulk_g2s(sh<unsigned char>(c.dst), c.src, c.bytes, bar);
 }
 
 __device__ void issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
@@ -304,19 +320,58 @@ __device__ __forceinline__ UpView view(const UpTab &t) {
                   sh<const int32_t>(t.mptr), sh<const int32_t>(t.iseq), sh<const int32_t>(t.col), sh<float>(t.val)};
 }
 
-// ev, regret update, post-op and regret matching of infoset i (na <= kRegA),
-// with V already complete
-__device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int na, int variant, bool pred,
-                                            const ItemParams &ip) {
+// One infoset i with na <= kRegA actions, in registers: V of its sequences
+// (payoff row sum in CSR order, each product rounded before it is added, then
+// the child ev in child order; the actions' loops interleaved), ev, regret
+// update, post-op and regret matching.
+struct LevelIn {
+    const float *val, *gx, *evc;
+    int n0, cj0;
+    float sign;
+    bool kids;
+};
+__device__ __forceinline__ void up_step_reg(const UpView &t, const LevelIn &in, int i, int q0, int na, int variant,
+                                            bool pred, const ItemParams &ip) {
     float V[kRegA], bb[kRegA], qv[kRegA];
     float2 rr[kRegA];
+    int e[kRegA], e1[kRegA];
+    int len = 0;
 #pragma unroll
-    for (int a = 0; a < kRegA; a++)
+    for (int a = 0; a < kRegA; a++) {
+        V[a] = 0.f;
+        e[a] = e1[a] = 0;
         if (a < na) {
-            V[a] = t.V[q0 + a];
+            e[a] = t.mptr[q0 + a] - in.n0;
+            e1[a] = t.mptr[q0 + a + 1] - in.n0;
+            len = max(len, e1[a] - e[a]);
             bb[a] = t.b[q0 + a];
             rr[a] = t.r[q0 + a];
         }
+    }
+    for (int k = 0; k < len; k++) {
+#pragma unroll
+        for (int a = 0; a < kRegA; a++)
+            if (e[a] + k < e1[a]) V[a] = __fadd_rn(V[a], __fmul_rn(in.val[e[a] + k], in.gx[e[a] + k]));
+    }
+#pragma unroll
+    for (int a = 0; a < kRegA; a++) V[a] *= in.sign;
+    if (in.kids) {
+        len = 0;
+#pragma unroll
+        for (int a = 0; a < kRegA; a++) {
+            e[a] = e1[a] = 0;
+            if (a < na) {
+                e[a] = t.sch[q0 + a] - in.cj0;
+                e1[a] = t.sch[q0 + a + 1] - in.cj0;
+                len = max(len, e1[a] - e[a]);
+            }
+        }
+        for (int k = 0; k < len; k++) {
+#pragma unroll
+            for (int a = 0; a < kRegA; a++)
+                if (e[a] + k < e1[a]) V[a] += in.evc[e[a] + k];
+        }
+    }
     float ev = 0.f;
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
@@ -338,12 +393,25 @@ __device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int 
     const float uni = 1.0f / (float)na;
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
-        if (a < na) t.b[q0 + a] = pos > 0.f ? qv[a] * inv : uni;
+        if (a < na) {
+            t.b[q0 + a] = pos > 0.f ? qv[a] * inv : uni;
+            t.V[q0 + a] = V[a];   // kept for the root's top-down pass (overwritten there)
+        }
 }
 
 // the same for infosets with more actions, through shared memory
-__device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, int variant, bool pred, ItemParams ip) {
+__device__ __noinline__ void up_step_wide(UpTab tt, LevelIn in, int i, int q0, int q1, int variant, bool pred,
+                                          ItemParams ip) {
     const UpView t = view(tt);
+    for (int q = q0; q < q1; q++) {
+        float acc = 0.f;
+        for (int e = t.mptr[q] - in.n0; e < t.mptr[q + 1] - in.n0; e++)
+            acc = __fadd_rn(acc, __fmul_rn(in.val[e], in.gx[e]));
+        float v = in.sign * acc;
+        if (in.kids)
+            for (int c = t.sch[q] - in.cj0; c < t.sch[q + 1] - in.cj0; c++) v += in.evc[c];
+        t.V[q] = v;
+    }
     float ev = 0.f;
     for (int q = q0; q < q1; q++) ev = fmaf(t.b[q], t.V[q], ev);
     t.ev[i] = ev;
@@ -412,32 +480,22 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
     for (int k = nl - 1; k >= 0; k--) {
         const SLvl L = lv[k];
         const UpView t = view(tab[k]);
-        const int ns = L.s1 - L.s0, ni = L.j1 - L.j0;
+        const int ni = L.j1 - L.j0;
         // children of this level: the unit's next level, or (an internal
         // unit's deepest level) the staged child units' top levels
         const bool deepest = (k + 1 == nl);
-        const bool kids = !deepest || internal;
-        const int cj0 = deepest ? cev->c0 : lv[k + 1].j0;
-        const float *evc = sh<const float>(deepest ? cev->ev : tab[k + 1].ev);
-        // V[s] = sign * (payoff row, in CSR order) + child ev (in child order);
-        // each product rounded before it is added
-        const float *gx = sh<const float>(tab[k].gx);
-        for (int q = tid; q < ns; q += nt) {
-            float acc = 0.f;
-            const int e1 = t.mptr[q + 1] - L.n0;
-            for (int e = t.mptr[q] - L.n0; e < e1; e++) acc = __fadd_rn(acc, __fmul_rn(t.val[e], gx[e]));
-            float v = ia.sign * acc;
-            if (kids) {
-                const int c1 = t.sch[q + 1] - cj0;
-                for (int c = t.sch[q] - cj0; c < c1; c++) v += evc[c];
-            }
-            t.V[q] = v;
-        }
-        consumer_sync();
+        LevelIn in;
+        in.val = sh<const float>(tab[k].val);
+        in.gx = sh<const float>(tab[k].gx);
+        in.evc = sh<const float>(deepest ? cev->ev : tab[k + 1].ev);
+        in.n0 = L.n0;
+        in.cj0 = deepest ? cev->c0 : lv[k + 1].j0;
+        in.sign = ia.sign;
+        in.kids = !deepest || internal;
         for (int i = tid; i < ni; i += nt) {
             const int q0 = t.iseq[i] - L.s0, q1 = t.iseq[i + 1] - L.s0;
-            if (q1 - q0 <= kRegA) up_step_reg(t, i, q0, q1 - q0, ia.variant, pred, ip);
-            else up_step_wide(tab[k], i, q0, q1, ia.variant, pred, ip);
+            if (q1 - q0 <= kRegA) up_step_reg(t, in, i, q0, q1 - q0, ia.variant, pred, ip);
+            else up_step_wide(tab[k], in, i, q0, q1, ia.variant, pred, ip);
         }
         consumer_sync();
     }

@@ -1,7 +1,7 @@
 """Host game compiler: layout invariants and an FP64 replay of the kernels'
-schedule (leaf units from the queue deepest level first, each internal unit
-once its last child is done; then every unit top-down in queue order) over
-the compiled index arrays, checked against the oracle.  CPU only."""
+schedule (units bottom-up in queue order, each unit deepest level first; then
+every unit top-down in queue order) over the compiled index arrays, checked
+against the oracle.  CPU only."""
 import numpy as np
 import pytest
 
@@ -81,7 +81,13 @@ def check_invariants(lay, G_):
             assert bool(flags & 4) == (par >= 0 and units[par][5] < 0)
         # queues: leaves for the bottom-up pass; all units, parents first, for
         # the top-down pass
-        assert sorted(d["up_queue"].tolist()) == [u for u in range(len(units)) if units[u][6] == 0]
+        # the bottom-up queue holds every unit, each after all its children
+        assert sorted(d["up_queue"].tolist()) == list(range(len(units)))
+        upos = np.empty(len(units), np.int64)
+        upos[d["up_queue"]] = np.arange(len(units))
+        for ui in range(len(units)):
+            if units[ui][5] >= 0:
+                assert upos[units[ui][5]] > upos[ui]
         assert sorted(d["down_queue"].tolist()) == list(range(len(units)))
         pos = np.empty(len(units), np.int64)
         pos[d["down_queue"]] = np.arange(len(units))
@@ -204,18 +210,13 @@ class Sim:
                 for j in range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]):
                     step(j, t[g])
 
-        # leaves in queue order; an internal unit runs when its last child is done
+        # queue order; an internal unit runs once all its children are done
         done = np.zeros(len(units), np.int64)
         for ui in d["up_queue"]:
+            assert done[ui] == units[ui][6]
             run(ui)
-            v = ui
-            while units[v][5] >= 0:
-                par = units[v][5]
-                done[par] += 1
-                if done[par] < units[par][6]:
-                    break
-                run(par)
-                v = par
+            if units[ui][5] >= 0:
+                done[units[ui][5]] += 1
 
     def down(self, p, st, w):
         d = self.lay.pl[p]
