@@ -15,6 +15,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/cfr.h"
@@ -29,18 +30,25 @@ using namespace cfrb;
 // ---------------------------------------------------------------------------
 namespace cfrb {
 
-// the last CTA to leave a launch resets the queue for the next launch and
-// advances the epoch
-__device__ __forceinline__ void launch_exit(const DevPlayer &P) {
+// the last CTA to leave a launch resets the queue words q = {head, exit
+// count, epoch} for the next launch and advances the epoch
+__device__ __forceinline__ void launch_exit(int32_t *q) {
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(P.exits, 1) == (int)gridDim.x - 1) {
-            *P.work = 0;
-            *P.exits = 0;
-            atomicAdd(P.epoch, 1);
+        if (atomicAdd(&q[1], 1) == (int)gridDim.x - 1) {
+            q[0] = 0;
+            q[1] = 0;
+            atomicAdd(&q[2], 1);
         }
     }
 }
+
+// Programmatic dependent launch: a pass may start while the previous kernel
+// on the stream finishes.  pdl_wait blocks until that kernel has completed and
+// its memory is visible (it returns at once for an ordinary launch);
+// pdl_trigger lets the next kernel start.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Bottom-up completion of unit u (every thread of the CTA, after its
 // results are written): count it at its parent.
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
     __shared__ ItemParams s_ip;
     for (;;) {
         if (threadIdx.x == 0) {
-            s_item = atomicAdd(P.work, 1);
+            s_item = atomicAdd(&P.qup[0], 1);
             s_err = 0;
         }
         __syncthreads();
@@ -123,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         unit_done(P, u);
         if (threadIdx.x == 0 && tr.x < 0 && MODE == MODE_BR) gm.br[d.x] = __ldcg(&P.ev64[d.x]);
     }
-    launch_exit(P);
+    launch_exit(P.qup);
 }
 
 // Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
@@ -156,20 +164,30 @@ __global__ void __launch_bounds__(NT, MINB)
         mbar_init(&cbar[0], 1);
         mbar_init(&cbar[1], 1);
         fence_mbar_init();
-        s_cur = atomicAdd(P.work, 1);
+        s_cur = atomicAdd(&P.qup[0], 1);
         s_err = 0;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u}, cph[2] = {0u, 0u};
     int cur = s_cur, buf = 0;
+    // prologue, overlapping the previous kernel: nothing read here is written
+    // by it (the other player's x, gathered in compute_up, waits, and so do
+    // the parameters of a pass that follows the iteration's first pass, which
+    // advances the iteration counter)
+    int gfirst = 0;
     if (warp == 0) {
         if (cur < n) {
             const int4 h = P.units[P.up_queue[cur]];
-            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x, P.err);
+            gfirst = h.x;
+            if (tid == 0 && ia.first_of_iter) s_ip[0] = unit_params(gm, ia, h.x, P.err);
             if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0], &cev[0]);
         }
-        if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
+        if (tid == 0) s_nxt = cur < n ? atomicAdd(&P.qup[0], 1) : n;
     }
+    __syncthreads();
+    pdl_trigger();
+    pdl_wait();
+    if (tid == 0 && !ia.first_of_iter && cur < n) s_ip[0] = unit_params(gm, ia, gfirst, P.err);
     __syncthreads();
     int nxt = s_nxt;
     while (cur < n) {
@@ -187,7 +205,7 @@ __global__ void __launch_bounds__(NT, MINB)
         if (warp == 0) {
             // producer: the next unit's parameters and copies into the other
             // buffer, then the unit after it from the queue
-            if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
+            if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
             if (nxt < n) {
                 const int4 hn = P.units[P.up_queue[nxt]];
                 if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(NT, MINB)
         nxt = nxt2;
         buf ^= 1;
     }
-    launch_exit(P);
+    launch_exit(P.qup);
 }
 
 // one unit top-down from global memory (units too large to stage)
@@ -266,23 +284,34 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        s_epoch = __ldcg(P.epoch);
-        s_cur = atomicAdd(P.work, 1);
+        s_epoch = __ldcg(&P.qdn[2]);
+        s_cur = atomicAdd(&P.qdn[0], 1);
         s_err = 0;
     }
     __syncthreads();
     const int done_flag = s_epoch + 1;
     uint32_t ph[2] = {0u, 0u};
     int cur = s_cur, buf = 0;
+    // prologue, overlapping the previous kernel (this player's up pass): the
+    // first unit's own arrays first; b, the parameters (the iteration counter)
+    // and xn only once that kernel is done
     if (warp == 0) {
+        int4 h = make_int4(0, 0, 0, 0);
+        uint32_t carried = 0;
         if (cur < n) {
-            const int4 h = P.units[P.down_queue[cur]];
-            if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0]);
+            h = P.units[P.down_queue[cur]];
+            if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0], kDownOwn, 0);
+        }
+        if (tid == 0) s_nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
+        pdl_wait();
+        if (cur < n) {
+            if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0], kDownB, carried);
             if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x, P.err);
         }
-        if (tid == 0) s_nxt = cur < n ? atomicAdd(P.work, 1) : n;
     }
     __syncthreads();
+    pdl_trigger();
+    pdl_wait();
     int nxt = s_nxt;
     while (cur < n) {
         const int u = P.down_queue[cur];
@@ -301,10 +330,11 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         if (warp == 0) {
             if (nxt < n) {
                 const int4 hn = P.units[P.down_queue[nxt]];
-                if (hn.w & kStaged) issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1]);
+                if (hn.w & kStaged)
+                    issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1], kDownOwn | kDownB, 0);
                 if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
             }
-            if (tid == 0) s_nxt = nxt < n ? atomicAdd(P.work, 1) : n;
+            if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
         } else if (ip.active && staged) {
             if (wait) {
                 if (tid == 32 && !flag_wait(&P.unit_flag[tr.x], done_flag, P.err)) s_err = 1;
@@ -339,7 +369,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         nxt = nxt2;
         buf ^= 1;
     }
-    launch_exit(P);
+    launch_exit(P.qdn);
 }
 
 // uniform behavioural strategy (regret matching of r = 0)
@@ -512,6 +542,7 @@ struct cfr_ctx {
     std::vector<uint8_t> active_host;
     int64_t dev_bytes = 0, h2d_bytes = 0;
     int cfg = kDefaultConfig;       // staged launch shape (kConfigs)
+    bool pdl = true;                // passes may overlap the previous pass's tail
     int threads = 256;              // threads of a staged CTA
     int item_bytes = 48 * 1024;     // one staged unit buffer (two per CTA)
     size_t smem_staged = 0;
@@ -584,8 +615,28 @@ int launch_rebuild_x(cfr_ctx *c, int p) {
     return CFR_OK;
 }
 
+// Launch a pass kernel; with pdl it may start while the previous kernel on the
+// stream finishes (programmatic dependent launch: the kernel waits for that
+// kernel itself before it reads anything the kernel writes).
+template <class... P, class... A>
+cudaError_t launch_pass(void (*fn)(P...), int grid, int threads, size_t smem, cudaStream_t st, bool pdl, A &&...a) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fn, std::forward<A>(a)...);
+}
+
 // one iteration: NextStrategy/ObserveUtility for both players (Alg. 2), in the
-// alternating or simultaneous schedule (Sec. 3.5.1)
+// alternating or simultaneous schedule (Sec. 3.5.1).  Each pass may overlap
+// the previous one's tail (not when timing the passes one by one, and not
+// right after the parameter table is refilled).
 int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double gamma, bool alternating,
                      bool params, cudaEvent_t *ev = nullptr) {
     if (params) TRY(launch_params(c, variant, alpha, beta, gamma));
@@ -601,23 +652,26 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
     const int ib = c->item_bytes, nt = c->threads;
     const UpFn up = kConfigs[c->cfg].up;
     const DownFn down = kConfigs[c->cfg].down;
+    const bool pdl = (ev == nullptr) && c->pdl;
+    const bool pdl0 = pdl && !params;
+    const float *x1 = A.d.x, *x2 = B.d.x;
     mark(0);
     if (alternating) {
-        up<<<A.grid_up, nt, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
+        CU(launch_pass(up, A.grid_up, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, ib));
         mark(1);
-        down<<<A.grid_down, nt, sm, c->stream>>>(A.d, gm, dn, ib);
+        CU(launch_pass(down, A.grid_down, nt, sm, c->stream, pdl, A.d, gm, dn, ib));
         mark(2);
-        up<<<B.grid_up, nt, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
+        CU(launch_pass(up, B.grid_up, nt, sm, c->stream, pdl, B.d, gm, x1, up2, ib));
         mark(3);
-        down<<<B.grid_down, nt, sm, c->stream>>>(B.d, gm, dn, ib);
+        CU(launch_pass(down, B.grid_down, nt, sm, c->stream, pdl, B.d, gm, dn, ib));
     } else {
-        up<<<A.grid_up, nt, sm, c->stream>>>(A.d, gm, B.d.x, up1, ib);
+        CU(launch_pass(up, A.grid_up, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, ib));
         mark(1);
-        up<<<B.grid_up, nt, sm, c->stream>>>(B.d, gm, A.d.x, up2, ib);
+        CU(launch_pass(up, B.grid_up, nt, sm, c->stream, pdl, B.d, gm, x1, up2, ib));
         mark(2);
-        down<<<A.grid_down, nt, sm, c->stream>>>(A.d, gm, dn, ib);
+        CU(launch_pass(down, A.grid_down, nt, sm, c->stream, pdl, A.d, gm, dn, ib));
         mark(3);
-        down<<<B.grid_down, nt, sm, c->stream>>>(B.d, gm, dn, ib);
+        CU(launch_pass(down, B.grid_down, nt, sm, c->stream, pdl, B.d, gm, dn, ib));
     }
     mark(4);
     CU(cudaGetLastError());
@@ -704,13 +758,12 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.xnorm, H.S));
     int32_t *ctr;
     const int64_t nu = (int64_t)H.units.size();
-    TRY(dalloc(c, &ctr, 2 * nu + 3));
-    CU(cudaMemsetAsync(ctr, 0, (2 * nu + 3) * sizeof(int32_t), c->stream));
+    TRY(dalloc(c, &ctr, 2 * nu + 8));
+    CU(cudaMemsetAsync(ctr, 0, (2 * nu + 8) * sizeof(int32_t), c->stream));
     d.unit_cnt = ctr;
     d.unit_flag = ctr + nu;
-    d.work = ctr + 2 * nu;
-    d.exits = ctr + 2 * nu + 1;
-    d.epoch = ctr + 2 * nu + 2;
+    d.qup = ctr + 2 * nu;
+    d.qdn = ctr + 2 * nu + 4;
     d.err = c->err;
     CU(cudaMemsetAsync(d.r, 0, H.S * sizeof(float2), c->stream));
     CU(cudaMemsetAsync(d.xbar, 0, H.S * sizeof(float2), c->stream));
@@ -783,6 +836,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
     c->G = L.G;
     c->Z = L.Z;
     c->cfg = staged_config();
+    if (const char *e = std::getenv("CFR_B300_PDL")) c->pdl = std::atoi(e) != 0;
     c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
     // two unit buffers; a unit too large to stage uses its buffer as the

@@ -57,11 +57,13 @@ struct DevPlayer {
     float *u, *ev;
     double *u64, *ev64, *xnorm;
     // unit_cnt: children completed in the current bottom-up pass (reset by
-    // the CTA that completes the last one); unit_flag: epoch + 1 once a unit's
-    // top-down x is final; work / exits: queue head and exit count of the
-    // current launch (reset by the last CTA to exit, which also advances the
-    // epoch); err: nonzero once a bounded wait gave up
-    int32_t *unit_cnt, *unit_flag, *work, *exits, *epoch, *err;
+    // the parent once it has seen them all); unit_flag: epoch + 1 once a
+    // unit's top-down x is final; qup / qdn: the bottom-up and top-down
+    // passes' queue words {head, exit count, epoch} (reset by the last CTA to
+    // exit a launch, which also advances the epoch; separate words let one
+    // pass start while the previous one finishes); err: nonzero once a
+    // bounded wait gave up
+    int32_t *unit_cnt, *unit_flag, *qup, *qdn, *err;
 };
 
 struct ItemParams;

@@ -264,8 +264,14 @@ __device__ __forceinline__ void issue_child_ev(const ChildEv &c, uint64_t *bar) 
     if (c.bytes) bulk_g2s(sh<unsigned char>(c.dst), c.src, c.bytes, bar);
 }
 
-__device__ void issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
-                           DownTab *tab) {
+// Warp 0: lay out a down unit in buffer `buf` and start its copies.  `what`
+// selects the arrays: kDownOwn (x, xbar and the index arrays, which the
+// previous kernel does not write) and/or kDownB (the strategy b the up pass
+// just wrote).  The call that issues b arms the barrier with `carried` plus
+// its own bytes; the return value is this lane's bytes when b is not issued.
+constexpr int kDownOwn = 1, kDownB = 2;
+__device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
+                               DownTab *tab, int what, uint32_t carried) {
     const int lane = threadIdx.x & 31;
     const int32_t *rng = P.ranges + hdr.z;
     const int nl = hdr.y;
@@ -278,7 +284,7 @@ __device__ void issue_down(const DevPlayer &P, const int4 hdr, unsigned char *bu
     }
     unsigned char *cur = buf + level_offset(bytes);
     fence_proxy_async();
-    uint32_t mine = 0;
+    uint32_t mine = carried;
     const bool lvl = lane < nl;
     if (lvl) lv[lane] = L;
 #pragma unroll 1
@@ -295,9 +301,14 @@ __device__ void issue_down(const DevPlayer &P, const int4 hdr, unsigned char *bu
             default: t.iseq = sh_off(place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &dst, &src, &nb)); break;
             }
         }
+        if (!(what & (f == 0 ? kDownB : kDownOwn))) nb = 0;
         mine += issue_copy(dst, src, nb, bar);
     }
-    arm(bar, mine);
+    if (what & kDownB) {
+        arm(bar, mine);
+        return 0;
+    }
+    return mine;
 }
 
 // Up pass of a staged unit (consumer warps only): gathers of the other
