@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         __syncthreads();
         const int it = s_item;
         if (it >= P.n_up) break;
-        const int u = P.up_queue[it];
-        const int4 d = P.units[u];
-        const int2 tr = P.unit_tree[u];
+        const int4 d = P.upq[2 * it];
+        const int4 q = P.upq[2 * it + 1];
+        const int u = q.x;
+        const int2 tr = make_int2(q.y, q.z);
         if (threadIdx.x == 0) {
             item_params(gm, ia, d.x, &s_ip);
             if (s_ip.active && tr.y > 0) {
@@ -171,15 +172,11 @@ __global__ void __launch_bounds__(NT, MINB)
     uint32_t ph[2] = {0u, 0u}, cph[2] = {0u, 0u};
     int cur = s_cur, buf = 0;
     // prologue, overlapping the previous kernel: nothing read here is written
-    // by it (the other player's x, gathered in compute_up, waits, and so do
-    // the parameters of a pass that follows the iteration's first pass, which
-    // advances the iteration counter)
-    int gfirst = 0;
+    // by it (the other player's x, gathered in compute_up, waits)
     if (warp == 0) {
         if (cur < n) {
-            const int4 h = P.units[P.up_queue[cur]];
-            gfirst = h.x;
-            if (tid == 0 && ia.first_of_iter) s_ip[0] = unit_params(gm, ia, h.x, P.err);
+            const int4 h = P.upq[2 * cur];
+            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x);
             if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0], &cev[0]);
         }
         if (tid == 0) s_nxt = cur < n ? atomicAdd(&P.qup[0], 1) : n;
@@ -187,13 +184,12 @@ __global__ void __launch_bounds__(NT, MINB)
     __syncthreads();
     pdl_trigger();
     pdl_wait();
-    if (tid == 0 && !ia.first_of_iter && cur < n) s_ip[0] = unit_params(gm, ia, gfirst, P.err);
-    __syncthreads();
     int nxt = s_nxt;
     while (cur < n) {
-        const int u = P.up_queue[cur];
-        const int4 h = P.units[u];
-        const int2 tr = P.unit_tree[u];
+        const int4 h = P.upq[2 * cur];
+        const int4 q = P.upq[2 * cur + 1];
+        const int u = q.x;
+        const int2 tr = make_int2(q.y, q.z);
         const bool staged = (h.w & kStaged) != 0, internal = tr.y > 0, root = tr.x < 0;
         if (staged) {
             if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
@@ -207,8 +203,8 @@ __global__ void __launch_bounds__(NT, MINB)
             // buffer, then the unit after it from the queue
             if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
             if (nxt < n) {
-                const int4 hn = P.units[P.up_queue[nxt]];
-                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
+                const int4 hn = P.upq[2 * nxt];
+                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x);
                 if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1], &cev[buf ^ 1]);
             }
         } else if (ip.active) {
@@ -299,14 +295,14 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         int4 h = make_int4(0, 0, 0, 0);
         uint32_t carried = 0;
         if (cur < n) {
-            h = P.units[P.down_queue[cur]];
+            h = P.downq[2 * cur];
             if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0], kDownOwn, 0);
         }
         if (tid == 0) s_nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
         pdl_wait();
         if (cur < n) {
             if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0], kDownB, carried);
-            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x, P.err);
+            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x);
         }
     }
     __syncthreads();
@@ -314,9 +310,10 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
     pdl_wait();
     int nxt = s_nxt;
     while (cur < n) {
-        const int u = P.down_queue[cur];
-        const int4 h = P.units[u];
-        const int2 tr = P.unit_tree[u];
+        const int4 h = P.downq[2 * cur];
+        const int4 q = P.downq[2 * cur + 1];
+        const int u = q.x;
+        const int2 tr = make_int2(q.y, q.z);
         const bool staged = (h.w & kStaged) != 0;
         const bool below_root = (h.w & kChildOfRoot) != 0;
         if (staged) {
@@ -329,10 +326,10 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         const bool wait = ip.active && tr.x >= 0 && !below_root;
         if (warp == 0) {
             if (nxt < n) {
-                const int4 hn = P.units[P.down_queue[nxt]];
+                const int4 hn = P.downq[2 * nxt];
                 if (hn.w & kStaged)
                     issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1], kDownOwn | kDownB, 0);
-                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x, P.err);
+                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x);
             }
             if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
         } else if (ip.active && staged) {
@@ -594,7 +591,7 @@ DevGames dev_games(const cfr_ctx *c) { return DevGames{c->t_done, c->active, nul
 
 // the parameter table for the next kParamSpan iterations of every game
 int launch_params(cfr_ctx *c, int variant, double alpha, double beta, double gamma) {
-    IterArgs ia{variant, 0, 0.f, alpha, beta, gamma, 0};
+    IterArgs ia{variant, 0, 0.f, alpha, beta, gamma, 0, 0};
     const int64_t n = c->G * (kParamSpan + 1);
     k_params<<<(unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096), kThreads, 0, c->stream>>>(
         dev_games(c), ia, (int)c->G);
@@ -638,12 +635,16 @@ cudaError_t launch_pass(void (*fn)(P...), int grid, int threads, size_t smem, cu
 // the previous one's tail (not when timing the passes one by one, and not
 // right after the parameter table is refilled).
 int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double gamma, bool alternating,
-                     bool params, cudaEvent_t *ev = nullptr) {
+                     int k, cudaEvent_t *ev = nullptr) {
+    const bool params = (k % kParamSpan) == 0;
+    const int pslot = k % kParamSpan + 1;
     if (params) TRY(launch_params(c, variant, alpha, beta, gamma));
     const DevGames gm = dev_games(c);
-    IterArgs up1{variant, 1, +1.f, alpha, beta, gamma, 1};
-    IterArgs up2{variant, 0, -1.f, alpha, beta, gamma, 1};
-    IterArgs dn{variant, 0, 0.f, alpha, beta, gamma, 1};
+    // every pass of the k-th iteration since the table was filled runs at
+    // t = t_done + k + 1 of that moment
+    IterArgs up1{variant, 1, +1.f, alpha, beta, gamma, 1, pslot};
+    IterArgs up2{variant, 0, -1.f, alpha, beta, gamma, 1, pslot};
+    IterArgs dn{variant, 0, 0.f, alpha, beta, gamma, 1, pslot};
     PlayerBuf &A = c->pl[0], &B = c->pl[1];
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], c->stream);
@@ -735,10 +736,20 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     d.unit_tree = p2;
     TRY(upload(c, &p32, H.ranges));
     d.ranges = p32;
-    TRY(upload(c, &p32, H.up_queue));
-    d.up_queue = p32;
-    TRY(upload(c, &p32, H.down_queue));
-    d.down_queue = p32;
+    auto queue = [&](const std::vector<int32_t> &qv, const int4 **out) {
+        std::vector<int4> q(2 * qv.size());
+        for (size_t k = 0; k < qv.size(); k++) {
+            const Unit &u = H.units[qv[k]];
+            q[2 * k] = make_int4(u.game, u.nlvl, u.rng, u.flags);
+            q[2 * k + 1] = make_int4(qv[k], u.parent, u.nchild, 0);
+        }
+        int4 *pq;
+        TRY(upload(c, &pq, q));
+        *out = pq;
+        return CFR_OK;
+    };
+    TRY(queue(H.up_queue, &d.upq));
+    TRY(queue(H.down_queue, &d.downq));
     TRY(upload(c, &p32, H.game_root));
     d.game_root = p32;
     TRY(upload(c, &B.ext_inf, H.ext_inf));
@@ -883,8 +894,6 @@ int check_err(cfr_ctx *c) {
     CU(cudaStreamSynchronize(c->stream));
     if (e) {
         c->poisoned = true;
-        if (e == kErrParams)
-            return set_err(CFR_ERR_STATE, "internal: a pass ran outside its parameter table (context unusable)");
         return set_err(CFR_ERR_TIMEOUT, "a bounded device wait gave up (a copy or a parent unit did not complete)");
     }
     return CFR_OK;
@@ -910,7 +919,7 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
             CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = CFR_OK;
             for (int k = 0; k < K && rc == CFR_OK; k++)
-                rc = launch_iteration(c, variant, alpha, beta, gamma, alt, k % kParamSpan == 0);
+                rc = launch_iteration(c, variant, alpha, beta, gamma, alt, k);
             cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
@@ -928,7 +937,7 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
         for (; done + K <= n; done += K) CU(cudaGraphLaunch(exec, c->stream));
     }
     for (int64_t k = 0; done < n; done++, k++)
-        TRY(launch_iteration(c, variant, alpha, beta, gamma, alt, k % kParamSpan == 0));
+        TRY(launch_iteration(c, variant, alpha, beta, gamma, alt, (int)k));
     return CFR_OK;
 }
 
@@ -1202,7 +1211,7 @@ int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha,
     double tot[4] = {0, 0, 0, 0};
     int rc = CFR_OK;
     for (int64_t i = 0; i < n && rc == CFR_OK; i++) {
-        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, i % kParamSpan == 0, ev);
+        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, (int)i, ev);
         if (rc) break;
         cudaError_t e = cudaEventSynchronize(ev[4]);
         if (e != cudaSuccess) {

@@ -45,7 +45,11 @@ struct DevPlayer {
     const double *m_val64;
     const int4 *units;              // {game, nlvl, rng, flags}; ranges: kLvl ints per level
     const int2 *unit_tree;          // {parent unit (-1: root), child units}
-    const int32_t *ranges, *up_queue, *down_queue, *game_root;
+    // the queues in order, two int4 per entry: the unit's header
+    // {game, nlvl, rng, flags} and {unit, parent, child units, 0}, so a pass
+    // reads an entry with two independent loads
+    const int4 *upq, *downq;
+    const int32_t *ranges, *game_root;
     int32_t n_units, n_up, G;
     // state
     float2 *r;       // cumulative regret, float-float (hi, lo)
@@ -82,6 +86,8 @@ struct IterArgs {
     float sign;             // +1: u1 = M y ; -1: u2 = -M^T x
     double alpha, beta, gamma;
     int average;            // down pass: accumulate xbar (0 when only rebuilding x)
+    int pslot;              // parameter-table entry of this pass: iteration t = t_done + pslot
+                            // at the time the table was filled
 };
 
 // ---------------------------------------------------------------------------
@@ -152,17 +158,11 @@ __device__ __forceinline__ void item_params(const DevGames &gm, const IterArgs &
 }
 // The parameters of game g for this pass, from the table filled ahead of the
 // iterations (FP64 pow is slow on this part and costs registers: the table
-// keeps it out of the passes).  The host refreshes the table at least every
-// kParamSpan iterations; a t outside it sets the error word.
-constexpr int kErrParams = 2;
-__device__ __forceinline__ ItemParams unit_params(const DevGames &gm, const IterArgs &ia, int g, int32_t *err) {
-    const int32_t t = __ldcg(&gm.t_done[g]) + (ia.first_of_iter ? 1 : 0);
-    int32_t k = t - __ldcg(&gm.pbase[g]);
-    if (k < 0 || k > kParamSpan) {
-        atomicExch(err, kErrParams);
-        k = 0;
-    }
-    return gm.par[(int64_t)g * (kParamSpan + 1) + k];
+// keeps it out of the passes).  The host refills the table every kParamSpan
+// iterations and gives each pass its entry, so the lookup depends on no
+// counter another kernel writes.
+__device__ __forceinline__ ItemParams unit_params(const DevGames &gm, const IterArgs &ia, int g) {
+    return gm.par[(int64_t)g * (kParamSpan + 1) + ia.pslot];
 }
 
 // ---------------------------------------------------------------------------
