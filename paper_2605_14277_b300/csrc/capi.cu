@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(NT, MINB)
     pdl_trigger();
     pdl_wait();
     int nxt = s_nxt;
+    int done_par = -1;   // parent of the previous unit, counted by the producer
     while (cur < n) {
         const int4 h = P.upq[2 * cur];
         const int4 q = P.upq[2 * cur + 1];
@@ -199,9 +200,17 @@ __global__ void __launch_bounds__(NT, MINB)
         if (s_err) break;
         const ItemParams ip = s_ip[buf];
         if (warp == 0) {
-            // producer: the next unit's parameters and copies into the other
-            // buffer, then the unit after it from the queue
-            if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
+            // producer: count the previous unit at its parent (its results
+            // were written before the barrier above), then the next unit's
+            // parameters and copies into the other buffer, then the unit after
+            // it from the queue
+            if (tid == 0) {
+                if (done_par >= 0) {
+                    __threadfence();
+                    atomicAdd(&P.unit_cnt[done_par], 1);
+                }
+                s_nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
+            }
             if (nxt < n) {
                 const int4 hn = P.upq[2 * nxt];
                 if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x);
@@ -232,12 +241,18 @@ __global__ void __launch_bounds__(NT, MINB)
                 run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
                 if (root) root_topdown_global(P, h.y, P.ranges + h.z);
             }
-            unit_done(P, u);
             if (tid == 0 && root && ia.first_of_iter) gm.t_done[h.x] = ip.t;
         }
+        done_par = ip.active ? tr.x : -1;
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
+    }
+    // the last unit's count (nothing else of this CTA is pending)
+    __syncthreads();
+    if (tid == 0 && done_par >= 0) {
+        __threadfence();
+        atomicAdd(&P.unit_cnt[done_par], 1);
     }
     launch_exit(P.qup);
 }
@@ -309,6 +324,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
     pdl_trigger();
     pdl_wait();
     int nxt = s_nxt;
+    int done_u = -1;   // previous unit, published by the producer
     while (cur < n) {
         const int4 h = P.downq[2 * cur];
         const int4 q = P.downq[2 * cur + 1];
@@ -325,6 +341,12 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         const ItemParams ip = s_ip[buf];
         const bool wait = ip.active && tr.x >= 0 && !below_root;
         if (warp == 0) {
+            // producer: publish the previous unit (its x was written before
+            // the barrier above), then the next unit's copies and parameters
+            if (tid == 0 && done_u >= 0) {
+                __threadfence();
+                st_release(&P.unit_flag[done_u], done_flag);
+            }
             if (nxt < n) {
                 const int4 hn = P.downq[2 * nxt];
                 if (hn.w & kStaged)
@@ -337,14 +359,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
                 if (tid == 32 && !flag_wait(&P.unit_flag[tr.x], done_flag, P.err)) s_err = 1;
                 consumer_sync();
             }
-            if (!s_err) {
-                compute_down(P, ia, ip, h.y, lv[buf], tab[buf], below_root);
-                if (tr.y > 0 && tr.x >= 0) {
-                    __threadfence();
-                    consumer_sync();
-                    if (tid == 32) st_release(&P.unit_flag[u], done_flag);
-                }
-            }
+            if (!s_err) compute_down(P, ia, ip, h.y, lv[buf], tab[buf], below_root);
         }
         __syncthreads();
         if (s_err) break;
@@ -356,15 +371,18 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
                 if (s_err) break;
             }
             run_down(P, ia, ip, h.y, P.ranges + h.z, below_root);
-            if (tr.y > 0 && tr.x >= 0) {
-                __threadfence();
-                __syncthreads();
-                if (tid == 0) st_release(&P.unit_flag[u], done_flag);
-            }
         }
+        // published by the producer at the next loop top (units below the
+        // root's children wait for it; the root's children read xn instead)
+        done_u = (ip.active && tr.y > 0 && tr.x >= 0) ? u : -1;
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
+    }
+    __syncthreads();
+    if (tid == 0 && done_u >= 0) {
+        __threadfence();
+        st_release(&P.unit_flag[done_u], done_flag);
     }
     launch_exit(P.qdn);
 }
@@ -373,7 +391,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
 __global__ void k_uniform(DevPlayer P, int64_t J) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x) {
         const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
-        const float v = 1.0f / (float)(s1 - s0);
+        const float v = __frcp_rn((float)(s1 - s0));
         for (int s = s0; s < s1; s++) P.b[s] = v;
     }
 }
@@ -820,6 +838,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
         opt.item_bytes = cf.item_bytes;
         if (const char *e = std::getenv("CFR_B300_INTERNAL_DIV")) opt.internal_div = std::max(1, std::atoi(e));
         if (const char *e = std::getenv("CFR_B300_LEAF_ORDER")) opt.leaf_order = std::atoi(e);
+        if (const char *e = std::getenv("CFR_B300_FLAT")) opt.flat = std::atoi(e) != 0;
     }
     try {
         rc = compile_forest(tv.data(), n, opt, &L, &err);

@@ -449,6 +449,7 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                     for (int32_t j = lv[d].first; j < lv[d].second; j++) mx = std::max(mx, f[j]);
                     if (mx + slack_per_level * (below - d) <= tier_target) c = d;
                 }
+                if (opt.flat && c > 0) c = below - 1;   // one level per tier until the rest fits one unit
                 if (c < 0) c = below - 1;   // a single level per tier; wider units run unstaged
                 tops.push_back(c);
                 top_f.emplace_back(f.begin() + lv[c].first, f.begin() + lv[c].second);

@@ -218,12 +218,14 @@ __device__ void spmv_ranges(const int32_t *__restrict__ m_ptr, const int32_t *__
 // bottom-up step for one infoset j (MODE_CFR, global memory): counterfactual
 // values, regret update, variant post-op and the next behavioural strategy.
 // ---------------------------------------------------------------------------
+// Branch-free, so the lanes of a warp never split on the sign of r (a zero
+// regret stays zero; only its sign bit may change).
 __device__ __forceinline__ float2 post_op(float2 r, int variant, const ItemParams &ip) {
     if (variant == VAR_PLUS || variant == VAR_PCFR_PLUS) {
-        if (r.x < 0.f) r = make_float2(0.f, 0.f);
+        r = r.x < 0.f ? make_float2(0.f, 0.f) : r;
     } else if (variant == VAR_DCFR) {
-        if (r.x > 0.f) r = ff_mul(r, ip.fpos);
-        else if (r.x < 0.f) r = ff_mul(r, ip.fneg);
+        const float2 f = r.x > 0.f ? ip.fpos : (r.x < 0.f ? ip.fneg : make_float2(1.f, 0.f));
+        r = ff_mul(r, f);
     }
     return r;
 }
@@ -258,8 +260,8 @@ __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const Ite
         P.u[s] = q;
         pos += q;
     }
-    const float inv = pos > 0.f ? 1.0f / pos : 0.f;
-    const float uni = 1.0f / (float)na;
+    const float inv = pos > 0.f ? __frcp_rn(pos) : 0.f;   // = 1/pos correctly rounded
+    const float uni = __frcp_rn((float)na);
     for (int s = s0; s < s1; s++) P.b[s] = pos > 0.f ? P.u[s] * inv : uni;
 }
 

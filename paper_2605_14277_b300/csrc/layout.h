@@ -116,6 +116,7 @@ struct CompileOptions {
     int64_t slots = 296;               // CTAs resident at once (units are sized to give each ~2)
     int64_t internal_div = 1;          // internal units aim for target / internal_div
     int leaf_order = 0;                // 0: largest first; 1: tree order (children of one parent together)
+    bool flat = false;                 // one level per unit below a root unit that holds the narrow top
 };
 
 // status codes shared with the C ABI

@@ -400,8 +400,8 @@ __device__ __forceinline__ void up_step_reg(const UpView &t, const LevelIn &in, 
             qv[a] = x > 0.f ? x : 0.f;
             pos += qv[a];
         }
-    const float inv = pos > 0.f ? 1.0f / pos : 0.f;
-    const float uni = 1.0f / (float)na;
+    const float inv = pos > 0.f ? __frcp_rn(pos) : 0.f;   // = 1/pos correctly rounded
+    const float uni = __frcp_rn((float)na);
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
         if (a < na) {
@@ -437,8 +437,8 @@ __device__ __noinline__ void up_step_wide(UpTab tt, LevelIn in, int i, int q0, i
         t.V[q] = qq;   // V is no longer needed: keep the clipped regret
         pos += qq;
     }
-    const float inv = pos > 0.f ? 1.0f / pos : 0.f;
-    const float uni = 1.0f / (float)(q1 - q0);
+    const float inv = pos > 0.f ? __frcp_rn(pos) : 0.f;
+    const float uni = __frcp_rn((float)(q1 - q0));
     for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? t.V[q] * inv : uni;
 }
 

@@ -1,6 +1,7 @@
 // Test-only host wrapper around the game compiler: exposes the compiled layout
 // to the CPU tests so its index arrays can be checked without a GPU.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -23,6 +24,7 @@ void *probe_compile(int64_t G, const int64_t *n, const int32_t *const *parent, c
     for (int64_t g = 0; g < G; g++) tv[g] = {n[g], parent[g], kind[g], infoset[g], action[g], prob[g], payoff[g]};
     Layout *L = new Layout();
     CompileOptions o;
+    if (const char *f = std::getenv("LAYOUT_PROBE_FLAT")) o.flat = std::atoi(f) != 0;
     if (item_bytes > 0) {
         o.item_bytes = item_bytes;
         o.min_item_bytes = std::min<int64_t>(o.min_item_bytes, item_bytes);
