@@ -714,7 +714,7 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     DevPlayer &d = B.d;
     B.S = H.S;
     B.J = H.J;
-    B.n_units = (int64_t)H.units.size();
+    B.n_units = (int64_t)H.dunits.size();
     B.n_up = (int64_t)H.up_queue.size();
     B.n_levels = H.n_levels;
     B.game_J = H.game_J;
@@ -754,10 +754,10 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     d.unit_tree = p2;
     TRY(upload(c, &p32, H.ranges));
     d.ranges = p32;
-    auto queue = [&](const std::vector<int32_t> &qv, const int4 **out) {
+    auto queue = [&](const std::vector<int32_t> &qv, const std::vector<Unit> &units, const int4 **out) {
         std::vector<int4> q(2 * qv.size());
         for (size_t k = 0; k < qv.size(); k++) {
-            const Unit &u = H.units[qv[k]];
+            const Unit &u = units[qv[k]];
             q[2 * k] = make_int4(u.game, u.nlvl, u.rng, u.flags);
             q[2 * k + 1] = make_int4(qv[k], u.parent, u.nchild, 0);
         }
@@ -766,13 +766,13 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
         *out = pq;
         return CFR_OK;
     };
-    TRY(queue(H.up_queue, &d.upq));
-    TRY(queue(H.down_queue, &d.downq));
+    TRY(queue(H.up_queue, H.units, &d.upq));
+    TRY(queue(H.down_queue, H.dunits, &d.downq));
     TRY(upload(c, &p32, H.game_root));
     d.game_root = p32;
     TRY(upload(c, &B.ext_inf, H.ext_inf));
     TRY(upload(c, &B.ext_seq0, H.ext_seq0));
-    d.n_units = (int32_t)H.units.size();
+    d.n_units = (int32_t)H.dunits.size();
     d.n_up = (int32_t)H.up_queue.size();
     d.G = (int32_t)L.G;
     TRY(dalloc(c, &d.r, H.S));
@@ -786,7 +786,7 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.ev64, H.J));
     TRY(dalloc(c, &d.xnorm, H.S));
     int32_t *ctr;
-    const int64_t nu = (int64_t)H.units.size();
+    const int64_t nu = (int64_t)std::max(H.units.size(), H.dunits.size());
     TRY(dalloc(c, &ctr, 2 * nu + 8));
     CU(cudaMemsetAsync(ctr, 0, (2 * nu + 8) * sizeof(int32_t), c->stream));
     d.unit_cnt = ctr;

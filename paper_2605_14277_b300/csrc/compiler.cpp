@@ -520,6 +520,61 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 spans.swap(next);
             }
         }
+        // top-down units: consecutive siblings (same parent, so adjacent
+        // ranges at every level) merged while their top-down footprint fits
+        {
+            const int64_t nu0 = (int64_t)P.units.size();
+            std::vector<int32_t> down_of(nu0, -1);
+            P.dunits.clear();
+            auto build = [&](int64_t a, int64_t b) {   // up units [a, b), all siblings
+                const Unit &f = P.units[a];
+                Unit d{f.game, f.lvl0, 0, (int32_t)P.ranges.size(), 0, -1, 0, f.depth};
+                int32_t lo = P.ranges[f.rng], hi = P.ranges[P.units[b - 1].rng + 1];
+                int32_t nl = 0;
+                for (int64_t k = a; k < b; k++) nl = std::max(nl, P.units[k].nlvl);
+                int64_t fd = 0;
+                for (int32_t k = 0; k < nl && lo < hi; k++) {
+                    push_level(lo, hi);
+                    const int32_t slo = P.inf_seq[lo], shi = P.inf_seq[hi];
+                    fd += down_level_bytes(shi - slo, hi - lo);
+                    d.nlvl++;
+                    lo = P.seq_child[slo];
+                    hi = P.seq_child[shi];
+                }
+                if (d.nlvl < kMaxStagedLevels && fd <= opt.item_bytes) d.flags |= kStaged;
+                const int32_t up_par = f.parent;
+                if (up_par >= 0) {
+                    d.parent = down_of[up_par];
+                    P.dunits[d.parent].nchild++;
+                    if (P.units[up_par].parent < 0) d.flags |= kChildOfRoot;
+                }
+                const int32_t id = (int32_t)P.dunits.size();
+                for (int64_t k = a; k < b; k++) down_of[k] = id;
+                P.dunits.push_back(d);
+            };
+            auto fdown = [&](const Unit &u) {
+                int64_t fd = 0;
+                for (int32_t k = 0; k < u.nlvl; k++) {
+                    const int32_t *r = &P.ranges[u.rng + kLvl * k];
+                    fd += down_level_bytes(r[3] - r[2], r[1] - r[0]);
+                }
+                return fd;
+            };
+            int64_t a = 0, acc = 0;
+            for (int64_t k = 0; k < nu0; k++) {
+                const Unit &u = P.units[k];
+                const int64_t fk = fdown(u);
+                const bool same = k > a && u.game == P.units[a].game && u.parent == P.units[a].parent &&
+                                  u.parent >= 0 && u.lvl0 == P.units[a].lvl0;
+                if (!same || acc + fk > opt.item_bytes) {
+                    if (k > a) build(a, k);
+                    a = k;
+                    acc = 0;
+                }
+                acc += fk;
+            }
+            if (nu0 > a) build(a, nu0);
+        }
         // queues: leaves largest first for the bottom-up passes (a dynamic
         // queue then finishes with small units); every unit by tree depth for
         // the top-down pass, so a unit's parent always comes first
@@ -536,7 +591,16 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
         // bottom-up queue: every leaf, largest first, then the internal units
         // deepest first, so a unit is always taken after all its children
         P.up_queue.clear();
-        P.down_queue.resize(nu);
+        const int64_t nd = (int64_t)P.dunits.size();
+        std::vector<int64_t> dsz(nd);
+        for (int64_t k = 0; k < nd; k++) {
+            const Unit &u = P.dunits[k];
+            int64_t s = 0;
+            for (int32_t d = 0; d < u.nlvl; d++)
+                s += P.ranges[u.rng + kLvl * d + 3] - P.ranges[u.rng + kLvl * d + 2];
+            dsz[k] = s;
+        }
+        P.down_queue.resize(nd);
         std::iota(P.down_queue.begin(), P.down_queue.end(), 0);
         std::vector<int32_t> internal;
         for (int64_t k = 0; k < nu; k++)
@@ -550,8 +614,8 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
         });
         P.up_queue.insert(P.up_queue.end(), internal.begin(), internal.end());
         std::stable_sort(P.down_queue.begin(), P.down_queue.end(), [&](int32_t a, int32_t b) {
-            if (P.units[a].depth != P.units[b].depth) return P.units[a].depth < P.units[b].depth;
-            return usz[a] > usz[b];
+            if (P.dunits[a].depth != P.dunits[b].depth) return P.dunits[a].depth < P.dunits[b].depth;
+            return dsz[a] > dsz[b];
         });
     }
     L.game_nnz.assign(G, 0);

@@ -50,7 +50,7 @@ struct DevPlayer {
     // reads an entry with two independent loads
     const int4 *upq, *downq;
     const int32_t *ranges, *game_root;
-    int32_t n_units, n_up, G;
+    int32_t n_units, n_up, G;       // n_units: top-down units; n_up: bottom-up queue length
     // state
     float2 *r;       // cumulative regret, float-float (hi, lo)
     float *b;        // behavioural strategy to be played next

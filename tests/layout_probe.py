@@ -56,7 +56,7 @@ class Layout:
         for p in (0, 1):
             d = {}
             for name in ("inf_seq", "seq_child", "inf_par", "seq_game", "m_ptr", "m_col", "ranges",
-                         "up_queue", "down_queue", "game_root", "game_tiers", "ext_inf", "ext_seq0", "units"):
+                         "up_queue", "down_queue", "game_root", "game_tiers", "ext_inf", "ext_seq0", "units", "dunits"):
                 m = L.probe_i32(h, p, name.encode(), None)
                 a = np.zeros(m, np.int32)
                 L.probe_i32(h, p, name.encode(), a.ctypes.data)
@@ -71,6 +71,7 @@ class Layout:
                 L.probe_i64(h, p, name.encode(), a.ctypes.data)
                 d[name] = a
             d["units"] = d["units"].reshape(-1, 8)   # game, lvl0, nlvl, rng, flags, parent, nchild, depth
+            d["dunits"] = d["dunits"].reshape(-1, 8)
             self.pl[p] = d
 
     def __del__(self):

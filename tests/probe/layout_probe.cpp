@@ -57,8 +57,8 @@ int64_t probe_i32(void *h, int p, const char *name, void *out) {
     if (s == "game_tiers") return copy_out(P.game_tiers, out);
     if (s == "ext_inf") return copy_out(P.ext_inf, out);
     if (s == "ext_seq0") return copy_out(P.ext_seq0, out);
-    if (s == "units") {
-        const std::vector<Unit> &v = P.units;
+    if (s == "units" || s == "dunits") {
+        const std::vector<Unit> &v = s == "units" ? P.units : P.dunits;
         if (out)
             for (size_t k = 0; k < v.size(); k++) {
                 int32_t *o = (int32_t *)out + 8 * k;

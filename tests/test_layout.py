@@ -88,13 +88,43 @@ def check_invariants(lay, G_):
         for ui in range(len(units)):
             if units[ui][5] >= 0:
                 assert upos[units[ui][5]] > upos[ui]
-        assert sorted(d["down_queue"].tolist()) == list(range(len(units)))
-        pos = np.empty(len(units), np.int64)
-        pos[d["down_queue"]] = np.arange(len(units))
-        for ui in range(len(units)):
-            if units[ui][5] >= 0:
-                assert pos[units[ui][5]] < pos[ui]
-        assert (np.diff(units[d["down_queue"], 7]) >= 0).all()
+        # top-down units: merged runs of siblings; they cover every infoset
+        # once, hang below their parent's deepest level, and come after it
+        du = d["dunits"]
+        cover = np.zeros(J, np.int64)
+        dunit_of = {}
+        for di, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(du):
+            prev = None
+            for k in range(nlvl):
+                lo, hi, s0, s1 = rng[r0 + 6 * k: r0 + 6 * k + 4]
+                assert hi > lo and s0 == inf_seq[lo] and s1 == inf_seq[hi]
+                cover[lo:hi] += 1
+                for j in range(lo, hi):
+                    dunit_of[j] = (di, k)
+                if prev is not None:
+                    assert lo == seq_child[inf_seq[prev[0]]] and hi == seq_child[inf_seq[prev[1]]]
+                prev = (lo, hi)
+        assert (cover == 1).all()
+        nchild_d = np.zeros(len(du), np.int64)
+        for di, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(du):
+            lo, hi = rng[r0], rng[r0 + 1]
+            if par < 0:
+                assert lvl0 == 0 and hi - lo == 1
+                continue
+            nchild_d[par] += 1
+            for j in range(lo, hi):
+                pinf = np.searchsorted(inf_seq, inf_par[j], side="right") - 1
+                assert dunit_of[pinf] == (par, du[par][2] - 1)
+            assert bool(flags & 4) == (du[par][5] < 0)
+        assert nchild_d.tolist() == du[:, 6].tolist()
+        assert len(du) <= len(units)
+        assert sorted(d["down_queue"].tolist()) == list(range(len(du)))
+        pos = np.empty(len(du), np.int64)
+        pos[d["down_queue"]] = np.arange(len(du))
+        for di in range(len(du)):
+            if du[di][5] >= 0:
+                assert pos[du[di][5]] < pos[di]
+        assert (np.diff(du[d["down_queue"], 7]) >= 0).all()
 
 
 @pytest.mark.parametrize("item_bytes", [0, 600, 4000])
@@ -113,6 +143,11 @@ def test_staged_units_fit_their_buffer():
         for p in (0, 1):
             d = lay.pl[p]
             n_staged = 0
+            for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["dunits"]:
+                rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
+                fd = sum(down_bytes(s1 - s0, j1 - j0) for j0, j1, s0, s1, n0, n1 in rng)
+                if flags & 1:
+                    assert fd <= item_bytes and nlvl <= 24
             for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["units"]:
                 rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
                 fu = sum(up_bytes(s1 - s0, j1 - j0, n1 - n0) for j0, j1, s0, s1, n0, n1 in rng)
@@ -222,7 +257,7 @@ class Sim:
         d = self.lay.pl[p]
         inf_seq, rng, inf_par = d["inf_seq"], d["ranges"], d["inf_par"]
         x, xbar, b = st[p]["x"], st[p]["xbar"], st[p]["b"]
-        units = d["units"]
+        units = d["dunits"]
         finished = np.zeros(len(units), bool)
         for ui in d["down_queue"]:
             g, lvl0, nlvl, r0, flags, par = units[ui][:6]
