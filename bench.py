@@ -51,6 +51,39 @@ def workload(name):
     raise ValueError(name)
 
 
+def sources_sha256():
+    """sha256 over the kernel sources (file name, then contents, in name order)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2605_14277_b300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel_slot):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when that summary was taken on other sources."""
+    path = os.path.join(ROOT, "profiles", "k_up_staged_large.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    want = None
+    for line in txt.splitlines():
+        line = line.strip().strip("`")
+        if "sources_sha256:" in line:
+            want = line.split("sources_sha256:")[1].strip().strip("`").split()[0]
+    if want != sources_sha256():
+        return None
+    key = f"traffic_bytes_per_launch_{kernel_slot}:"
+    for line in txt.splitlines():
+        if line.startswith(key):
+            return int(line[len(key):].strip())
+    return None
+
+
 def alg_bytes(sz):
     """Algorithmic bytes per launch (forest totals include one root per game).
 
@@ -265,7 +298,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": 4 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": f"k_up_staged ({dom})",
+                         "frac": achieved / hbm, "traffic": profiled_traffic(dom),
+                         "kernel": f"{'k_up_staged' if dom.startswith('up') else 'k_down_staged'} ({dom})",
                          "alg_bytes_per_launch": kbytes[dom], "avg_launch_us": avg_ms[dom] * 1e3,
                          "peak_source": src},
             "iteration": {"alg_bytes": iter_bytes, "alg_GBps": iter_bytes / (ms / args.steps * 1e-3) / 1e9,
