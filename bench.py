@@ -316,13 +316,175 @@ def run_ours(args):
     return 0
 
 
+def gpu_uuid(local):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        return local
+
+
+def batch_alg_bytes(sizes):
+    """Algorithmic bytes of one iteration over a batch: the per-launch formula
+    of alg_bytes on the forest totals (one root per game)."""
+    tot = {k: sum(z[k] for z in sizes) for k in ("S1", "S2", "J1", "J2", "nnz")}
+    G_ = len(sizes)
+    S1, S2, J1, J2, Z = tot["S1"] + G_, tot["S2"] + G_, tot["J1"] + G_, tot["J2"] + G_, tot["nnz"]
+    return (8 * Z + 32 * S1 + 4 * J1 + 4 * S2) + (28 * S1 + 8 * J1) + (8 * Z + 32 * S2 + 4 * J2 + 4 * S1) + \
+        (28 * S2 + 8 * J2)
+
+
+def run_batch(args):
+    """4096 seeded games of 10^2-10^5 nodes advanced together by CFR+: one
+    launch per pass for all games, 64 iterations per CUDA graph, layout and
+    launch shape from the autotuner; against per-game launches on a sample."""
+    import torch
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2605_14277_b300 import autotune
+    from paper_2605_14277_b300 import cfr as C
+
+    variant = "cfr+"
+    n_games = args.batch_games
+    trees = G.batch_games(n_games, seed0=1000 + rank * n_games)
+    nodes = sum(t.n_nodes for t in trees)
+    stream = torch.cuda.Stream()
+    # autotune on a sample of the batch (every 8th game)
+    tuned = autotune.tune(trees[::8], variant=variant, iterations=64, repeats=2, stream=stream,
+                          budget_s=args.tune_budget)
+    s = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"])
+    s.set_graph_iterations(64)
+    sizes = [s.sizes(g) for g in range(n_games)]
+    s.iterate(max(args.warmup, 64), variant)
+    s.sync()
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.iterate(args.steps, variant)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_prof = 64
+    kms = s.profile(n_prof, variant)
+    names = ["up_p1", "down_p1", "up_p2", "down_p2"]
+    s.close()
+    value = nodes * args.steps * world / (ms * 1e-3)
+    iter_bytes = batch_alg_bytes(sizes)
+    hbm, src = peaks()
+    if rank == 0:
+        # per-game launches: the same iterations, one context per game, each
+        # game's 64-iteration graph replayed in turn on the same stream
+        sample = trees[:: max(1, n_games // args.per_game_sample)][: args.per_game_sample]
+        solos = [C.Solver(t, stream=stream) for t in sample]
+        for x in solos:
+            x.set_graph_iterations(64)
+            x.iterate(64, variant)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for x in solos:
+            x.iterate(64, variant)
+        e1.record(stream)
+        e1.synchronize()
+        solo_ms = e0.elapsed_time(e1)
+        solo_nodes = sum(t.n_nodes for t in sample)
+        for x in solos:
+            x.close()
+        per_game = {"value": solo_nodes * 64 / (solo_ms * 1e-3), "unit": UNIT,
+                    "sample": f"{len(sample)} of the {n_games} games, 64 CFR+ iterations each, one context per game"}
+        # end to end from host arrays: load, the iterations, exploitability back
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"])
+        s2.iterate(args.e2e_iters, variant)
+        expl, _, _ = s2.exploitability_batch()
+        el = time.perf_counter() - t0
+        h2d = s2.sizes()["h2d_bytes"]
+        s2.close()
+        e2e = {"value": nodes * args.e2e_iters / el, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.e2e_iters, "d2h_bytes_per_step": expl.nbytes / args.e2e_iters,
+               "iterations": args.e2e_iters, "seconds": el, "max_exploitability": float(expl.max()),
+               "what": "Solver(host trees) + iterate + exploitability of every game, wall clock"}
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            cpu = cpu_baseline_batch(trees[:: max(1, n_games // 64)], variant, budget_s=args.cpu_budget)
+        line = {
+            "metric": "node-updates/s per CFR iteration (CFR+, 4096-game batch)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 passes, f32+f32 (Kahan) accumulators, f64 best response", "data": "synthetic",
+            "config": {"workload": f"batch of {n_games} random games, nodes log-uniform in [1e2, 1e5]",
+                       "games": n_games, "nodes": nodes, "variant": "cfr+", "updates": "alternating",
+                       "graph_iterations": 64, "shape": tuned["shape"], "flat": tuned["flat"],
+                       "shape_info": C.shapes()[tuned["shape"]],
+                       "l2": f"inputs larger than L2: {iter_bytes / 2**20:.0f} MiB streamed per iteration vs 126 MiB L2",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": 4 * args.steps + (args.steps + 63) // 64,
+            "roofline": {"bound": "hbm", "achieved": iter_bytes / (ms / args.steps * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": iter_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm, "traffic": None,
+                         "kernel": "whole iteration (4 pass launches)", "alg_bytes_per_iteration": iter_bytes,
+                         "peak_source": src},
+            "iteration": {"kernel_us": {n: kms[i] / n_prof * 1e3 for i, n in enumerate(names)}},
+            "autotune": {"table": [[a, b, round(c, 2)] for a, b, c in tuned["table"]],
+                         "sample": "every 8th game of the batch"},
+            "per_game_launches": per_game,
+            "batched_over_per_game": value / world / per_game["value"],
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_batch(trees, variant, budget_s=15.0):
+    """The FP64 oracle, single-threaded, on a bounded sample of the batch."""
+    from oracle.oracle import Oracle
+    os_ = [Oracle(t) for t in trees]
+    t0 = time.perf_counter()
+    for o in os_:
+        o.iterate(1, variant)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(200, budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    for o in os_:
+        o.iterate(n, variant)
+    el = time.perf_counter() - t0
+    nodes = sum(t.n_nodes for t in trees)
+    return {"value": nodes * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} {variant} iterations of {len(trees)} of the batch's games (every 64th)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "poker", "small"])
+    ap.add_argument("--workload", default="large", choices=["large", "poker", "small", "batch"])
+    ap.add_argument("--batch-games", type=int, default=4096)
+    ap.add_argument("--per-game-sample", type=int, default=128)
+    ap.add_argument("--tune-budget", type=float, default=60.0)
     ap.add_argument("--e2e-iters", type=int, default=10000)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -331,6 +493,8 @@ def main():
         ap.error("warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -90,6 +90,36 @@ int cfr_load_tree(const cfr_tree_desc *tree, void *cuda_stream, cfr_ctx **out);
  * iteration counter.  games: host array of n_games descriptors. */
 int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream, cfr_ctx **out);
 
+/* Layout and launch choices made at load time.  All zero selects the
+ * library's defaults.
+ *   shape: 0 = default, k >= 1 = launch shape k of cfr_shape_info (threads per
+ *          CTA, CTAs per SM, unit buffer bytes); the units of work are sized
+ *          for the shape.
+ *   flat:  1 = one tree level per unit below a root unit that holds the narrow
+ *          top of each game; 0 = several levels per unit (default).
+ *   reserved: must be zero.
+ * Every choice computes the same iteration; they differ only in speed (see
+ * the autotuner in the Python package). */
+typedef struct {
+    int32_t shape;
+    int32_t flat;
+    int32_t reserved[6];
+} cfr_load_options;
+
+/* cfr_load_batch with load options (NULL = defaults).  CFR_ERR_ARG on an
+ * unknown shape, a flat value other than 0/1 or a nonzero reserved field. */
+int cfr_load_batch_opts(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream,
+                        const cfr_load_options *options, cfr_ctx **out);
+
+/* Number of launch shapes (shape indices 1..cfr_num_shapes()), and the shape
+ * that options.shape = 0 selects. */
+int cfr_num_shapes(void);
+int cfr_default_shape(void);
+
+/* Launch shape k: host_out3 = {threads per CTA, CTAs per SM, unit buffer
+ * bytes}.  CFR_ERR_ARG for k outside 1..cfr_num_shapes(). */
+int cfr_shape_info(int shape, int32_t *host_out3);
+
 /* Run n iterations of the chosen variant on every game (Alg. 2 NextStrategy /
  * ObserveUtility per player; Alg. 3/4/5 post-ops).  alpha, beta: DCFR
  * exponents (ignored by the other variants).  gamma: average-strategy weight

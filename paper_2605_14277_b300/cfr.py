@@ -28,6 +28,10 @@ class CFRError(RuntimeError):
         self.status = status
 
 
+class LoadOptions(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
 class TreeDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("parent", ctypes.c_void_p), ("kind", ctypes.c_void_p),
                 ("infoset", ctypes.c_void_p), ("action", ctypes.c_void_p),
@@ -46,6 +50,11 @@ def lib():
         P, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         L.cfr_load_tree.argtypes = [ctypes.POINTER(TreeDesc), P, ctypes.POINTER(P)]
         L.cfr_load_batch.argtypes = [ctypes.POINTER(TreeDesc), i64, P, ctypes.POINTER(P)]
+        L.cfr_load_batch_opts.argtypes = [ctypes.POINTER(TreeDesc), i64, P, ctypes.POINTER(LoadOptions),
+                                          ctypes.POINTER(P)]
+        L.cfr_num_shapes.argtypes = []
+        L.cfr_default_shape.argtypes = []
+        L.cfr_shape_info.argtypes = [i, P]
         L.cfr_iterate.argtypes = [P, i64, i, d, d, d]
         L.cfr_iterate_batch.argtypes = [P, i64, i, d, d, d, P]
         L.cfr_set_update_mode.argtypes = [P, i]
@@ -67,6 +76,22 @@ def lib():
         L.cfr_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
+
+
+def default_shape() -> int:
+    """The launch shape the library uses when none is chosen."""
+    return int(lib().cfr_default_shape())
+
+
+def shapes():
+    """Launch shapes: {k: (threads per CTA, CTAs per SM, unit buffer bytes)}."""
+    L = lib()
+    out = {}
+    for k in range(1, L.cfr_num_shapes() + 1):
+        v = np.zeros(3, dtype=np.int32)
+        _check(L.cfr_shape_info(k, _ptr(v)), "cfr_shape_info")
+        out[k] = tuple(int(x) for x in v)
+    return out
 
 
 def _check(rc: int, where: str):
@@ -113,14 +138,17 @@ class Solver:
     ``Solver(tree)`` loads one game; ``Solver([t1, t2, ...])`` loads a batch
     advanced together by every launch."""
 
-    def __init__(self, trees, stream=None):
+    def __init__(self, trees, stream=None, shape: int = 0, flat: bool = False):
         L = lib()
         batch = isinstance(trees, (list, tuple))
         trees = list(trees) if batch else [trees]
         keep = []
         descs = (TreeDesc * len(trees))(*[_desc(t, keep) for t in trees])
         h = ctypes.c_void_p()
-        _check(L.cfr_load_batch(descs, len(trees), _stream_handle(stream), ctypes.byref(h)), "cfr_load_batch")
+        opts = LoadOptions(int(shape), int(bool(flat)))
+        _check(L.cfr_load_batch_opts(descs, len(trees), _stream_handle(stream), ctypes.byref(opts), ctypes.byref(h)),
+               "cfr_load_batch_opts")
+        self.shape, self.flat = int(shape), bool(flat)
         self._h = h
         self.n_games = len(trees)
         self.batch = batch

@@ -505,15 +505,6 @@ const StagedConfig kConfigs[] = {
 constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 constexpr int kDefaultConfig = 1;
 
-// the launch shape: CFR_B300_STAGED_CONFIG (an index into kConfigs) if set
-int staged_config() {
-    const char *e = std::getenv("CFR_B300_STAGED_CONFIG");
-    if (e && *e) {
-        const int k = std::atoi(e);
-        if (k >= 0 && k < kNumConfigs) return k;
-    }
-    return kDefaultConfig;
-}
 
 struct PlayerBuf {
     DevPlayer d{};
@@ -557,7 +548,7 @@ struct cfr_ctx {
     std::vector<uint8_t> active_host;
     int64_t dev_bytes = 0, h2d_bytes = 0;
     int cfg = kDefaultConfig;       // staged launch shape (kConfigs)
-    bool pdl = true;                // passes may overlap the previous pass's tail
+    bool pdl = true;                // passes may overlap the previous pass's tail (not while profiling)
     int threads = 256;              // threads of a staged CTA
     int item_bytes = 48 * 1024;     // one staged unit buffer (two per CTA)
     size_t smem_staged = 0;
@@ -814,9 +805,19 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     return CFR_OK;
 }
 
-int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
+int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_options *lo, cfr_ctx **out) {
     if (!out) return set_err(CFR_ERR_ARG, "out is NULL");
     *out = nullptr;
+    int shape = kDefaultConfig;
+    bool flat = false;
+    if (lo) {
+        if (lo->shape < 0 || lo->shape > kNumConfigs) return set_err(CFR_ERR_ARG, "unknown launch shape");
+        if (lo->flat != 0 && lo->flat != 1) return set_err(CFR_ERR_ARG, "flat must be 0 or 1");
+        for (int k = 0; k < 6; k++)
+            if (lo->reserved[k] != 0) return set_err(CFR_ERR_ARG, "reserved load options must be zero");
+        if (lo->shape > 0) shape = lo->shape - 1;
+        flat = lo->flat != 0;
+    }
     if (!games || n < 1) return set_err(CFR_ERR_ARG, "no games");
     std::vector<TreeView> tv(n);
     for (int64_t g = 0; g < n; g++) {
@@ -833,12 +834,10 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
         int dev = 0, sms = 148;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaGetLastError();
-        const StagedConfig &cf = kConfigs[staged_config()];
+        const StagedConfig &cf = kConfigs[shape];
         opt.slots = std::max(1, sms) * cf.ctas_per_sm;
         opt.item_bytes = cf.item_bytes;
-        if (const char *e = std::getenv("CFR_B300_INTERNAL_DIV")) opt.internal_div = std::max(1, std::atoi(e));
-        if (const char *e = std::getenv("CFR_B300_LEAF_ORDER")) opt.leaf_order = std::atoi(e);
-        if (const char *e = std::getenv("CFR_B300_FLAT")) opt.flat = std::atoi(e) != 0;
+        opt.flat = flat;
     }
     try {
         rc = compile_forest(tv.data(), n, opt, &L, &err);
@@ -865,8 +864,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, cfr_ctx **out) {
     }
     c->G = L.G;
     c->Z = L.Z;
-    c->cfg = staged_config();
-    if (const char *e = std::getenv("CFR_B300_PDL")) c->pdl = std::atoi(e) != 0;
+    c->cfg = shape;
     c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
     // two unit buffers; a unit too large to stage uses its buffer as the
@@ -1052,11 +1050,30 @@ int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl) {
 }
 
 int cfr_load_tree(const cfr_tree_desc *tree, void *cuda_stream, cfr_ctx **out) {
-    return load(tree, 1, cuda_stream, out);
+    return load(tree, 1, cuda_stream, nullptr, out);
 }
 
 int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream, cfr_ctx **out) {
-    return load(games, n_games, cuda_stream, out);
+    return load(games, n_games, cuda_stream, nullptr, out);
+}
+
+int cfr_load_batch_opts(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream,
+                        const cfr_load_options *options, cfr_ctx **out) {
+    return load(games, n_games, cuda_stream, options, out);
+}
+
+int cfr_num_shapes(void) { return kNumConfigs; }
+
+int cfr_default_shape(void) { return kDefaultConfig + 1; }
+
+int cfr_shape_info(int shape, int32_t *host_out3) {
+    if (!host_out3) return set_err(CFR_ERR_ARG, "host_out3 is NULL");
+    if (shape < 1 || shape > kNumConfigs) return set_err(CFR_ERR_ARG, "unknown launch shape");
+    const StagedConfig &cf = kConfigs[shape - 1];
+    host_out3[0] = cf.threads;
+    host_out3[1] = cf.ctas_per_sm;
+    host_out3[2] = cf.item_bytes;
+    return CFR_OK;
 }
 
 int cfr_iterate(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma) {

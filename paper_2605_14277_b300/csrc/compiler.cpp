@@ -427,14 +427,17 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                     f[j] = u;
                 }
         };
+        // unit size: enough units for ~2 per resident CTA over the whole batch,
+        // within the buffer.  (The arithmetic of a sequence does not depend on
+        // how the game is cut: every sum runs in the same fixed order, so a game
+        // gives the same results alone and inside a batch.)
+        int64_t batch_raw = 0;
+        for (int64_t g = 0; g < G; g++) batch_raw += raw_up[g];
+        int64_t target = batch_raw / std::max<int64_t>(1, 2 * opt.slots);
+        target = std::max(opt.min_item_bytes, std::min(target, opt.item_bytes));
         for (int64_t g = 0; g < G; g++) {
             const auto &lv = glv[g];
             const int32_t nl = (int32_t)lv.size();   // levels 0..nl-1; level 0 = the root pseudo-infoset
-            // unit size: enough units for ~2 per resident CTA if this game were
-            // alone, within the buffer.  It depends on this game only, so a game
-            // is cut into the same units alone and inside a batch.
-            int64_t target = raw_up[g] / std::max<int64_t>(1, 2 * opt.slots);
-            target = std::max(opt.min_item_bytes, std::min(target, opt.item_bytes));
             // tiers, bottom up: each tier starts at the shallowest level whose
             // subtrees, truncated at the tier below, fit the target
             std::vector<int32_t> tops;
