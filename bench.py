@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -180,11 +182,82 @@ def dist_setup():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def run_reference_batch(args):
+    """The oracle on the batched workload: a bounded sample of the games."""
+    from oracle.oracle import Oracle
+    trees = G.batch_games(args.batch_games)[:: max(1, args.batch_games // 64)]
+    os_ = [Oracle(t) for t in trees]
+    t0 = time.perf_counter()
+    for o in os_:
+        o.iterate(max(1, args.warmup), "cfr+")
+    per = (time.perf_counter() - t0) / max(1, args.warmup)
+    k = int(min(args.steps, max(3, 120.0 / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    for o in os_:
+        o.iterate(k, "cfr+")
+    el = time.perf_counter() - t0
+    nodes = sum(t.n_nodes for t in trees)
+    value = nodes * k / el
+    sample = f"{k} cfr+ iterations of {len(trees)} of the {args.batch_games} games (every 64th)"
+    line = {"metric": "node-updates/s per CFR iteration (CFR+, 4096-game batch)", "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / k,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": f"batch of {args.batch_games} random games", "variant": "cfr+"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_serve(args):
+    """The oracle on the serving workload: requests solved one at a time, in
+    arrival order, until the time budget is spent."""
+    from oracle.oracle import Oracle
+    from paper_2605_14277_b300 import serving as SV
+    n = max(1, int(round(args.serve_rate * args.serve_seconds)))
+    seed0 = 500000
+    arrivals = G.poisson_arrivals(seed0, args.serve_rate, n)
+    t0 = time.perf_counter()
+    lat, done = [], 0
+    for k in range(n):
+        if time.perf_counter() - t0 > 120.0:
+            break
+        tree = G.serving_request(seed0 + 1 + k)
+        rng = SV.payoff_range(tree)
+        o = Oracle(tree)
+        it = 0
+        while True:
+            o.iterate(64, "dcfr", alpha=1.5, beta=0.0, gamma=2.0)
+            it += 64
+            if o.exploitability()[0] <= 1e-3 * rng or it >= 100000:
+                break
+        done += 1
+        lat.append(time.perf_counter() - t0 - arrivals[k])
+    el = time.perf_counter() - t0
+    value = done / el
+    line = {"metric": "solves/s at exploitability <= 1e-3 of the payoff range (serving, Poisson arrivals)",
+            "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": done, "warmup": 0,
+            "ms_per_step": 1e3 * el / max(done, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s", "variant": "dcfr(1.5,0,2)"},
+            "latency": {"p50_s": float(np.percentile(lat, 50)) if lat else None,
+                        "p99_s": float(np.percentile(lat, 99)) if lat else None},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the first {done} of {n} requests, one at a time, 120 s budget"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: same workload and metric."""
     world, rank, local = dist_setup()
     if rank != 0:
         return 0
+    if args.workload == "batch":
+        return run_reference_batch(args)
+    if args.workload == "serve":
+        return run_reference_serve(args)
     tree, variant = workload(args.workload)
     from oracle.oracle import Oracle
     o = Oracle(tree)
@@ -457,6 +530,71 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Subgame-solve requests (nodes log-uniform in [1e3, 1e6], N(0,1)
+    payoffs) arriving as a Poisson process, admitted under a 120 GB budget in
+    cohorts and solved by DCFR to exploitability <= 1e-3 of the payoff range;
+    against the one-at-a-time loop on a sample."""
+    import torch
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    from paper_2605_14277_b300 import cfr as C
+    from paper_2605_14277_b300 import serving as SV
+
+    n = max(1, int(round(args.serve_rate * args.serve_seconds)))
+    seed0 = 500000 + rank * 100000
+    arrivals = G.poisson_arrivals(seed0, args.serve_rate, n)
+    trees = [G.serving_request(seed0 + 1 + k) for k in range(n)]
+    factory = lambda ts, st: C.Solver(ts, stream=st)   # noqa: E731
+    # warm-up: one small cohort through the whole path (library load, graphs)
+    warm = SV.make_requests(trees[:4], [0.0] * 4)
+    SV.Server(factory, stream_factory=torch.cuda.Stream, max_iterations=256).run(warm)
+    reqs = SV.make_requests(trees, arrivals)
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=2, initializer=torch.cuda.set_device, initargs=(local,)) as pool:
+        srv = SV.Server(factory, hbm_budget=args.serve_budget_gb * 1e9, round_iters=64, variant="dcfr",
+                        target_rel=1e-3, max_cohort_nodes=args.serve_cohort_nodes,
+                        stream_factory=torch.cuda.Stream, loader=pool.submit)
+        st = srv.run(reqs, time_limit=args.serve_time_limit)
+    clocks = sampler.stop()
+    # one request at a time, on the first requests (bounded)
+    base_n = min(n, args.serve_baseline)
+    base = SV.make_requests(trees[:base_n], arrivals[:base_n])
+    bst = SV.serve_one_at_a_time(factory, base, round_iters=64, variant="dcfr", target_rel=1e-3,
+                                 time_limit=args.serve_time_limit)
+    nodes = sum(t.n_nodes for t in trees)
+    if rank == 0:
+        line = {
+            "metric": "solves/s at exploitability <= 1e-3 of the payoff range (serving, Poisson arrivals)",
+            "value": st["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": n, "warmup": 4,
+            "ms_per_step": 1e3 / st["solves_per_s"] if st["solves_per_s"] else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 passes, f32+f32 (Kahan) accumulators, f64 best response", "data": "synthetic",
+            "config": {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s, nodes log-uniform in [1e3, 1e6]",
+                       "nodes": nodes, "variant": "dcfr(1.5,0,2)", "round_iterations": 64,
+                       "cohort_nodes_max": args.serve_cohort_nodes, "loader_threads": 2,
+                       "hbm_budget_gb": args.serve_budget_gb, "parallelism": f"replicas x{world}"},
+            "latency": {"p50_s": st["p50_latency_s"], "p99_s": st["p99_latency_s"]},
+            "serving": st,
+            "node_updates_per_s": st["node_iterations"] / max(st["elapsed_s"], 1e-9),
+            "one_at_a_time": {"requests": base_n, "solves_per_s": bst["solves_per_s"],
+                              "p50_s": bst["p50_latency_s"], "p99_s": bst["p99_latency_s"],
+                              "completed": bst["completed"]},
+            "clocks": clocks,
+            "e2e": {"value": st["solves_per_s"], "unit": "solves/s",
+                    "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                    "what": "request trees from host memory: compile, upload, iterate, exploitability checks"},
+            "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def cpu_baseline_batch(trees, variant, budget_s=15.0):
     """The FP64 oracle, single-threaded, on a bounded sample of the batch."""
     from oracle.oracle import Oracle
@@ -481,7 +619,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "poker", "small", "batch"])
+    ap.add_argument("--workload", default="large", choices=["large", "poker", "small", "batch", "serve"])
+    ap.add_argument("--serve-rate", type=float, default=1000.0)
+    ap.add_argument("--serve-seconds", type=float, default=0.25)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-time-limit", type=float, default=120.0)
+    ap.add_argument("--serve-baseline", type=int, default=16)
+    ap.add_argument("--serve-cohort-nodes", type=float, default=4e6)
     ap.add_argument("--batch-games", type=int, default=4096)
     ap.add_argument("--per-game-sample", type=int, default=128)
     ap.add_argument("--tune-budget", type=float, default=60.0)
@@ -495,6 +639,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -1,0 +1,130 @@
+"""Serving loop host logic (admission under a budget, rounds, completion at
+the exploitability target, cohort release) with a stand-in solver: CPU only."""
+import numpy as np
+
+from paper_2605_14277_b300 import games as G
+from paper_2605_14277_b300 import serving as S
+
+
+class FakeClock:
+    def __init__(self, dt=1e-4):
+        self.t = 0.0
+        self.dt = dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+class FakeSolver:
+    """exploitability of game k after n iterations: range_k * 0.5 / n, so a
+    1e-3 target is met after 512 iterations; holds 100 bytes per node."""
+    log = []
+
+    def __init__(self, trees, stream=None):
+        self.trees = trees
+        self.n = np.zeros(len(trees))
+        self.ranges = np.array([S.payoff_range(t) for t in trees])
+        self.closed = False
+        FakeSolver.log.append(self)
+        self.masks = []
+
+    def iterate(self, n, variant="dcfr", active=None):
+        a = np.ones(len(self.trees), bool) if active is None else np.asarray(active, bool)
+        self.masks.append(a.copy())
+        self.n[a] += n
+
+    def exploitability_batch(self):
+        e = self.ranges * 0.5 / np.maximum(self.n, 1)
+        return e, e, e
+
+    def sizes(self, g=0):
+        return {"device_bytes": 100 * sum(t.n_nodes for t in self.trees)}
+
+    def close(self):
+        self.closed = True
+
+
+def reqs(n=12, rate=2000.0):
+    trees = [G.small_random_game(s) for s in range(n)]
+    return S.make_requests(trees, G.poisson_arrivals(5, rate, n))
+
+
+def test_all_requests_complete_at_their_target():
+    FakeSolver.log = []
+    rq = reqs()
+    srv = S.Server(FakeSolver, hbm_budget=1e12, round_iters=64, clock=FakeClock())
+    st = srv.run(rq)
+    assert st["completed"] == len(rq)
+    for r in rq:
+        assert r.done >= r.admitted >= r.arrival
+        assert r.iterations == 512          # first multiple of 64 with 0.5/n <= 1e-3
+    assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
+    assert st["solves_per_s"] > 0
+    assert all(s.closed for s in FakeSolver.log)
+    assert srv.in_use == 0
+
+
+def test_budget_limits_what_is_resident():
+    FakeSolver.log = []
+    rq = reqs(8)
+    one = max(r.nodes for r in rq) * 100
+    srv = S.Server(FakeSolver, hbm_budget=1.5 * one, round_iters=64, bytes_per_node=100.0, clock=FakeClock())
+    st = srv.run(rq)
+    assert st["completed"] == len(rq)
+    assert st["peak_bytes"] <= 1.5 * one
+    assert st["cohorts"] >= 2 and st["rejected"] == 0
+
+
+def test_request_larger_than_the_budget_is_rejected():
+    FakeSolver.log = []
+    rq = reqs(4)
+    big = max(rq, key=lambda r: r.nodes)
+    srv = S.Server(FakeSolver, hbm_budget=big.nodes * 100 - 1, bytes_per_node=100.0, clock=FakeClock())
+    st = srv.run(rq)
+    assert st["rejected"] >= 1 and big.done < 0
+    assert st["completed"] == len(rq) - st["rejected"]
+
+
+def test_no_request_is_admitted_before_it_arrives_and_done_games_are_masked():
+    FakeSolver.log = []
+    rq = reqs(6, rate=50.0)          # arrivals spread out
+    srv = S.Server(FakeSolver, hbm_budget=1e12, round_iters=64, clock=FakeClock(1e-3))
+    srv.run(rq)
+    for r in rq:
+        assert r.admitted >= r.arrival
+    # a cohort of several games: once a game is done its slot is masked off
+    for s in FakeSolver.log:
+        seen_done = np.zeros(len(s.trees), bool)
+        for m in s.masks:
+            assert not (m & seen_done).any()
+            seen_done |= ~m
+
+
+def test_mixed_sizes_finish_in_a_shared_cohort():
+    FakeSolver.log = []
+    trees = [G.small_random_game(1), G.poker_game(), G.rps()]
+    rq = S.make_requests(trees, [0.0, 0.0, 0.0])
+    srv = S.Server(FakeSolver, hbm_budget=1e12, clock=FakeClock())
+    st = srv.run(rq)
+    assert st["completed"] == 3 and st["cohorts"] == 1
+
+
+def test_one_at_a_time_baseline():
+    rq = reqs(5)
+    st = S.serve_one_at_a_time(FakeSolver, rq, clock=FakeClock())
+    assert st["completed"] == 5
+    assert all(r.iterations == 512 for r in rq)
+
+
+def test_background_loader():
+    from concurrent.futures import ThreadPoolExecutor
+    FakeSolver.log = []
+    rq = reqs(10)
+    with ThreadPoolExecutor(max_workers=2) as pool:
+        srv = S.Server(FakeSolver, hbm_budget=1e12, max_cohort_nodes=1500, clock=FakeClock(),
+                       loader=pool.submit)
+        st = srv.run(rq)
+    assert st["completed"] == len(rq)
+    assert st["cohorts"] >= 2          # the node cap splits the arrivals
+    assert srv.in_use == 0
