@@ -177,6 +177,28 @@ def cpu_baseline(tree, variant, budget_s=15.0):
             "sec_per_iteration": el / n}
 
 
+def max_over_ranks(x, dist):
+    """The largest value over all ranks (the slowest rank's time), on every rank."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist):
+    """The sum over all ranks (work done by the whole job), on every rank."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def dist_setup():
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -321,11 +343,7 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     s.sync()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     # per-kernel device time (events between eager launches, same stream)
     n_prof = max(50, min(2000, args.steps // 5))
     kms = s.profile(n_prof, variant)
@@ -336,7 +354,7 @@ def run_ours(args):
     hbm, src = peaks()
     achieved = kbytes[dom] / (avg_ms[dom] * 1e-3) / 1e9
     iter_bytes = sum(kbytes.values())
-    value = tree.n_nodes * args.steps * world / (ms * 1e-3)
+    value = sum_over_ranks(tree.n_nodes * args.steps, dist) / (ms * 1e-3)
     if rank == 0:
         # end to end through the public API from host buffers: load (compile +
         # upload), the config's iterations, exploitability and both average
@@ -452,16 +470,12 @@ def run_batch(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     n_prof = 64
     kms = s.profile(n_prof, variant)
     names = ["up_p1", "down_p1", "up_p2", "down_p2"]
     s.close()
-    value = nodes * args.steps * world / (ms * 1e-3)
+    value = sum_over_ranks(nodes * args.steps, dist) / (ms * 1e-3)
     iter_bytes = batch_alg_bytes(sizes)
     hbm, src = peaks()
     if rank == 0:
