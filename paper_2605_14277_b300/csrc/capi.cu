@@ -76,11 +76,56 @@ __device__ void root_topdown_global(const DevPlayer &P, int nlvl, const int32_t 
     }
 }
 
-// xn of every game's root unit from the current b (one CTA per game), when x
-// is rebuilt outside an iteration
+// The next x of game g's internal units below the root (their b is final once
+// the root is done), top down from the root's xn into xn, by the threads
+// [t0, t0 + nt) of the CTA; `sync` separates the levels.
+// Each thread takes kTdU infosets at a time and issues all their loads before
+// using any (the work is a few dependent global loads per infoset: one CTA
+// must keep many in flight).
+constexpr int kTdU = 4;
+template <class Sync>
+__device__ void internal_topdown(const DevPlayer &P, int g, int t0, int nt, Sync sync) {
+    const int64_t e0 = P.itd_off[g], e1 = P.itd_off[g + 1];
+    for (int64_t e = e0; e < e1; e++) {
+        const int32_t j0 = P.itd[3 * e], j1 = P.itd[3 * e + 1];
+        for (int base = j0 + (int)threadIdx.x - t0; base < j1; base += kTdU * nt) {
+            int par[kTdU], sa[kTdU], sb[kTdU];
+            float xp[kTdU], bv[kTdU][kRegA];
+#pragma unroll
+            for (int u = 0; u < kTdU; u++) {
+                const int j = base + u * nt;
+                par[u] = -1;
+                sa[u] = sb[u] = 0;
+                if (j < j1) {
+                    par[u] = P.inf_par[j];
+                    sa[u] = P.inf_seq[j];
+                    sb[u] = P.inf_seq[j + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kTdU; u++) {
+                xp[u] = par[u] >= 0 ? __ldcg(&P.xn[par[u]]) : 0.f;
+#pragma unroll
+                for (int a = 0; a < kRegA; a++) bv[u][a] = sa[u] + a < sb[u] ? __ldcg(&P.b[sa[u] + a]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kTdU; u++) {
+#pragma unroll
+                for (int a = 0; a < kRegA; a++)
+                    if (sa[u] + a < sb[u]) P.xn[sa[u] + a] = xp[u] * bv[u][a];
+                for (int q = sa[u] + kRegA; q < sb[u]; q++) P.xn[q] = xp[u] * __ldcg(&P.b[q]);
+            }
+        }
+        if (P.itd[3 * e + 2]) sync();
+    }
+}
+
+// xn of every game's root unit and internal units from the current b (one
+// CTA per game), when x is rebuilt outside an iteration
 __global__ void k_root_topdown(DevPlayer P) {
     const int4 h = P.units[P.game_root[blockIdx.x]];
     root_topdown_global(P, h.y, P.ranges + h.z);
+    internal_topdown(P, blockIdx.x, 0, blockDim.x, []() { __syncthreads(); });
 }
 
 // Per-game parameters of iterations t = t_done + k, k = 0..kParamSpan, for the
@@ -231,7 +276,14 @@ __global__ void __launch_bounds__(NT, MINB)
                 if (staged) cph[buf] ^= 1u;
                 consumer_sync();
             }
-            if (staged && !s_err) compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], &cev[buf], internal, root);
+            if (staged && !s_err) {
+                compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], &cev[buf], internal, root);
+                if (root) {
+                    consumer_sync();
+                    internal_topdown(P, h.x, kProducerThreads, (int)blockDim.x - kProducerThreads,
+                                     []() { consumer_sync(); });
+                }
+            }
         }
         __syncthreads();
         if (s_err) break;
@@ -239,7 +291,10 @@ __global__ void __launch_bounds__(NT, MINB)
         if (ip.active) {
             if (!staged) {
                 run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
-                if (root) root_topdown_global(P, h.y, P.ranges + h.z);
+                if (root) {
+                    root_topdown_global(P, h.y, P.ranges + h.z);
+                    internal_topdown(P, h.x, 0, blockDim.x, []() { __syncthreads(); });
+                }
             }
             if (tid == 0 && root && ia.first_of_iter) gm.t_done[h.x] = ip.t;
         }
@@ -257,12 +312,12 @@ __global__ void __launch_bounds__(NT, MINB)
     launch_exit(P.qup);
 }
 
-// one unit top-down from global memory (units too large to stage)
-__device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nlvl, const int32_t *rng,
-                         bool child_of_root) {
+// one unit top-down from global memory (units too large to stage); the top
+// level's parents' next x is in xn
+__device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nlvl, const int32_t *rng) {
     const bool avg = ia.average != 0;
     for (int k = 0; k < nlvl; k++) {
-        const float *xpar = (k == 0 && child_of_root) ? P.xn : P.x;
+        const float *xpar = (k == 0) ? P.xn : P.x;
         for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
             const int par = P.inf_par[j];
             const float xp = par < 0 ? 1.f : __ldcg(&xpar[par]);
@@ -276,10 +331,9 @@ __device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParam
 }
 
 // Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y) and the average
-// xbar += t^gamma x.  Units come from the queue in unit-tree depth order, so a
-// unit's parent was taken earlier by a running CTA.  A unit's copies start at
-// once; its computation waits until the parent has published its x (flag =
-// epoch + 1), except below the root, whose next x the up pass published in xn.
+// xbar += t^gamma x.  Every unit's top-level parents belong to the root or to
+// internal units, whose next x the bottom-up pass published in xn, so the
+// units are independent of one another.
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -287,7 +341,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ SLvl lv[2][kMaxStagedLevels];
     __shared__ DownTab tab[2][kMaxStagedLevels];
-    __shared__ int s_cur, s_nxt, s_err, s_epoch;
+    __shared__ int s_cur, s_nxt, s_err;
     __shared__ ItemParams s_ip[2];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_units;
@@ -295,12 +349,10 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        s_epoch = __ldcg(&P.qdn[2]);
         s_cur = atomicAdd(&P.qdn[0], 1);
         s_err = 0;
     }
     __syncthreads();
-    const int done_flag = s_epoch + 1;
     uint32_t ph[2] = {0u, 0u};
     int cur = s_cur, buf = 0;
     // prologue, overlapping the previous kernel (this player's up pass): the
@@ -324,14 +376,9 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
     pdl_trigger();
     pdl_wait();
     int nxt = s_nxt;
-    int done_u = -1;   // previous unit, published by the producer
     while (cur < n) {
         const int4 h = P.downq[2 * cur];
-        const int4 q = P.downq[2 * cur + 1];
-        const int u = q.x;
-        const int2 tr = make_int2(q.y, q.z);
         const bool staged = (h.w & kStaged) != 0;
-        const bool below_root = (h.w & kChildOfRoot) != 0;
         if (staged) {
             if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
             ph[buf] ^= 1u;
@@ -339,14 +386,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
         __syncthreads();
         if (s_err) break;
         const ItemParams ip = s_ip[buf];
-        const bool wait = ip.active && tr.x >= 0 && !below_root;
         if (warp == 0) {
-            // producer: publish the previous unit (its x was written before
-            // the barrier above), then the next unit's copies and parameters
-            if (tid == 0 && done_u >= 0) {
-                __threadfence();
-                st_release(&P.unit_flag[done_u], done_flag);
-            }
             if (nxt < n) {
                 const int4 hn = P.downq[2 * nxt];
                 if (hn.w & kStaged)
@@ -355,34 +395,14 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
             }
             if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
         } else if (ip.active && staged) {
-            if (wait) {
-                if (tid == 32 && !flag_wait(&P.unit_flag[tr.x], done_flag, P.err)) s_err = 1;
-                consumer_sync();
-            }
-            if (!s_err) compute_down(P, ia, ip, h.y, lv[buf], tab[buf], below_root);
+            compute_down(P, ia, ip, h.y, lv[buf], tab[buf]);
         }
         __syncthreads();
-        if (s_err) break;
         const int nxt2 = s_nxt;
-        if (ip.active && !staged) {
-            if (wait) {
-                if (tid == 0 && !flag_wait(&P.unit_flag[tr.x], done_flag, P.err)) s_err = 1;
-                __syncthreads();
-                if (s_err) break;
-            }
-            run_down(P, ia, ip, h.y, P.ranges + h.z, below_root);
-        }
-        // published by the producer at the next loop top (units below the
-        // root's children wait for it; the root's children read xn instead)
-        done_u = (ip.active && tr.y > 0 && tr.x >= 0) ? u : -1;
+        if (ip.active && !staged) run_down(P, ia, ip, h.y, P.ranges + h.z);
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
-    }
-    __syncthreads();
-    if (tid == 0 && done_u >= 0) {
-        __threadfence();
-        st_release(&P.unit_flag[done_u], done_flag);
     }
     launch_exit(P.qdn);
 }
@@ -761,6 +781,11 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(queue(H.down_queue, H.dunits, &d.downq));
     TRY(upload(c, &p32, H.game_root));
     d.game_root = p32;
+    TRY(upload(c, &p32, H.itd));
+    d.itd = p32;
+    int64_t *p64;
+    TRY(upload(c, &p64, H.itd_off));
+    d.itd_off = p64;
     TRY(upload(c, &B.ext_inf, H.ext_inf));
     TRY(upload(c, &B.ext_seq0, H.ext_seq0));
     d.n_units = (int32_t)H.dunits.size();
@@ -777,13 +802,12 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.ev64, H.J));
     TRY(dalloc(c, &d.xnorm, H.S));
     int32_t *ctr;
-    const int64_t nu = (int64_t)std::max(H.units.size(), H.dunits.size());
-    TRY(dalloc(c, &ctr, 2 * nu + 8));
-    CU(cudaMemsetAsync(ctr, 0, (2 * nu + 8) * sizeof(int32_t), c->stream));
+    const int64_t nu = (int64_t)H.units.size();
+    TRY(dalloc(c, &ctr, nu + 8));
+    CU(cudaMemsetAsync(ctr, 0, (nu + 8) * sizeof(int32_t), c->stream));
     d.unit_cnt = ctr;
-    d.unit_flag = ctr + nu;
-    d.qup = ctr + 2 * nu;
-    d.qdn = ctr + 2 * nu + 4;
+    d.qup = ctr + nu;
+    d.qdn = ctr + nu + 4;
     d.err = c->err;
     CU(cudaMemsetAsync(d.r, 0, H.S * sizeof(float2), c->stream));
     CU(cudaMemsetAsync(d.xbar, 0, H.S * sizeof(float2), c->stream));

@@ -523,6 +523,46 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 spans.swap(next);
             }
         }
+        // internal ranges below each game's root unit, by absolute level,
+        // adjacent ranges of one level merged
+        {
+            P.itd.clear();
+            P.itd_off.assign(G + 1, 0);
+            std::vector<std::vector<std::pair<int32_t, int32_t>>> bylevel;
+            int64_t gcur = -1;
+            auto flush = [&]() {
+                for (auto &lvr : bylevel) {
+                    std::sort(lvr.begin(), lvr.end());
+                    std::vector<std::pair<int32_t, int32_t>> merged;
+                    for (auto &r : lvr) {
+                        if (!merged.empty() && merged.back().second == r.first) merged.back().second = r.second;
+                        else merged.push_back(r);
+                    }
+                    for (size_t k = 0; k < merged.size(); k++) {
+                        P.itd.push_back(merged[k].first);
+                        P.itd.push_back(merged[k].second);
+                        P.itd.push_back(k + 1 == merged.size() ? 1 : 0);
+                    }
+                }
+                bylevel.clear();
+            };
+            for (size_t k = 0; k < P.units.size(); k++) {
+                const Unit &u = P.units[k];
+                if (u.game != gcur) {
+                    flush();
+                    for (int64_t g2 = gcur + 1; g2 <= u.game; g2++) P.itd_off[g2] = (int64_t)P.itd.size() / 3;
+                    gcur = u.game;
+                }
+                if (u.parent < 0 || u.nchild == 0) continue;   // the root itself, and leaves
+                for (int32_t d = 0; d < u.nlvl; d++) {
+                    const int32_t lvl = u.lvl0 + d;
+                    if ((int32_t)bylevel.size() <= lvl) bylevel.resize(lvl + 1);
+                    bylevel[lvl].push_back({P.ranges[u.rng + kLvl * d], P.ranges[u.rng + kLvl * d + 1]});
+                }
+            }
+            flush();
+            for (int64_t g2 = gcur + 1; g2 <= G; g2++) P.itd_off[g2] = (int64_t)P.itd.size() / 3;
+        }
         // top-down units: consecutive siblings (same parent, so adjacent
         // ranges at every level) merged while their top-down footprint fits
         {

@@ -13,13 +13,12 @@
 //          root unit.
 //   down : per unit, top-down: x[(j,a)] = x[p_j] b_j[a]          (Alg. 2: y += L^T y; x = A^T y)
 //          and the average xbar += t^gamma x (for the x being replaced).
-//          Units come from a queue in unit-tree depth order; a unit starts
-//          its top level once its parent unit has published its x.
+//          The up pass's root unit published the next x of every internal
+//          unit (xn), so the units are independent.
 //
-// The bottom-up pass never waits for another CTA: completion is counted with
-// one atomic per unit (threadfence-reduction pattern).  In the top-down pass
-// a unit's parent always comes earlier in the queue, so the CTA holding it is
-// running; that wait is bounded in time all the same.  Cumulative regrets and
+// Completion is counted with one atomic per unit (threadfence-reduction
+// pattern); an internal unit waits, bounded in time, for its children, which
+// come earlier in the queue and are held by running CTAs.  Cumulative regrets and
 // average sums are float-float pairs (Kahan-compensated FP32): B300's FP64
 // rate is far below its FP32 rate, so the hot path does no FP64 arithmetic.
 // The best-response pass (MODE_BR) runs in FP64.
@@ -50,6 +49,8 @@ struct DevPlayer {
     // reads an entry with two independent loads
     const int4 *upq, *downq;
     const int32_t *ranges, *game_root;
+    const int32_t *itd;             // internal ranges below each root: {j0, j1, last of level}
+    const int64_t *itd_off;         // [G + 1]
     int32_t n_units, n_up, G;       // n_units: top-down units; n_up: bottom-up queue length
     // state
     float2 *r;       // cumulative regret, float-float (hi, lo)
@@ -61,13 +62,11 @@ struct DevPlayer {
     float *u, *ev;
     double *u64, *ev64, *xnorm;
     // unit_cnt: children completed in the current bottom-up pass (reset by
-    // the parent once it has seen them all); unit_flag: epoch + 1 once a
-    // unit's top-down x is final; qup / qdn: the bottom-up and top-down
-    // passes' queue words {head, exit count, epoch} (reset by the last CTA to
-    // exit a launch, which also advances the epoch; separate words let one
-    // pass start while the previous one finishes); err: nonzero once a
-    // bounded wait gave up
-    int32_t *unit_cnt, *unit_flag, *qup, *qdn, *err;
+    // the parent once it has seen them all); qup / qdn: the bottom-up and
+    // top-down passes' queue words {head, exit count, launches} (reset by the
+    // last CTA to exit a launch; separate words let one pass start while the
+    // previous one finishes); err: nonzero once a bounded wait gave up
+    int32_t *unit_cnt, *qup, *qdn, *err;
 };
 
 struct ItemParams;

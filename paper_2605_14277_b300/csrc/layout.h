@@ -44,8 +44,9 @@ struct TreeView {
 // the child infosets of its deepest level at the top levels of its child
 // units.  Bottom-up passes take every leaf, then the internal units deepest
 // first, from one queue; an internal unit stages its own arrays at once and
-// starts computing when all its children are done.  Top-down passes take
-// every unit in tree-depth order and start a unit once its parent is done.
+// starts computing when all its children are done.  The root unit, last,
+// also runs the top-down pass over itself and the internal units, so the
+// top-down pass proper finds every unit's parents' next x ready.
 constexpr int kLvl = 6;
 struct Unit {
     int32_t game, lvl0, nlvl, rng;
@@ -58,7 +59,7 @@ constexpr int kStaged = 1;       // the unit fits one shared-memory buffer in bo
 constexpr int kInternal = 2;     // the deepest level's child infosets are other units' top levels;
                                  // their range [c0, c1) follows the unit's levels as one more
                                  // kLvl record {c0, c1, 0, 0, 0, 0}
-constexpr int kChildOfRoot = 4;  // the parent is the game's root unit
+constexpr int kChildOfRoot = 4;  // the parent is the game's root unit (informational)
 constexpr int kMaxStagedLevels = 24;
 
 // Shared-memory bytes a staged unit level needs (host and device agree on
@@ -96,6 +97,12 @@ struct PlayerLayout {
                                         // sequence); parent / nchild / depth in this tree
     std::vector<int32_t> down_queue;    // all top-down units by tree depth, then largest first
     std::vector<int32_t> game_root;     // [G] root unit of each game
+    // Per game, the infoset ranges of its internal units below the root unit,
+    // top down: {j0, j1, last range of its level} triples.  The bottom-up
+    // pass's root unit runs the top-down pass over them, so every unit's
+    // parents have their next x published before the top-down pass starts.
+    std::vector<int32_t> itd;           // 3 ints per range
+    std::vector<int64_t> itd_off;       // [G + 1] range offsets
     std::vector<int32_t> game_tiers;    // [G] depth of the game's unit tree + 1
     // caller order: game g's caller infoset k is ext_inf[game_jbase[g] + k]; its
     // sequences start at caller index ext_seq0[game_jbase[g] + k]

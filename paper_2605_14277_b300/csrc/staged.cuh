@@ -72,9 +72,6 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int32_t *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 // bounded wait for *flag == want (one thread): false (and the error word set)
 // if it does not happen within kFlagWaitNs
 __device__ __forceinline__ bool flag_wait(const int32_t *flag, int want, int32_t *err) {
@@ -531,13 +528,13 @@ __device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, con
 
 // Down pass of a staged unit: x[(j,a)] = x[p_j] b_j[a] top-down, and
 // xbar += w x for the strategy being replaced.  The top level's parents
-// belong to the parent unit, whose x is final (the root's next x was
-// published in xn by the up pass); the roots' parent is the empty sequence.
+// belong to the root or to internal units, whose next x the bottom-up pass
+// published in xn; the roots' parent is the empty sequence (x = 1).
 __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv,
-                             const DownTab *tab, bool child_of_root) {
+                             const DownTab *tab) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     const bool avg = ia.average != 0;
-    const float *xtop = child_of_root ? P.xn : P.x;
+    const float *xtop = P.xn;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
         const DownTab t = tab[k];

@@ -88,6 +88,36 @@ def check_invariants(lay, G_):
         for ui in range(len(units)):
             if units[ui][5] >= 0:
                 assert upos[units[ui][5]] > upos[ui]
+        # the internal ranges below each root: exactly the infosets of the
+        # game's internal non-root units, level by level top down, each level
+        # closed by a sync mark
+        itd, off = d["itd"].reshape(-1, 3), d["itd_off"]
+        assert off[0] == 0 and off[-1] == itd.shape[0] and len(off) == G_ + 1
+        level_of = np.zeros(J, np.int64)
+        for (g, lvl0, nlvl, r0, flags, par, nch, depth) in units:
+            for k in range(nlvl):
+                level_of[rng[r0 + 6 * k]: rng[r0 + 6 * k + 1]] = lvl0 + k
+        for g in range(G_):
+            want = set()
+            for (gg, lvl0, nlvl, r0, flags, par, nch, depth) in units:
+                if gg == g and par >= 0 and nch > 0:
+                    for k in range(nlvl):
+                        want.update(range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]))
+            got, last_level = [], -1
+            ents = itd[off[g]:off[g + 1]]
+            for k, (j0, j1, last) in enumerate(ents):
+                assert j1 > j0
+                lvls = set(level_of[j0:j1].tolist())
+                assert len(lvls) == 1
+                lvl = lvls.pop()
+                assert lvl >= last_level
+                if lvl > last_level and k > 0:
+                    assert ents[k - 1][2] == 1
+                last_level = lvl
+                got.extend(range(j0, j1))
+            assert len(got) == len(set(got)) and set(got) == want
+            if len(ents):
+                assert ents[-1][2] == 1
         # top-down units: merged runs of siblings; they cover every infoset
         # once, hang below their parent's deepest level, and come after it
         du = d["dunits"]
