@@ -450,7 +450,7 @@ def run_batch(args):
     # autotune on a sample of the batch (every 8th game)
     tuned = autotune.tune(trees[::8], variant=variant, iterations=64, repeats=2, stream=stream,
                           budget_s=args.tune_budget)
-    s = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"])
+    s = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"], passes=tuned["passes"])
     s.set_graph_iterations(64)
     sizes = [s.sizes(g) for g in range(n_games)]
     s.iterate(max(args.warmup, 64), variant)
@@ -501,7 +501,7 @@ def run_batch(args):
         # end to end from host arrays: load, the iterations, exploitability back
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"])
+        s2 = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"], passes=tuned["passes"])
         s2.iterate(args.e2e_iters, variant)
         expl, _, _ = s2.exploitability_batch()
         el = time.perf_counter() - t0
@@ -522,16 +522,17 @@ def run_batch(args):
             "config": {"workload": f"batch of {n_games} random games, nodes log-uniform in [1e2, 1e5]",
                        "games": n_games, "nodes": nodes, "variant": "cfr+", "updates": "alternating",
                        "graph_iterations": 64, "shape": tuned["shape"], "flat": tuned["flat"],
+                       "launches_per_player": 1 if tuned["passes"] == 1 else 2,
                        "shape_info": C.shapes()[tuned["shape"]],
                        "l2": f"inputs larger than L2: {iter_bytes / 2**20:.0f} MiB streamed per iteration vs 126 MiB L2",
                        "parallelism": f"replicas x{world}"},
-            "gpu_launches": 4 * args.steps + (args.steps + 63) // 64,
+            "gpu_launches": (2 if tuned["passes"] == 1 else 4) * args.steps + (args.steps + 63) // 64,
             "roofline": {"bound": "hbm", "achieved": iter_bytes / (ms / args.steps * 1e-3) / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": iter_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm, "traffic": None,
-                         "kernel": "whole iteration (4 pass launches)", "alg_bytes_per_iteration": iter_bytes,
+                         "kernel": "whole iteration (every pass launch)", "alg_bytes_per_iteration": iter_bytes,
                          "peak_source": src},
             "iteration": {"kernel_us": {n: kms[i] / n_prof * 1e3 for i, n in enumerate(names)}},
-            "autotune": {"table": [[a, b, round(c, 2)] for a, b, c in tuned["table"]],
+            "autotune": {"table": [[a, b, c, round(d, 2)] for a, b, c, d in tuned["table"]],
                          "sample": "every 8th game of the batch"},
             "per_game_launches": per_game,
             "batched_over_per_game": value / world / per_game["value"],

@@ -97,17 +97,25 @@ int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_strea
  *          for the shape.
  *   flat:  1 = one tree level per unit below a root unit that holds the narrow
  *          top of each game; 0 = several levels per unit (default).
+ *   passes: how the alternating schedule launches one player's bottom-up
+ *          and top-down passes.  1 = one kernel, in which the top-down units
+ *          of a game start as soon as that game's bottom-up pass is complete
+ *          (pays off when the games of a batch finish at different times);
+ *          2 = two kernels; 0 = the library's choice (one kernel when more
+ *          than one game is loaded, two for a single game).
  *   reserved: must be zero.
  * Every choice computes the same iteration; they differ only in speed (see
  * the autotuner in the Python package). */
 typedef struct {
     int32_t shape;
     int32_t flat;
-    int32_t reserved[6];
+    int32_t passes;
+    int32_t reserved[5];
 } cfr_load_options;
 
 /* cfr_load_batch with load options (NULL = defaults).  CFR_ERR_ARG on an
- * unknown shape, a flat value other than 0/1 or a nonzero reserved field. */
+ * unknown shape, a flat value other than 0/1, passes outside 0..2 or a
+ * nonzero reserved field. */
 int cfr_load_batch_opts(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream,
                         const cfr_load_options *options, cfr_ctx **out);
 
@@ -197,8 +205,9 @@ int cfr_set_state(cfr_ctx *ctx, int64_t game, int player, const double *host_r, 
  * between consecutive kernel launches on the context's stream, and return the
  * summed device time (ms) of each launch slot of an iteration in host_ms[4]:
  * [player-1 up, player-1 down, player-2 up, player-2 down] (simultaneous
- * schedule: [p1 up, p2 up, p1 down, p2 down]).  The iterations are real:
- * state and counters advance as in cfr_iterate. */
+ * schedule: [p1 up, p2 up, p1 down, p2 down]).  Tracing always launches
+ * the two passes of a player separately (load option passes = 2).  The
+ * iterations are real: state and counters advance as in cfr_iterate. */
 int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma,
                            float *host_ms);
 

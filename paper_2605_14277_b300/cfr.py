@@ -29,7 +29,8 @@ class CFRError(RuntimeError):
 
 
 class LoadOptions(ctypes.Structure):
-    _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class TreeDesc(ctypes.Structure):
@@ -136,19 +137,22 @@ class Solver:
     """CFR state of one game or of a batch of games resident on the GPU.
 
     ``Solver(tree)`` loads one game; ``Solver([t1, t2, ...])`` loads a batch
-    advanced together by every launch."""
+    advanced together by every launch.  ``shape``, ``flat`` and ``passes`` are
+    the load options of the C ABI (launch shape, unit layout, one or two
+    launches per player and half-iteration; 0 / False = the library's
+    choice); every choice computes the same iterations."""
 
-    def __init__(self, trees, stream=None, shape: int = 0, flat: bool = False):
+    def __init__(self, trees, stream=None, shape: int = 0, flat: bool = False, passes: int = 0):
         L = lib()
         batch = isinstance(trees, (list, tuple))
         trees = list(trees) if batch else [trees]
         keep = []
         descs = (TreeDesc * len(trees))(*[_desc(t, keep) for t in trees])
         h = ctypes.c_void_p()
-        opts = LoadOptions(int(shape), int(bool(flat)))
+        opts = LoadOptions(int(shape), int(bool(flat)), int(passes))
         _check(L.cfr_load_batch_opts(descs, len(trees), _stream_handle(stream), ctypes.byref(opts), ctypes.byref(h)),
                "cfr_load_batch_opts")
-        self.shape, self.flat = int(shape), bool(flat)
+        self.shape, self.flat, self.passes = int(shape), bool(flat), int(passes)
         self._h = h
         self.n_games = len(trees)
         self.batch = batch

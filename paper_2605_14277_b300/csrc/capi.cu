@@ -180,6 +180,24 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
     launch_exit(P.qup);
 }
 
+// Shared state of the bottom-up and top-down loops of a CTA.
+struct UpSmem {
+    uint64_t bar[2];    // a buffer's own arrays
+    uint64_t cbar[2];   // an internal unit's child ev
+    SLvl lv[2][kMaxStagedLevels];
+    UpTab tab[2][kMaxStagedLevels];
+    ChildEv cev[2];
+    ItemParams ip[2];
+    int cur, nxt, err;
+};
+struct DownSmem {
+    uint64_t bar[2];
+    SLvl lv[2][kMaxStagedLevels];
+    DownTab tab[2][kMaxStagedLevels];
+    ItemParams ip[2];
+    int cur, nxt, err, epoch;
+};
+
 // Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
 // Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take units
 // from the bottom-up queue: every leaf, then the internal units deepest first.
@@ -189,47 +207,41 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
 // staged at once; its children's ev is copied in when its completion count
 // shows all children done (a bounded wait: the children were taken earlier by
 // running CTAs and never wait themselves).  The game's root unit also
-// publishes its next x (xn).
-template <int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB)
-    k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *bufs[2] = {smem, smem + item_bytes};
-    __shared__ __align__(8) uint64_t bar[2];    // a buffer's own arrays
-    __shared__ __align__(8) uint64_t cbar[2];   // an internal unit's child ev
-    __shared__ SLvl lv[2][kMaxStagedLevels];
-    __shared__ UpTab tab[2][kMaxStagedLevels];
-    __shared__ ChildEv cev[2];
-    __shared__ int s_cur, s_nxt, s_err;
-    __shared__ ItemParams s_ip[2];
+// publishes the next x of itself and every internal unit (xn) and, when
+// `root_flag` is nonzero, sets the game's root_done word to it.
+__device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__restrict__ xo, const IterArgs &ia,
+                        unsigned char *const *bufs, UpSmem &S, int root_flag) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_up;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&cbar[0], 1);
-        mbar_init(&cbar[1], 1);
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_init(&S.cbar[0], 1);
+        mbar_init(&S.cbar[1], 1);
         fence_mbar_init();
-        s_cur = atomicAdd(&P.qup[0], 1);
-        s_err = 0;
+        S.cur = atomicAdd(&P.qup[0], 1);
+        S.err = 0;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u}, cph[2] = {0u, 0u};
-    int cur = s_cur, buf = 0;
+    int cur = S.cur, buf = 0;
     // prologue, overlapping the previous kernel: nothing read here is written
     // by it (the other player's x, gathered in compute_up, waits)
     if (warp == 0) {
         if (cur < n) {
             const int4 h = P.upq[2 * cur];
-            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x);
-            if (h.w & kStaged) issue_up(P, h, bufs[0], &bar[0], lv[0], tab[0], &cev[0]);
+            if (tid == 0) S.ip[0] = unit_params(gm, ia, h.x);
+            if (h.w & kStaged) issue_up(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], &S.cev[0]);
         }
-        if (tid == 0) s_nxt = cur < n ? atomicAdd(&P.qup[0], 1) : n;
+        if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qup[0], 1) : n;
     }
     __syncthreads();
-    pdl_trigger();
+    // wait before letting the next kernel start: then at most two kernels of
+    // the stream are resident, and a launch never shares its queue words with
+    // a running one
     pdl_wait();
-    int nxt = s_nxt;
+    pdl_trigger();
+    int nxt = S.nxt;
     int done_par = -1;   // parent of the previous unit, counted by the producer
     while (cur < n) {
         const int4 h = P.upq[2 * cur];
@@ -238,12 +250,12 @@ __global__ void __launch_bounds__(NT, MINB)
         const int2 tr = make_int2(q.y, q.z);
         const bool staged = (h.w & kStaged) != 0, internal = tr.y > 0, root = tr.x < 0;
         if (staged) {
-            if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+            if (warp != 0 && !mbar_wait(&S.bar[buf], ph[buf], P.err)) S.err = 1;
             ph[buf] ^= 1u;
         }
         __syncthreads();
-        if (s_err) break;
-        const ItemParams ip = s_ip[buf];
+        if (S.err) break;
+        const ItemParams ip = S.ip[buf];
         if (warp == 0) {
             // producer: count the previous unit at its parent (its results
             // were written before the barrier above), then the next unit's
@@ -254,30 +266,31 @@ __global__ void __launch_bounds__(NT, MINB)
                     __threadfence();
                     atomicAdd(&P.unit_cnt[done_par], 1);
                 }
-                s_nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
+                S.nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
             }
             if (nxt < n) {
                 const int4 hn = P.upq[2 * nxt];
-                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x);
-                if (hn.w & kStaged) issue_up(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1], &cev[buf ^ 1]);
+                if (tid == 0) S.ip[buf ^ 1] = unit_params(gm, ia, hn.x);
+                if (hn.w & kStaged)
+                    issue_up(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], &S.cev[buf ^ 1]);
             }
         } else if (ip.active) {
             if (internal) {
                 // all children done, then their ev
                 if (tid == 32) {
-                    if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) s_err = 1;
+                    if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) S.err = 1;
                     P.unit_cnt[u] = 0;
-                    if (staged) issue_child_ev(cev[buf], &cbar[buf]);
+                    if (staged) issue_child_ev(S.cev[buf], &S.cbar[buf]);
                 }
                 consumer_sync();
-                if (staged && !s_err) {
-                    if (!mbar_wait(&cbar[buf], cph[buf], P.err)) s_err = 1;
+                if (staged && !S.err) {
+                    if (!mbar_wait(&S.cbar[buf], cph[buf], P.err)) S.err = 1;
                 }
                 if (staged) cph[buf] ^= 1u;
                 consumer_sync();
             }
-            if (staged && !s_err) {
-                compute_up(P, xo, ia, ip, h.y, lv[buf], tab[buf], &cev[buf], internal, root);
+            if (staged && !S.err) {
+                compute_up(P, xo, ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal, root);
                 if (root) {
                     consumer_sync();
                     internal_topdown(P, h.x, kProducerThreads, (int)blockDim.x - kProducerThreads,
@@ -286,8 +299,8 @@ __global__ void __launch_bounds__(NT, MINB)
             }
         }
         __syncthreads();
-        if (s_err) break;
-        const int nxt2 = s_nxt;
+        if (S.err) break;
+        const int nxt2 = S.nxt;
         if (ip.active) {
             if (!staged) {
                 run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
@@ -297,6 +310,12 @@ __global__ void __launch_bounds__(NT, MINB)
                 }
             }
             if (tid == 0 && root && ia.first_of_iter) gm.t_done[h.x] = ip.t;
+        }
+        if (tid == 0 && root && root_flag) {
+            // the game's bottom-up pass is complete: b and xn final (set for
+            // games masked off too, whose top-down units then do nothing)
+            __threadfence();
+            st_release(&P.root_done[h.x], root_flag);
         }
         done_par = ip.active ? tr.x : -1;
         cur = nxt;
@@ -309,6 +328,15 @@ __global__ void __launch_bounds__(NT, MINB)
         __threadfence();
         atomicAdd(&P.unit_cnt[done_par], 1);
     }
+}
+
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_up_staged(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs ia, int item_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *bufs[2] = {smem, smem + item_bytes};
+    __shared__ UpSmem S;
+    up_loop(P, gm, xo, ia, bufs, S, 0);
     launch_exit(P.qup);
 }
 
@@ -333,77 +361,119 @@ __device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParam
 // Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y) and the average
 // xbar += t^gamma x.  Every unit's top-level parents belong to the root or to
 // internal units, whose next x the bottom-up pass published in xn, so the
-// units are independent of one another.
-template <int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *bufs[2] = {smem, smem + item_bytes};
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ SLvl lv[2][kMaxStagedLevels];
-    __shared__ DownTab tab[2][kMaxStagedLevels];
-    __shared__ int s_cur, s_nxt, s_err;
-    __shared__ ItemParams s_ip[2];
+// units are independent of one another.  With `wait_roots` (the loop follows
+// this player's bottom-up loop in the same launch) a unit's b is copied in,
+// and the unit computed, only once its game's root_done word shows the
+// bottom-up pass of that game complete (a bounded wait; the root unit was
+// taken by a running CTA before any top-down unit was).
+__device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, unsigned char *const *bufs,
+                          DownSmem &S, bool wait_roots) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_units;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
         fence_mbar_init();
-        s_cur = atomicAdd(&P.qdn[0], 1);
-        s_err = 0;
+        S.cur = atomicAdd(&P.qdn[0], 1);
+        S.err = 0;
     }
     __syncthreads();
+    const int flag = S.epoch + 1;
     uint32_t ph[2] = {0u, 0u};
-    int cur = s_cur, buf = 0;
-    // prologue, overlapping the previous kernel (this player's up pass): the
-    // first unit's own arrays first; b, the parameters (the iteration counter)
-    // and xn only once that kernel is done
+    int cur = S.cur, buf = 0;
+    // warp 0: the game's bottom-up pass must be complete before b is read;
+    // every lane then acquires the flag itself, since every lane issues copies
+    auto root_ready = [&](int g) {
+        if (!wait_roots) return true;
+        bool ok = true;
+        if ((tid & 31) == 0) ok = flag_wait(&P.root_done[g], flag, P.err);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (ok) ok = ld_acquire(&P.root_done[g]) == flag;
+        return __all_sync(0xffffffffu, ok) != 0;
+    };
+    // prologue, overlapping the previous kernel (or this launch's bottom-up
+    // loop): the first unit's own arrays first; b once that is done
     if (warp == 0) {
         int4 h = make_int4(0, 0, 0, 0);
         uint32_t carried = 0;
         if (cur < n) {
             h = P.downq[2 * cur];
-            if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0], kDownOwn, 0);
+            if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], kDownOwn, 0);
         }
-        if (tid == 0) s_nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
+        if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
         pdl_wait();
         if (cur < n) {
-            if (h.w & kStaged) issue_down(P, h, bufs[0], &bar[0], lv[0], tab[0], kDownB, carried);
-            if (tid == 0) s_ip[0] = unit_params(gm, ia, h.x);
+            if (!root_ready(h.x) && tid == 0) S.err = 1;
+            if (h.w & kStaged) issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], kDownB, carried);
+            if (tid == 0) S.ip[0] = unit_params(gm, ia, h.x);
         }
     }
     __syncthreads();
     pdl_trigger();
     pdl_wait();
-    int nxt = s_nxt;
-    while (cur < n) {
+    int nxt = S.nxt;
+    while (cur < n && !S.err) {
         const int4 h = P.downq[2 * cur];
         const bool staged = (h.w & kStaged) != 0;
         if (staged) {
-            if (warp != 0 && !mbar_wait(&bar[buf], ph[buf], P.err)) s_err = 1;
+            if (warp != 0 && !mbar_wait(&S.bar[buf], ph[buf], P.err)) S.err = 1;
             ph[buf] ^= 1u;
         }
         __syncthreads();
-        if (s_err) break;
-        const ItemParams ip = s_ip[buf];
+        if (S.err) break;
+        const ItemParams ip = S.ip[buf];
         if (warp == 0) {
             if (nxt < n) {
                 const int4 hn = P.downq[2 * nxt];
+                if (!root_ready(hn.x) && tid == 0) S.err = 1;
                 if (hn.w & kStaged)
-                    issue_down(P, hn, bufs[buf ^ 1], &bar[buf ^ 1], lv[buf ^ 1], tab[buf ^ 1], kDownOwn | kDownB, 0);
-                if (tid == 0) s_ip[buf ^ 1] = unit_params(gm, ia, hn.x);
+                    issue_down(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], kDownOwn | kDownB,
+                               0);
+                if (tid == 0) S.ip[buf ^ 1] = unit_params(gm, ia, hn.x);
             }
-            if (tid == 0) s_nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
+            if (tid == 0) S.nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
         } else if (ip.active && staged) {
-            compute_down(P, ia, ip, h.y, lv[buf], tab[buf]);
+            compute_down(P, ia, ip, h.y, S.lv[buf], S.tab[buf]);
         }
         __syncthreads();
-        const int nxt2 = s_nxt;
+        const int nxt2 = S.nxt;
         if (ip.active && !staged) run_down(P, ia, ip, h.y, P.ranges + h.z);
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
     }
+}
+
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames gm, IterArgs ia, int item_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *bufs[2] = {smem, smem + item_bytes};
+    __shared__ DownSmem S;
+    if (threadIdx.x == 0) S.epoch = 0;
+    down_loop(P, gm, ia, bufs, S, false);
+    launch_exit(P.qdn);
+}
+
+// One player's whole half-step in one launch (alternating updates): the
+// bottom-up loop, then, as each CTA runs out of bottom-up units, the top-down
+// loop; a game's top-down units start once that game's root unit is done.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_half_step(DevPlayer P, DevGames gm, const float *__restrict__ xo, IterArgs up_ia, IterArgs dn_ia,
+                int item_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *bufs[2] = {smem, smem + item_bytes};
+    __shared__ UpSmem SU;
+    __shared__ DownSmem SD;
+    // this launch's root flag is the top-down epoch + 1: the previous launch
+    // on these queue words finished before this one started (each pass lets
+    // the next kernel start only after its own wait on the previous one)
+    if (threadIdx.x == 0) SD.epoch = __ldcg(&P.qdn[2]);
+    __syncthreads();
+    up_loop(P, gm, xo, up_ia, bufs, SU, SD.epoch + 1);
+    launch_exit(P.qup);
+    __syncthreads();
+    if (!SU.err) down_loop(P, gm, dn_ia, bufs, SD, true);
     launch_exit(P.qdn);
 }
 
@@ -510,18 +580,18 @@ int set_err_static(int code, const char *m) {
 // barrier waits and copy latency with another's compute.
 using UpFn = void (*)(DevPlayer, DevGames, const float *, IterArgs, int);
 using DownFn = void (*)(DevPlayer, DevGames, IterArgs, int);
+using HalfFn = void (*)(DevPlayer, DevGames, const float *, IterArgs, IterArgs, int);
 struct StagedConfig {
     int threads, ctas_per_sm, item_bytes;
     UpFn up;
     DownFn down;
+    HalfFn half;
 };
+#define CFR_SHAPE(nt, minb, kb) {nt, minb, kb * 1024, k_up_staged<nt, minb>, k_down_staged<nt, minb>, k_half_step<nt, minb>}
 const StagedConfig kConfigs[] = {
-    {512, 1, 96 * 1024, k_up_staged<512, 1>, k_down_staged<512, 1>},
-    {256, 2, 48 * 1024, k_up_staged<256, 2>, k_down_staged<256, 2>},
-    {256, 3, 32 * 1024, k_up_staged<256, 3>, k_down_staged<256, 3>},
-    {512, 2, 48 * 1024, k_up_staged<512, 2>, k_down_staged<512, 2>},
-    {256, 4, 24 * 1024, k_up_staged<256, 4>, k_down_staged<256, 4>},
+    CFR_SHAPE(512, 1, 96), CFR_SHAPE(256, 2, 48), CFR_SHAPE(256, 3, 32), CFR_SHAPE(512, 2, 48), CFR_SHAPE(256, 4, 24),
 };
+#undef CFR_SHAPE
 constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 constexpr int kDefaultConfig = 1;
 
@@ -531,7 +601,7 @@ struct PlayerBuf {
     int32_t *ext_inf = nullptr, *ext_seq0 = nullptr;
     int64_t S = 0, J = 0, n_units = 0, n_up = 0;
     int n_levels = 0;
-    int grid_up = 1, grid_up_br = 1, grid_down = 1;
+    int grid_up = 1, grid_up_br = 1, grid_down = 1, grid_half = 1;
     size_t smem_br = 0;
     std::vector<int32_t> game_J, game_S;
     std::vector<int64_t> game_jbase;
@@ -569,6 +639,7 @@ struct cfr_ctx {
     int64_t dev_bytes = 0, h2d_bytes = 0;
     int cfg = kDefaultConfig;       // staged launch shape (kConfigs)
     bool pdl = true;                // passes may overlap the previous pass's tail (not while profiling)
+    bool split = false;             // alternating schedule: separate bottom-up and top-down launches
     int threads = 256;              // threads of a staged CTA
     int item_bytes = 48 * 1024;     // one staged unit buffer (two per CTA)
     size_t smem_staged = 0;
@@ -686,7 +757,11 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
     const bool pdl0 = pdl && !params;
     const float *x1 = A.d.x, *x2 = B.d.x;
     mark(0);
-    if (alternating) {
+    if (alternating && !c->split && !ev) {
+        const HalfFn half = kConfigs[c->cfg].half;
+        CU(launch_pass(half, A.grid_half, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, dn, ib));
+        CU(launch_pass(half, B.grid_half, nt, sm, c->stream, pdl, B.d, gm, x1, up2, dn, ib));
+    } else if (alternating) {
         CU(launch_pass(up, A.grid_up, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, ib));
         mark(1);
         CU(launch_pass(down, A.grid_down, nt, sm, c->stream, pdl, A.d, gm, dn, ib));
@@ -809,6 +884,8 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     d.qup = ctr + nu;
     d.qdn = ctr + nu + 4;
     d.err = c->err;
+    TRY(dalloc(c, &d.root_done, L.G));
+    CU(cudaMemsetAsync(d.root_done, 0, L.G * sizeof(int32_t), c->stream));
     CU(cudaMemsetAsync(d.r, 0, H.S * sizeof(float2), c->stream));
     CU(cudaMemsetAsync(d.xbar, 0, H.S * sizeof(float2), c->stream));
     CU(cudaMemsetAsync(d.ev, 0, H.J * sizeof(float), c->stream));
@@ -823,6 +900,10 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(occupancy_grid((const void *)cf.up, c->threads, c->smem_staged, B.n_up, &B.grid_up));
     TRY(occupancy_grid((const void *)k_up<MODE_BR>, kThreads, B.smem_br, B.n_up, &B.grid_up_br));
     TRY(occupancy_grid((const void *)cf.down, c->threads, c->smem_staged, B.n_units, &B.grid_down));
+    CU(cudaFuncSetAttribute((const void *)cf.half, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->smem_staged));
+    TRY(occupancy_grid((const void *)cf.half, c->threads, c->smem_staged, std::max(B.n_up, B.n_units),
+                       &B.grid_half));
     k_uniform<<<(unsigned)std::min<int64_t>((H.J + kThreads - 1) / kThreads, 65535), kThreads, 0, c->stream>>>(d,
                                                                                                              H.J);
     CU(cudaGetLastError());
@@ -834,13 +915,16 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     *out = nullptr;
     int shape = kDefaultConfig;
     bool flat = false;
+    int passes = 0;
     if (lo) {
         if (lo->shape < 0 || lo->shape > kNumConfigs) return set_err(CFR_ERR_ARG, "unknown launch shape");
         if (lo->flat != 0 && lo->flat != 1) return set_err(CFR_ERR_ARG, "flat must be 0 or 1");
-        for (int k = 0; k < 6; k++)
+        if (lo->passes < 0 || lo->passes > 2) return set_err(CFR_ERR_ARG, "passes must be 0, 1 or 2");
+        for (int k = 0; k < 5; k++)
             if (lo->reserved[k] != 0) return set_err(CFR_ERR_ARG, "reserved load options must be zero");
         if (lo->shape > 0) shape = lo->shape - 1;
         flat = lo->flat != 0;
+        passes = lo->passes;
     }
     if (!games || n < 1) return set_err(CFR_ERR_ARG, "no games");
     std::vector<TreeView> tv(n);
@@ -889,6 +973,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     c->G = L.G;
     c->Z = L.Z;
     c->cfg = shape;
+    c->split = passes == 2 || (passes == 0 && L.G == 1);
     c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
     // two unit buffers; a unit too large to stage uses its buffer as the

@@ -67,6 +67,9 @@ struct DevPlayer {
     // last CTA to exit a launch; separate words let one pass start while the
     // previous one finishes); err: nonzero once a bounded wait gave up
     int32_t *unit_cnt, *qup, *qdn, *err;
+    // root_done[g]: set by the bottom-up loop of a fused half-step once game
+    // g's root unit has written b and xn (the launch's top-down epoch + 1)
+    int32_t *root_done;
 };
 
 struct ItemParams;

@@ -72,6 +72,9 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void st_release(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 // bounded wait for *flag == want (one thread): false (and the error word set)
 // if it does not happen within kFlagWaitNs
 __device__ __forceinline__ bool flag_wait(const int32_t *flag, int want, int32_t *err) {

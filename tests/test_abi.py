@@ -60,7 +60,8 @@ def test_calls_that_need_no_device(lib):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 def test_load_rejects_bad_arguments_before_device_work(lib):
@@ -72,6 +73,8 @@ def test_load_rejects_bad_arguments_before_device_work(lib):
     bad = _Opts(99, 0)
     assert lib.cfr_load_batch_opts(None, 1, None, ctypes.byref(bad), ctypes.byref(h)) == -6
     bad = _Opts(0, 2)
+    assert lib.cfr_load_batch_opts(None, 1, None, ctypes.byref(bad), ctypes.byref(h)) == -6
+    bad = _Opts(0, 0, 3)
     assert lib.cfr_load_batch_opts(None, 1, None, ctypes.byref(bad), ctypes.byref(h)) == -6
     bad = _Opts(0, 0)
     bad.reserved[3] = 1

@@ -43,17 +43,17 @@ def parity_games():
     }
 
 
-def one_step(cfr, tree, variant, mode, seed, game_in_batch=None):
+def one_step(cfr, tree, variant, mode, seed, game_in_batch=None, **load):
     o = Oracle(tree)
     rng = np.random.default_rng(seed)
     if game_in_batch is None:
-        s = cfr.Solver(tree)
+        s = cfr.Solver(tree, **load)
         gi = 0
     else:
         others, gi = game_in_batch
         trees = list(others)
         trees.insert(gi, tree)
-        s = cfr.Solver(trees)
+        s = cfr.Solver(trees, **load)
     s.set_update_mode(mode)
     for p in (1, 2):
         r, b, xb, t = random_state(o, p, rng)
@@ -90,6 +90,45 @@ def test_one_iteration_inside_a_batch(cfr):
             g_, o_ = out[p]
             assert rel(g_["r"], o_["r"]) <= ONE_STEP_RTOL
             assert rel(g_["xbar"], o_["xbar"]) <= ONE_STEP_RTOL
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_every_launch_choice_matches_oracle(cfr, passes):
+    """Every launch shape x unit layout, with each player's two passes fused
+    into one launch or split into two: one iteration from identical state
+    matches the oracle, for a game alone and inside a batch."""
+    tree = parity_games()["two_chance"]
+    others = [G.sized_random_game(60 + k, 10 ** (2 + k % 3)) for k in range(3)]
+    for shape in range(1, cfr.lib().cfr_num_shapes() + 1):
+        for flat in (False, True):
+            for gib in (None, (others, 1)):
+                o, s, out = one_step(cfr, tree, "dcfr", "alternating", seed=shape, game_in_batch=gib,
+                                     shape=shape, flat=flat, passes=passes)
+                for p in (1, 2):
+                    g_, o_ = out[p]
+                    assert rel(g_["r"], o_["r"]) <= ONE_STEP_RTOL, (shape, flat, p)
+                    assert rel(g_["xbar"], o_["xbar"]) <= ONE_STEP_RTOL, (shape, flat, p)
+                s.close()
+
+
+def test_fused_and_split_passes_are_identical(cfr):
+    """The fused half-step (one launch per player) and the split passes run
+    the same arithmetic on the same units: bit-identical state after many
+    launches, with games masked off part of the time."""
+    trees = [G.sized_random_game(3000 + k, 10 ** (2 + k % 4)) for k in range(6)] + [G.poker_game()]
+    a = cfr.Solver(trees, passes=1)
+    b = cfr.Solver(trees, passes=2)
+    mask = [1, 0, 1, 1, 0, 1, 1]
+    for s in (a, b):
+        s.iterate(70, "pcfr+")
+        s.iterate(65, "pcfr+", active=mask)
+        s.iterate(130, "dcfr")
+    for g in range(len(trees)):
+        for p in (1, 2):
+            x, y = a.get_state(p, game=g), b.get_state(p, game=g)
+            assert x["t"] == y["t"]
+            for k in ("r", "b", "xbar"):
+                assert np.array_equal(x[k], y[k]), (g, p, k)
 
 
 def test_exploitability_fp64_matches_oracle(cfr):
