@@ -188,7 +188,10 @@ struct UpSmem {
     UpTab tab[2][kMaxStagedLevels];
     ChildEv cev[2];
     ItemParams ip[2];
-    int cur, nxt, err;
+    UpPre pre;          // the unit to be issued next
+    BulkCmd cmd[kUpArrays * kMaxStagedLevels];   // the producer's staged copies
+    int unit[2];        // queue position of the unit in each buffer (n: none)
+    int err;
 };
 struct DownSmem {
     uint64_t bar[2];
@@ -219,21 +222,41 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         mbar_init(&S.cbar[0], 1);
         mbar_init(&S.cbar[1], 1);
         fence_mbar_init();
-        S.cur = atomicAdd(&P.qup[0], 1);
         S.err = 0;
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u}, cph[2] = {0u, 0u};
-    int cur = S.cur, buf = 0;
+    int buf = 0;
+    // The producer keeps a pipeline a round deep: the unit in each buffer
+    // (S.unit), the unit to be issued next with everything its issue reads
+    // (S.pre), and the queue position after that (pend, lane 0), whose
+    // fetch was started a round earlier.  A CTA's first three positions are
+    // blockIdx, + grid, + 2 grid (every CTA has work before any has a fourth
+    // unit); later ones come from the queue counter, past those.  Positions
+    // only grow along a CTA's pipeline.
+    const int G3 = 3 * (int)gridDim.x;
+    auto fetch = [&]() { return G3 + atomicAdd(&P.qup[0], 1); };
+    int pend = n;
+    int4 h0 = make_int4(0, 0, 0, 0), q0 = h0;
     // prologue, overlapping the previous kernel: nothing read here is written
-    // by it (the other player's x, gathered in compute_up, waits)
+    // by it (the other player's x waits)
     if (warp == 0) {
-        if (cur < n) {
-            const int4 h = P.upq[2 * cur];
-            if (tid == 0) S.ip[0] = unit_params(gm, ia, h.x);
-            if (h.w & kStaged) issue_up(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], &S.cev[0]);
+        const int p0 = blockIdx.x, p1 = blockIdx.x + gridDim.x;
+        if (tid == 0) pend = blockIdx.x + 2 * gridDim.x;
+        if (p0 < n) {
+            h0 = P.upq[2 * p0];
+            q0 = P.upq[2 * p0 + 1];
+            up_prefetch(P, gm, ia, p0, h0, q0, S.pre);
+            cp_async_wait_all();
+            __syncwarp();
+            if (tid == 0) S.ip[0] = S.pre.ip;
+            if (h0.w & kStaged)
+                issue_up(P, xo, S.pre, bufs[0], &S.bar[0], S.lv[0], S.tab[0], &S.cev[0], S.cmd, true);
         }
-        if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qup[0], 1) : n;
+        if (tid == 0) S.unit[0] = p0 < n ? p0 : n;
+        __syncwarp();
+        if (p1 < n) up_prefetch(P, gm, ia, p1, P.upq[2 * p1], P.upq[2 * p1 + 1], S.pre);
+        else if (tid == 0) S.pre.pos = n;
     }
     __syncthreads();
     // wait before letting the next kernel start: then at most two kernels of
@@ -241,8 +264,10 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
     // a running one
     pdl_wait();
     pdl_trigger();
-    int nxt = S.nxt;
+    // the first unit's x windows (the other player's x is final now)
+    if (warp == 0 && S.unit[0] < n && (h0.w & kStaged)) issue_up_x(P, xo, h0, q0, S.tab[0], &S.bar[0]);
     int done_par = -1;   // parent of the previous unit, counted by the producer
+    int cur = S.unit[0];
     while (cur < n) {
         const int4 h = P.upq[2 * cur];
         const int4 q = P.upq[2 * cur + 1];
@@ -258,22 +283,37 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         const ItemParams ip = S.ip[buf];
         if (warp == 0) {
             // producer: count the previous unit at its parent (its results
-            // were written before the barrier above), then the next unit's
-            // parameters and copies into the other buffer, then the unit after
-            // it from the queue
-            if (tid == 0) {
-                if (done_par >= 0) {
-                    __threadfence();
-                    atomicAdd(&P.unit_cnt[done_par], 1);
-                }
-                S.nxt = nxt < n ? atomicAdd(&P.qup[0], 1) : n;
+            // were written before the barrier above); issue the prefetched
+            // unit into the other buffer; then prefetch the unit after it,
+            // whose queue position came last round, and start fetching the
+            // next position
+            if (tid == 0 && done_par >= 0) {
+                __threadfence();
+                atomicAdd(&P.unit_cnt[done_par], 1);
             }
-            if (nxt < n) {
-                const int4 hn = P.upq[2 * nxt];
-                if (tid == 0) S.ip[buf ^ 1] = unit_params(gm, ia, hn.x);
-                if (hn.w & kStaged)
-                    issue_up(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], &S.cev[buf ^ 1]);
+            // the queue entry of the unit after next (its position came
+            // last round): loaded now, used after the issue below
+            const int p = __shfl_sync(0xffffffffu, pend, 0);
+            int4 hp = make_int4(0, 0, 0, 0), qp = hp;
+            if (p < n) {
+                hp = P.upq[2 * p];
+                qp = P.upq[2 * p + 1];
             }
+            // the next unit, whose records were copied in last round
+            cp_async_wait_all();
+            __syncwarp();
+            const int nx = S.pre.pos;
+            if (nx < n) {
+                if (tid == 0) S.ip[buf ^ 1] = S.pre.ip;
+                if (S.pre.h.w & kStaged)
+                    issue_up(P, xo, S.pre, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1],
+                             &S.cev[buf ^ 1], S.cmd, false);
+            }
+            if (tid == 0) S.unit[buf ^ 1] = nx;
+            __syncwarp();   // S.pre is read: the next one may overwrite it
+            if (tid == 0) pend = p < n ? fetch() : n;
+            if (p < n) up_prefetch(P, gm, ia, p, hp, qp, S.pre);
+            else if (tid == 0) S.pre.pos = n;
         } else if (ip.active) {
             if (internal) {
                 // all children done, then their ev
@@ -290,7 +330,9 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
                 consumer_sync();
             }
             if (staged && !S.err) {
-                compute_up(P, xo, ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal, root);
+                up_gather(xo, h.y, S.lv[buf], S.tab[buf]);
+                compute_up(ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal, root);
+                up_write_back(P, h.y, S.lv[buf], S.tab[buf], root);
                 if (root) {
                     consumer_sync();
                     internal_topdown(P, h.x, kProducerThreads, (int)blockDim.x - kProducerThreads,
@@ -300,7 +342,6 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         }
         __syncthreads();
         if (S.err) break;
-        const int nxt2 = S.nxt;
         if (ip.active) {
             if (!staged) {
                 run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
@@ -318,11 +359,12 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             st_release(&P.root_done[h.x], root_flag);
         }
         done_par = ip.active ? tr.x : -1;
-        cur = nxt;
-        nxt = nxt2;
+        cur = S.unit[buf ^ 1];
         buf ^= 1;
     }
-    // the last unit's count (nothing else of this CTA is pending)
+    // the last unit's count (nothing else of this CTA is pending; records
+    // prefetched for a unit not taken after an error land first)
+    cp_async_wait_all();
     __syncthreads();
     if (tid == 0 && done_par >= 0) {
         __threadfence();
@@ -819,6 +861,12 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     d.m_ptr = p32;
     TRY(upload(c, &p32, H.m_col));
     d.m_col = p32;
+    TRY(upload(c, &p32, H.lcol));
+    d.lcol = p32;
+    TRY(upload(c, &p32, H.rwin));
+    d.rwin = (const int4 *)p32;
+    TRY(upload(c, &p32, H.win));
+    d.win = (const int4 *)p32;
     float *pf;
     TRY(upload(c, &pf, H.m_val));
     d.m_val = pf;
@@ -840,20 +888,28 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     d.unit_tree = p2;
     TRY(upload(c, &p32, H.ranges));
     d.ranges = p32;
-    auto queue = [&](const std::vector<int32_t> &qv, const std::vector<Unit> &units, const int4 **out) {
+    // queue entries: {game, nlvl, rng, flags | x windows << 8}, {unit, parent,
+    // child units, first x window}; a staged up unit's windows are one run
+    auto queue = [&](const std::vector<int32_t> &qv, const std::vector<Unit> &units, bool up, const int4 **out) {
         std::vector<int4> q(2 * qv.size());
         for (size_t k = 0; k < qv.size(); k++) {
             const Unit &u = units[qv[k]];
-            q[2 * k] = make_int4(u.game, u.nlvl, u.rng, u.flags);
-            q[2 * k + 1] = make_int4(qv[k], u.parent, u.nchild, 0);
+            int32_t w0 = 0, nw = 0;
+            if (up && (u.flags & kStaged)) {
+                const int64_t rec = u.rng / kLvl;
+                w0 = H.rwin[4 * rec];
+                nw = H.rwin[4 * (rec + u.nlvl - 1) + 1] - w0;
+            }
+            q[2 * k] = make_int4(u.game, u.nlvl, u.rng, u.flags | (nw << 8));
+            q[2 * k + 1] = make_int4(qv[k], u.parent, u.nchild, w0);
         }
         int4 *pq;
         TRY(upload(c, &pq, q));
         *out = pq;
         return CFR_OK;
     };
-    TRY(queue(H.up_queue, H.units, &d.upq));
-    TRY(queue(H.down_queue, H.dunits, &d.downq));
+    TRY(queue(H.up_queue, H.units, true, &d.upq));
+    TRY(queue(H.down_queue, H.dunits, false, &d.downq));
     TRY(upload(c, &p32, H.game_root));
     d.game_root = p32;
     TRY(upload(c, &p32, H.itd));

@@ -401,6 +401,9 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
         std::vector<int64_t> f(J, 0);   // subtree footprint truncated at a tier's bottom
         P.units.clear();
         P.ranges.clear();
+        P.rwin.clear();
+        P.win.clear();
+        P.lcol = P.m_col;
         P.game_root.assign(G, -1);
         P.game_tiers.assign(G, 0);
         auto push_level = [&](int32_t j0, int32_t j1) {
@@ -411,6 +414,48 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             P.ranges.push_back(s1);
             P.ranges.push_back(P.m_ptr[s0]);
             P.ranges.push_back(P.m_ptr[s1]);
+            for (int k = 0; k < 4; k++) P.rwin.push_back(0);
+        };
+        // x windows of level k of a staged unit (payoff entries [n0, n1)): the
+        // sorted distinct columns cut wherever two are more than kWinGap
+        // apart.  Taken when at most kMaxWin windows together need no more
+        // shared memory than per-entry gathers.
+        std::vector<int32_t> cols;
+        auto windows = [&](int64_t rec, int32_t k, int32_t n0, int32_t n1) {
+            const int32_t here = (int32_t)(P.win.size() / 4);
+            P.rwin[4 * rec] = P.rwin[4 * rec + 1] = here;
+            P.rwin[4 * rec + 2] = (int32_t)work16(n1 - n0, 4);
+            if (n1 <= n0) return;
+            cols.assign(P.m_col.begin() + n0, P.m_col.begin() + n1);
+            std::sort(cols.begin(), cols.end());
+            cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+            std::vector<int32_t> w;
+            int64_t bytes = 0;
+            int32_t a = cols[0];
+            for (size_t k = 1; k <= cols.size(); k++) {
+                if (k == cols.size() || cols[k] - cols[k - 1] > kWinGap) {
+                    w.push_back(a);
+                    w.push_back(cols[k - 1] + 1);
+                    bytes += span16(cols[k - 1] + 1 - a, 4);
+                    if (k < cols.size()) a = cols[k];
+                }
+            }
+            const int64_t nw = (int64_t)w.size() / 2;
+            if (nw > kMaxWin || bytes > work16(n1 - n0, 4)) return;
+            int64_t off = 0;
+            for (int64_t q = 0; q < nw; q++) {
+                for (int32_t v : {w[2 * q], w[2 * q + 1], (int32_t)off, k}) P.win.push_back(v);
+                off += span16(w[2 * q + 1] - w[2 * q], 4);
+            }
+            P.rwin[4 * rec + 1] = here + (int32_t)nw;
+            P.rwin[4 * rec + 2] = (int32_t)bytes;
+            // each entry's float index into the level's x area
+            for (int32_t e = n0; e < n1; e++) {
+                const int32_t c = P.m_col[e];
+                int64_t base = 0, q = 0;
+                while (w[2 * q + 1] <= c) base += span16(w[2 * q + 1] - w[2 * q], 4) / 4, q++;
+                P.lcol[e] = (int32_t)(base + (w[2 * q] & 3) + (c - w[2 * q]));
+            }
         };
         // footprints of the levels [0, below) truncated at `below` (the
         // deepest level also stages one ev per child infoset)
@@ -494,10 +539,18 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                         u.flags |= kInternal;
                         next.push_back({id, lo, hi});
                         for (int32_t v : {lo, hi, 0, 0, 0, 0}) P.ranges.push_back(v);
+                        for (int k = 0; k < 4; k++) P.rwin.push_back(0);
                         fu += span16(hi - lo, 4);
                     }
-                    if (u.nlvl < kMaxStagedLevels && fu <= opt.item_bytes && fd <= opt.item_bytes)
+                    if (u.nlvl < kMaxStagedLevels && fu <= opt.item_bytes && fd <= opt.item_bytes) {
                         u.flags |= kStaged;
+                        // x windows never take more room than the gathers
+                        // the footprint above assumed
+                        for (int32_t k = 0; k < u.nlvl; k++) {
+                            const int32_t *r = &P.ranges[u.rng + kLvl * k];
+                            windows(u.rng / kLvl + k, k, r[4], r[5]);
+                        }
+                    }
                     if (par >= 0) {
                         P.units[par].nchild++;
                         if (P.units[par].parent < 0) u.flags |= kChildOfRoot;

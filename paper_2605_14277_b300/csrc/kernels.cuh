@@ -50,6 +50,12 @@ struct DevPlayer {
     const int4 *upq, *downq;
     const int32_t *ranges, *game_root;
     const int32_t *itd;             // internal ranges below each root: {j0, j1, last of level}
+    // the other player's x for a staged level: per-entry gathers, or copied
+    // windows of it (rwin: {w0, w1, x-area bytes, 0} per range record; win:
+    // {c0, c1, byte offset, level} per window; lcol: the staged columns,
+    // local to the level's x area where it has windows)
+    const int32_t *lcol;
+    const int4 *rwin, *win;
     const int64_t *itd_off;         // [G + 1]
     int32_t n_units, n_up, G;       // n_units: top-down units; n_up: bottom-up queue length
     // state
@@ -220,16 +226,42 @@ __device__ void spmv_ranges(const int32_t *__restrict__ m_ptr, const int32_t *__
 // bottom-up step for one infoset j (MODE_CFR, global memory): counterfactual
 // values, regret update, variant post-op and the next behavioural strategy.
 // ---------------------------------------------------------------------------
-// Branch-free, so the lanes of a warp never split on the sign of r (a zero
-// regret stays zero; only its sign bit may change).
-__device__ __forceinline__ float2 post_op(float2 r, int variant, const ItemParams &ip) {
-    if (variant == VAR_PLUS || variant == VAR_PCFR_PLUS) {
+// The variant's post-op on an updated cumulative regret (Alg. 3: floor at 0;
+// Alg. 4: discount positive regrets by fpos, negative ones by fneg; Alg. 5:
+// floor at 0).  Selects only, so the lanes of a warp never split on the sign
+// of r; VAR is a compile-time constant in the staged passes.
+template <int VAR>
+__device__ __forceinline__ float2 post_op_v(float2 r, float2 fpos, float2 fneg) {
+    if (VAR == VAR_PLUS || VAR == VAR_PCFR_PLUS) {
         r = r.x < 0.f ? make_float2(0.f, 0.f) : r;
-    } else if (variant == VAR_DCFR) {
-        const float2 f = r.x > 0.f ? ip.fpos : (r.x < 0.f ? ip.fneg : make_float2(1.f, 0.f));
+    } else if (VAR == VAR_DCFR) {
+        const float2 f = r.x > 0.f ? fpos : (r.x < 0.f ? fneg : make_float2(1.f, 0.f));
         r = ff_mul(r, f);
     }
     return r;
+}
+__device__ __forceinline__ float2 post_op(float2 r, int variant, const ItemParams &ip) {
+    switch (variant) {
+    case VAR_PLUS: return post_op_v<VAR_PLUS>(r, ip.fpos, ip.fneg);
+    case VAR_DCFR: return post_op_v<VAR_DCFR>(r, ip.fpos, ip.fneg);
+    case VAR_PCFR_PLUS: return post_op_v<VAR_PCFR_PLUS>(r, ip.fpos, ip.fneg);
+    default: return r;
+    }
+}
+
+// Regret matching's normaliser 1/sum(positive regrets): the hardware
+// reciprocal (rcp.approx.f32, within 1 ulp, subnormal inputs kept).  Every
+// path (staged, wide, global) uses this same instruction, so a sequence's
+// strategy does not depend on which path computed it.
+__device__ __forceinline__ float rm_inverse(float pos) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(pos));
+    return r;
+}
+// the uniform probability 1/na, correctly rounded (the constants are the
+// compiler's correctly rounded quotients)
+__device__ __forceinline__ float uniform_prob(int na) {
+    return na <= 2 ? (na == 1 ? 1.f : 0.5f) : (na == 3 ? 1.f / 3.f : (na == 4 ? 0.25f : __frcp_rn((float)na)));
 }
 
 // V[s] = u[s] + ev of each child infoset, added in child order
@@ -262,8 +294,8 @@ __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const Ite
         P.u[s] = q;
         pos += q;
     }
-    const float inv = pos > 0.f ? __frcp_rn(pos) : 0.f;   // = 1/pos correctly rounded
-    const float uni = __frcp_rn((float)na);
+    const float inv = pos > 0.f ? rm_inverse(pos) : 0.f;
+    const float uni = uniform_prob(na);
     for (int s = s0; s < s1; s++) P.b[s] = pos > 0.f ? P.u[s] * inv : uni;
 }
 

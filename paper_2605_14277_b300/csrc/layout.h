@@ -61,17 +61,23 @@ constexpr int kInternal = 2;     // the deepest level's child infosets are other
                                  // kLvl record {c0, c1, 0, 0, 0, 0}
 constexpr int kChildOfRoot = 4;  // the parent is the game's root unit (informational)
 constexpr int kMaxStagedLevels = 24;
+constexpr int32_t kWinGap = 16;   // x windows: columns further apart than this start a new window
+constexpr int64_t kMaxWin = 32;   // x windows: at most this many per staged level
 
 // Shared-memory bytes a staged unit level needs (host and device agree on
 // these): copied ranges get 32 bytes of slack for 16-byte alignment.
 __host__ __device__ inline int64_t span16(int64_t n, int e) { return (n * e + 32 + 15) / 16 * 16; }
 __host__ __device__ inline int64_t work16(int64_t n, int e) { return (n * e + 15) / 16 * 16; }
-__host__ __device__ inline int64_t up_level_bytes(int64_t ns, int64_t ni, int64_t nz) {
+// xb: bytes of the level's x area (the other player's x, per payoff entry
+// when gathered, or as copied windows of it)
+__host__ __device__ inline int64_t up_level_bytes_x(int64_t ns, int64_t ni, int64_t nz, int64_t xb) {
     // r (float2), b, seq_child, payoff row pointers, infoset segments, payoff
-    // columns, payoff values; work: the gathered x of the other player per
-    // payoff entry, V per sequence, ev per infoset
-    return span16(ns, 8) + span16(ns, 4) + 2 * span16(ns + 1, 4) + span16(ni + 1, 4) + 2 * span16(nz, 4) +
-           work16(nz, 4) + work16(ns, 4) + work16(ni, 4);
+    // columns, payoff values; work: the x area, V per sequence, ev per infoset
+    return span16(ns, 8) + span16(ns, 4) + 2 * span16(ns + 1, 4) + span16(ni + 1, 4) + 2 * span16(nz, 4) + xb +
+           work16(ns, 4) + work16(ni, 4);
+}
+__host__ __device__ inline int64_t up_level_bytes(int64_t ns, int64_t ni, int64_t nz) {
+    return up_level_bytes_x(ns, ni, nz, work16(nz, 4));
 }
 __host__ __device__ inline int64_t down_level_bytes(int64_t ns, int64_t ni) {
     // b, x, xbar (float2), infoset parents, infoset segments
@@ -91,6 +97,19 @@ struct PlayerLayout {
     std::vector<double> m_val64;        // [Z]
     std::vector<Unit> units;            // every unit of every game
     std::vector<int32_t> ranges;        // kLvl ints per level of every unit
+    // The other player's x as seen by one staged level's payoff entries: either
+    // gathered per entry, or (when the entries' columns cluster) copied in as
+    // a few contiguous windows [c0, c1) of it, placed one after another in
+    // the level's x area (each span16 bytes, its first column c0 % 4 floats
+    // in).  rwin holds {w0, w1, x-area bytes, 0} per range record (in `ranges`
+    // order); a staged unit's windows are the contiguous run win[w0 of its
+    // first level .. w1 of its last), 4 ints each: {c0, c1, byte offset in
+    // the level's x area, level within the unit}; w0 == w1 means gathered.
+    // lcol is the staged column array: for a windowed level, the entry's
+    // float index into its level's x area; otherwise m_col.
+    std::vector<int32_t> rwin;          // 4 ints per range record
+    std::vector<int32_t> win;           // 4 ints per window
+    std::vector<int32_t> lcol;          // [Z]
     std::vector<int32_t> up_queue;      // leaves largest first, then internal units deepest first
     std::vector<Unit> dunits;           // top-down units: runs of sibling units merged up to the
                                         // buffer (the top-down pass moves ~5x fewer bytes per

@@ -28,11 +28,21 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 // order this thread's (and, through a preceding barrier or acquire, other
 // threads') generic-proxy accesses before its later bulk copies
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// the same for shared memory only: a buffer's earlier generic accesses come
+// before the bulk copies that refill it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
 // global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s_to(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(dst)),
@@ -60,6 +70,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_
 // 4-byte asynchronous global -> shared copy (one gathered element)
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -119,7 +135,8 @@ struct UpTab {
     uint32_t b;     // float strategy
     uint32_t sch, mptr, iseq, col;   // int32 index arrays
     uint32_t val;   // float payoff values
-    uint32_t gx;    // float x of the other player at each payoff entry's column (gathered)
+    uint32_t gx;    // the other player's x: per payoff entry (gathered), or nwin copied windows
+    int32_t nwin;   // 0: gathered per entry
     uint32_t V;     // float counterfactual values, then clipped regrets, then (root) next x
     uint32_t ev;    // float ev per infoset
 };
@@ -190,6 +207,7 @@ __device__ __forceinline__ int64_t level_offset(int64_t bytes) {
 // zero until this arrival adds the total
 __device__ __forceinline__ void arm(uint64_t *bar, uint32_t mine) {
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    __syncwarp();   // the lanes' layout writes (lv, tab) come before the arrival (release)
     if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, mine);
 }
 
@@ -198,61 +216,167 @@ __device__ __forceinline__ void arm(uint64_t *bar, uint32_t mine) {
 // host packer used), a warp scan places the levels one after another, and the
 // lane places and issues the level's arrays one at a time.  For an internal
 // unit lane nl stages the child units' top-level ev.
-__device__ void issue_up(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
-                         UpTab *tab, ChildEv *cev) {
+// One bulk copy global -> shared, as staged by the producer before issue.
+struct BulkCmd {
+    const void *src;
+    uint32_t dst;     // shared address
+    uint32_t bytes;
+};
+constexpr int kUpArrays = 7;   // arrays staged per up level
+
+// What the producer needs to lay out and issue one up unit, copied into
+// shared memory a round before the unit is issued, so that issuing reads no
+// global memory: the queue entry, the unit's parameters, each level's range
+// record and window record, an internal unit's child range, and the unit's
+// first kPreWin x windows.
+constexpr int kPreWin = 64;
+struct __align__(16) UpPre {
+    int4 h, q;            // queue entry: {game, nlvl, rng, flags | nwin << 8}, {unit, parent, nchild, W0}
+    ItemParams ip;
+    int4 xw[kMaxStagedLevels];   // per level: {w0, w1, x-area bytes, 0}
+    int4 win[kPreWin];    // {c0, c1, byte offset, level}
+    SLvl lv[kMaxStagedLevels];
+    int2 child;           // internal unit: the child units' top-level infosets
+    int32_t pos;          // queue position; n: none
+};
+static_assert(sizeof(ItemParams) == 32, "ItemParams is copied as two 16-byte pieces");
+__device__ __forceinline__ int unit_nwin(const int4 h) { return h.w >> 8; }
+
+// Warp 0 (all lanes): start copying the records of the up unit at queue
+// position pos (< n), whose queue entry {h, q} is at hand, into `pre` with
+// asynchronous copies; they land while the producer goes on (the next
+// cp.async.wait_all of these lanes waits for them).  Range records are
+// 8-byte aligned (every record starts at an even int), the others 16.
+__device__ void up_prefetch(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, int pos, int4 h, int4 q,
+                            UpPre &pre) {
     const int lane = threadIdx.x & 31;
-    const int32_t *rng = P.ranges + hdr.z;
+    const int nl = h.y;
+    if (lane < nl) {
+        const int32_t *d = P.ranges + h.z + kLvl * lane;
+        int32_t *o = &pre.lv[lane].j0;
+        cp_async8(o, d);
+        cp_async8(o + 2, d + 2);
+        cp_async8(o + 4, d + 4);
+        cp_async16(&pre.xw[lane], &P.rwin[h.z / kLvl + lane]);
+    } else if (lane == nl && (h.w & kInternal)) {
+        cp_async8(&pre.child, P.ranges + h.z + kLvl * nl);
+    } else if (lane == 30 || lane == 31) {
+        const ItemParams *src = &gm.par[(int64_t)h.x * (kParamSpan + 1) + ia.pslot];
+        cp_async16((char *)&pre.ip + 16 * (lane - 30), (const char *)src + 16 * (lane - 30));
+    }
+    const int nw = min(unit_nwin(h), kPreWin);
+    for (int w = lane; w < nw; w += 32) cp_async16(&pre.win[w], &P.win[q.w + w]);
+    if (lane == 0) {
+        pre.h = h;
+        pre.q = q;
+        pre.pos = pos;
+    }
+}
+
+// Warp 0 (all lanes): the x windows of a staged unit, one window per lane,
+// each into its level's x area at its offset (the layout, tab[k].gx, is this
+// warp's own work, made visible by __syncwarp).  Windows past the prefetched
+// ones come from global memory.  Issues the copies when `issue`; returns this
+// lane's bytes either way.
+__device__ __forceinline__ uint32_t issue_windows(const DevPlayer &P, const float *__restrict__ xo, const int4 h,
+                                                  const int4 q, const int4 *prewin, const UpTab *tab, uint64_t *bar,
+                                                  bool issue) {
+    __syncwarp();
+    uint32_t mine = 0;
+    const int nw = unit_nwin(h);
+    for (int w = (int)(threadIdx.x & 31); w < nw; w += 32) {
+        const int4 d = (prewin && w < kPreWin) ? prewin[w] : P.win[q.w + w];   // {c0, c1, byte offset, level}
+        unsigned char *cur = sh<unsigned char>(tab[d.w].gx) + d.z;
+        uintptr_t dst = 0, src = 0;
+        uint32_t nb = 0;
+        place(cur, xo, d.x, d.y, 4, &dst, &src, &nb);
+        if (issue && nb) bulk_g2s((void *)dst, (const void *)src, nb, bar);
+        mine += nb;
+    }
+    return mine;
+}
+
+// Warp 0: the x windows of a unit laid out by issue_up with `defer_x`, once
+// the other player's x may be read (the previous kernel is done).
+__device__ void issue_up_x(const DevPlayer &P, const float *__restrict__ xo, const int4 h, const int4 q,
+                           const UpTab *tab, uint64_t *bar) {
+    if (unit_nwin(h) > 0) {
+        fence_proxy_async();
+        issue_windows(P, xo, h, q, nullptr, tab, bar, true);
+    }
+}
+
+// Warp 0 (all lanes): lay out the prefetched up unit in buffer `buf` and
+// start its copies.  Lane k < nl owns level k: it sizes the level (the same
+// formula the host packer used), a warp scan places the levels one after
+// another, and the lane places and issues the level's arrays one at a time.
+// For an internal unit lane nl places the child units' top-level ev.
+__device__ void issue_up(const DevPlayer &P, const float *__restrict__ xo, const UpPre &pre, unsigned char *buf,
+                         uint64_t *bar, SLvl *lv, UpTab *tab, ChildEv *cev, BulkCmd *cmd, bool defer_x) {
+    const int lane = threadIdx.x & 31;
+    const int4 hdr = pre.h;
     const int nl = hdr.y;
     const bool internal = (hdr.w & kInternal) != 0;
     SLvl L{0, 0, 0, 0, 0, 0};
     int64_t bytes = 0;
+    int2 xb = make_int2(0, 0);   // x-area bytes, x windows (0: gathered)
     if (lane < nl) {
-        const int32_t *d = rng + kLvl * lane;
-        L = SLvl{d[0], d[1], d[2], d[3], d[4], d[5]};
-        bytes = up_level_bytes(L.s1 - L.s0, L.j1 - L.j0, L.n1 - L.n0);
+        L = pre.lv[lane];
+        const int4 r = pre.xw[lane];
+        xb = make_int2(r.z, r.y - r.x);
+        bytes = up_level_bytes_x(L.s1 - L.s0, L.j1 - L.j0, L.n1 - L.n0, xb.x);
     } else if (internal && lane == nl) {
-        const int32_t *d = rng + kLvl * nl;
-        L = SLvl{d[0], d[1], 0, 0, 0, 0};
+        L = SLvl{pre.child.x, pre.child.y, 0, 0, 0, 0};
         bytes = span16(L.j1 - L.j0, 4);
     }
     unsigned char *cur = buf + level_offset(bytes);
-    fence_proxy_async();
-    uint32_t mine = 0;
-    const bool lvl = lane < nl;
-    if (lvl) lv[lane] = L;
-#pragma unroll 1
-    for (int f = 0; f < 7; f++) {
+    fence_proxy_async_smem();
+    // placement: each level's lane lays out its arrays and stages their
+    // copies as commands
+    if (lane < nl) {
+        lv[lane] = L;
+        UpTab &t = tab[lane];
+        BulkCmd *c = cmd + kUpArrays * lane;
         uintptr_t dst = 0, src = 0;
         uint32_t nb = 0;
-        if (lvl) {
-            UpTab &t = tab[lane];
-            switch (f) {
-            case 0: t.r = sh_off(place(cur, P.r, L.s0, L.s1, 8, &dst, &src, &nb)); break;
-            case 1: t.b = sh_off(place(cur, P.b, L.s0, L.s1, 4, &dst, &src, &nb)); break;
-            case 2: t.sch = sh_off(place(cur, P.seq_child, L.s0, L.s1 + 1, 4, &dst, &src, &nb)); break;
-            case 3: t.mptr = sh_off(place(cur, P.m_ptr, L.s0, L.s1 + 1, 4, &dst, &src, &nb)); break;
-            case 4: t.iseq = sh_off(place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &dst, &src, &nb)); break;
-            case 5: t.col = sh_off(place(cur, P.m_col, L.n0, L.n1, 4, &dst, &src, &nb)); break;
-            default: t.val = sh_off(place(cur, P.m_val, L.n0, L.n1, 4, &dst, &src, &nb)); break;
-            }
-        } else if (f == 0 && internal && lane == nl) {
-            // placed now, copied once the children are done (issue_child_ev)
-            cev->ev = sh_off(place(cur, P.ev, L.j0, L.j1, 4, &dst, &src, &nb));
-            cev->c0 = L.j0;
-            cev->dst = sh_off((const void *)dst);
-            cev->bytes = nb;
-            cev->src = (const void *)src;
-            nb = 0;
-        }
-        mine += issue_copy(dst, src, nb, bar);
-    }
-    if (lvl) {
-        tab[lane].gx = sh_off(cur);
-        cur += work16(L.n1 - L.n0, 4);
-        tab[lane].V = sh_off(cur);
+#define CFR_STAGE(field, arr, a, b, e, f)                                     \
+    t.field = sh_off(place(cur, arr, a, b, e, &dst, &src, &nb));             \
+    c[f] = BulkCmd{(const void *)src, smem_addr((const void *)dst), nb};
+        CFR_STAGE(r, P.r, L.s0, L.s1, 8, 0)
+        CFR_STAGE(b, P.b, L.s0, L.s1, 4, 1)
+        CFR_STAGE(sch, P.seq_child, L.s0, L.s1 + 1, 4, 2)
+        CFR_STAGE(mptr, P.m_ptr, L.s0, L.s1 + 1, 4, 3)
+        CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 4)
+        CFR_STAGE(col, P.lcol, L.n0, L.n1, 4, 5)
+        CFR_STAGE(val, P.m_val, L.n0, L.n1, 4, 6)
+#undef CFR_STAGE
+        t.gx = sh_off(cur);
+        t.nwin = xb.y;
+        cur += xb.x;
+        t.V = sh_off(cur);
         cur += work16(L.s1 - L.s0, 4);
-        tab[lane].ev = sh_off(cur);
+        t.ev = sh_off(cur);
+    } else if (internal && lane == nl) {
+        // placed now, copied once the children are done (issue_child_ev)
+        uintptr_t dst = 0, src = 0;
+        uint32_t nb = 0;
+        cev->ev = sh_off(place(cur, P.ev, L.j0, L.j1, 4, &dst, &src, &nb));
+        cev->c0 = L.j0;
+        cev->dst = sh_off((const void *)dst);
+        cev->bytes = nb;
+        cev->src = (const void *)src;
     }
+    __syncwarp();
+    // issue: one command per lane, all lanes at once (larger copies in
+    // kChunk pieces by their lane)
+    uint32_t mine = 0;
+    for (int k = lane; k < kUpArrays * nl; k += 32) {
+        const BulkCmd c = cmd[k];
+        for (uint32_t o = 0; o < c.bytes; o += kChunk)
+            bulk_g2s_to(c.dst + o, (const char *)c.src + o, min(kChunk, c.bytes - o), bar);
+        mine += c.bytes;
+    }
+    if (unit_nwin(hdr) > 0) mine += issue_windows(P, xo, hdr, pre.q, pre.win, tab, bar, !defer_x);
     arm(bar, mine);
 }
 
@@ -331,115 +455,104 @@ __device__ __forceinline__ UpView view(const UpTab &t) {
                   sh<const int32_t>(t.mptr), sh<const int32_t>(t.iseq), sh<const int32_t>(t.col), sh<float>(t.val)};
 }
 
-// One infoset i with na <= kRegA actions, in registers: V of its sequences
-// (payoff row sum in CSR order, each product rounded before it is added, then
-// the child ev in child order; the actions' loops interleaved), ev, regret
-// update, post-op and regret matching.
-struct LevelIn {
-    const float *val, *gx, *evc;
-    int n0, cj0;
-    float sign;
-    bool kids;
-};
-__device__ __forceinline__ void up_step_reg(const UpView &t, const LevelIn &in, int i, int q0, int na, int variant,
-                                            bool pred, const ItemParams &ip) {
-    float V[kRegA], bb[kRegA], qv[kRegA];
+// The staged bottom-up work of one level is split into phases, each a short
+// chain per thread, so that no thread walks a long data-dependent loop (a
+// shared-memory load is ~30-50 cycles, and a warp waits for its longest lane):
+//   rows:  V[s] = sign * (sum of the payoff products of row s, in CSR order),
+//          one thread per sequence, every level of the unit at once;
+//   kids:  V[s] += ev of each child infoset, in child order, one thread per
+//          sequence (the levels below are done);
+//   step:  one thread per infoset: ev = sum_a b[a] V[a], the regret update and
+//          post-op, regret matching (straight-line code for <= kRegA actions).
+// Every sum runs in the same order as in the global-memory path, so results
+// do not depend on how a game is cut into units.
+template <int VAR>
+__device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int na, float2 fpos, float2 fneg) {
+    float V[kRegA], bb[kRegA];
     float2 rr[kRegA];
-    int e[kRegA], e1[kRegA];
-    int len = 0;
 #pragma unroll
     for (int a = 0; a < kRegA; a++) {
-        V[a] = 0.f;
-        e[a] = e1[a] = 0;
-        if (a < na) {
-            e[a] = t.mptr[q0 + a] - in.n0;
-            e1[a] = t.mptr[q0 + a + 1] - in.n0;
-            len = max(len, e1[a] - e[a]);
-            bb[a] = t.b[q0 + a];
-            rr[a] = t.r[q0 + a];
-        }
-    }
-    for (int k = 0; k < len; k++) {
-#pragma unroll
-        for (int a = 0; a < kRegA; a++)
-            if (e[a] + k < e1[a]) V[a] = __fadd_rn(V[a], __fmul_rn(in.val[e[a] + k], in.gx[e[a] + k]));
-    }
-#pragma unroll
-    for (int a = 0; a < kRegA; a++) V[a] *= in.sign;
-    if (in.kids) {
-        len = 0;
-#pragma unroll
-        for (int a = 0; a < kRegA; a++) {
-            e[a] = e1[a] = 0;
-            if (a < na) {
-                e[a] = t.sch[q0 + a] - in.cj0;
-                e1[a] = t.sch[q0 + a + 1] - in.cj0;
-                len = max(len, e1[a] - e[a]);
-            }
-        }
-        for (int k = 0; k < len; k++) {
-#pragma unroll
-            for (int a = 0; a < kRegA; a++)
-                if (e[a] + k < e1[a]) V[a] += in.evc[e[a] + k];
-        }
+        const int q = q0 + min(a, na - 1);   // past the last action: a repeat, unused
+        V[a] = t.V[q];
+        bb[a] = t.b[q];
+        rr[a] = t.r[q];
     }
     float ev = 0.f;
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
         if (a < na) ev = fmaf(bb[a], V[a], ev);
     t.ev[i] = ev;
-    float pos = 0.f;
+    float pos = 0.f, qv[kRegA];
+#pragma unroll
+    for (int a = 0; a < kRegA; a++) {
+        const float d = V[a] - ev;
+        const float2 r = post_op_v<VAR>(ff_add_f(rr[a], d), fpos, fneg);
+        if (a < na) t.r[q0 + a] = r;
+        const float x = VAR == VAR_PCFR_PLUS ? r.x + d : r.x;
+        qv[a] = (a < na && x > 0.f) ? x : 0.f;
+        pos += qv[a];
+    }
+    const float inv = pos > 0.f ? rm_inverse(pos) : 0.f;
+    const float uni = uniform_prob(na);
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
-        if (a < na) {
-            const float d = V[a] - ev;
-            float2 r = ff_add_f(rr[a], d);
-            r = post_op(r, variant, ip);
-            t.r[q0 + a] = r;
-            const float x = pred ? r.x + d : r.x;
-            qv[a] = x > 0.f ? x : 0.f;
-            pos += qv[a];
-        }
-    const float inv = pos > 0.f ? __frcp_rn(pos) : 0.f;   // = 1/pos correctly rounded
-    const float uni = __frcp_rn((float)na);
-#pragma unroll
-    for (int a = 0; a < kRegA; a++)
-        if (a < na) {
-            t.b[q0 + a] = pos > 0.f ? qv[a] * inv : uni;
-            t.V[q0 + a] = V[a];   // kept for the root's top-down pass (overwritten there)
-        }
+        if (a < na) t.b[q0 + a] = pos > 0.f ? qv[a] * inv : uni;
 }
 
 // the same for infosets with more actions, through shared memory
-__device__ __noinline__ void up_step_wide(UpTab tt, LevelIn in, int i, int q0, int q1, int variant, bool pred,
-                                          ItemParams ip) {
+template <int VAR>
+__device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float2 fpos, float2 fneg) {
     const UpView t = view(tt);
-    for (int q = q0; q < q1; q++) {
-        float acc = 0.f;
-        for (int e = t.mptr[q] - in.n0; e < t.mptr[q + 1] - in.n0; e++)
-            acc = __fadd_rn(acc, __fmul_rn(in.val[e], in.gx[e]));
-        float v = in.sign * acc;
-        if (in.kids)
-            for (int c = t.sch[q] - in.cj0; c < t.sch[q + 1] - in.cj0; c++) v += in.evc[c];
-        t.V[q] = v;
-    }
     float ev = 0.f;
     for (int q = q0; q < q1; q++) ev = fmaf(t.b[q], t.V[q], ev);
     t.ev[i] = ev;
     float pos = 0.f;
     for (int q = q0; q < q1; q++) {
         const float d = t.V[q] - ev;
-        float2 r = ff_add_f(t.r[q], d);
-        r = post_op(r, variant, ip);
+        const float2 r = post_op_v<VAR>(ff_add_f(t.r[q], d), fpos, fneg);
         t.r[q] = r;
-        const float rr = pred ? r.x + d : r.x;
+        const float rr = VAR == VAR_PCFR_PLUS ? r.x + d : r.x;
         const float qq = rr > 0.f ? rr : 0.f;
         t.V[q] = qq;   // V is no longer needed: keep the clipped regret
         pos += qq;
     }
-    const float inv = pos > 0.f ? __frcp_rn(pos) : 0.f;
-    const float uni = __frcp_rn((float)(q1 - q0));
+    const float inv = pos > 0.f ? rm_inverse(pos) : 0.f;
+    const float uni = uniform_prob(q1 - q0);
     for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? t.V[q] * inv : uni;
+}
+
+// the levels of a staged unit, bottom-up, for one variant (the rows are done)
+template <int VAR>
+__device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
+                                          const ChildEv *cev, bool internal) {
+    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
+    const float2 fpos = ip.fpos, fneg = ip.fneg;
+    for (int k = nl - 1; k >= 0; k--) {
+        const SLvl L = lv[k];
+        const UpView t = view(tab[k]);
+        // children of this level: the unit's next level, or (an internal
+        // unit's deepest level) the staged child units' top levels
+        const bool deepest = (k + 1 == nl);
+        if (!deepest || internal) {
+            const float *evc = sh<const float>(deepest ? cev->ev : tab[k + 1].ev);
+            const int cj0 = deepest ? cev->c0 : lv[k + 1].j0;
+            const int ns = L.s1 - L.s0;
+            for (int q = tid; q < ns; q += nt) {
+                float v = t.V[q];
+                const int c1 = t.sch[q + 1] - cj0;
+                for (int c = t.sch[q] - cj0; c < c1; c++) v += evc[c];
+                t.V[q] = v;
+            }
+            consumer_sync();
+        }
+        const int ni = L.j1 - L.j0;
+        for (int i = tid; i < ni; i += nt) {
+            const int q0 = t.iseq[i] - L.s0, q1 = t.iseq[i + 1] - L.s0;
+            if (q1 - q0 <= kRegA) up_step_reg<VAR>(t, i, q0, q1 - q0, fpos, fneg);
+            else up_step_wide<VAR>(tab[k], i, q0, q1, fpos, fneg);
+        }
+        consumer_sync();
+    }
 }
 
 // the root's next x, top-down, into each level's V (no longer needed); level
@@ -471,47 +584,77 @@ __device__ __noinline__ void root_topdown(int nl, const SLvl *lv, const UpTab *t
     }
 }
 
-__device__ void compute_up(const DevPlayer &P, const float *__restrict__ xo, const IterArgs &ia,
-                           const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab, const ChildEv *cev,
-                           bool internal, bool root) {
+// The payoff rows of a staged unit are worked by one consumer thread per
+// sequence, every level of the unit in one numbering (the thread index runs on
+// across levels, so a short level does not idle a round).  f(k, q) is called
+// for level k, sequence q of the level, by the thread that owns it.
+template <class F>
+__device__ __forceinline__ void for_rows(int nl, const SLvl *lv, F &&f) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
-    // the other player's x at every payoff entry's column, gathered with
-    // 4-byte asynchronous copies: every load of the unit in flight at once,
-    // none of them holding a register
+    int off = 0;
     for (int k = 0; k < nl; k++) {
-        const int nz = lv[k].n1 - lv[k].n0;
+        const int ns = lv[k].s1 - lv[k].s0;
+        int q = tid - off;
+        if (q < 0) q += nt;
+        for (; q < ns; q += nt) f(k, q);
+        off = (off + ns) % nt;
+    }
+}
+
+// Up pass of a staged unit, part 1 (consumer warps): the other player's x at
+// every payoff entry's column, gathered with 4-byte asynchronous copies, each
+// row's by the thread that will sum it.  Issued as soon as the unit's arrays
+// are in, which is normally while the previous unit is still being written
+// back, so the gathers' latency is hidden.
+__device__ __forceinline__ void up_gather(const float *__restrict__ xo, int nl, const SLvl *lv, const UpTab *tab) {
+    for_rows(nl, lv, [&](int k, int q) {
+        if (tab[k].nwin) return;   // copied in as windows
+        const int n0 = lv[k].n0;
+        const int32_t *mptr = sh<const int32_t>(tab[k].mptr);
         const int32_t *col = sh<const int32_t>(tab[k].col);
         const uint32_t gx = smem_addr(sh<float>(tab[k].gx));
-#pragma unroll 4
-        for (int e = tid; e < nz; e += nt) cp_async4(gx + 4u * (uint32_t)e, xo + col[e]);
-    }
+        const int e1 = mptr[q + 1] - n0;
+        for (int e = mptr[q] - n0; e < e1; e++) cp_async4(gx + 4u * (uint32_t)e, xo + col[e]);
+    });
+}
+
+// Part 2: the row sums V[s] = sign * sum_e val[e] x[col[e]] (products rounded,
+// then added in CSR order), each by the thread that gathered the row (its
+// own copies are complete, no barrier needed); then the levels bottom-up and,
+// for the game's root unit, its top-down pass into V.
+__device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
+                           const ChildEv *cev, bool internal, bool root) {
     cp_async_wait_all();
-    consumer_sync();
-    const bool pred = (ia.variant == VAR_PCFR_PLUS);
-    for (int k = nl - 1; k >= 0; k--) {
-        const SLvl L = lv[k];
-        const UpView t = view(tab[k]);
-        const int ni = L.j1 - L.j0;
-        // children of this level: the unit's next level, or (an internal
-        // unit's deepest level) the staged child units' top levels
-        const bool deepest = (k + 1 == nl);
-        LevelIn in;
-        in.val = sh<const float>(tab[k].val);
-        in.gx = sh<const float>(tab[k].gx);
-        in.evc = sh<const float>(deepest ? cev->ev : tab[k + 1].ev);
-        in.n0 = L.n0;
-        in.cj0 = deepest ? cev->c0 : lv[k + 1].j0;
-        in.sign = ia.sign;
-        in.kids = !deepest || internal;
-        for (int i = tid; i < ni; i += nt) {
-            const int q0 = t.iseq[i] - L.s0, q1 = t.iseq[i + 1] - L.s0;
-            if (q1 - q0 <= kRegA) up_step_reg(t, in, i, q0, q1 - q0, ia.variant, pred, ip);
-            else up_step_wide(tab[k], in, i, q0, q1, ia.variant, pred, ip);
+    for_rows(nl, lv, [&](int k, int q) {
+        const int n0 = lv[k].n0;
+        const int32_t *mptr = sh<const int32_t>(tab[k].mptr);
+        const float *val = sh<const float>(tab[k].val);
+        const float *gx = sh<const float>(tab[k].gx);
+        float acc = 0.f;
+        const int e1 = mptr[q + 1] - n0;
+        if (tab[k].nwin) {
+            const int32_t *col = sh<const int32_t>(tab[k].col);
+            for (int e = mptr[q] - n0; e < e1; e++) acc = __fadd_rn(acc, __fmul_rn(val[e], gx[col[e]]));
+        } else {
+            for (int e = mptr[q] - n0; e < e1; e++) acc = __fadd_rn(acc, __fmul_rn(val[e], gx[e]));
         }
-        consumer_sync();
+        sh<float>(tab[k].V)[q] = ia.sign * acc;
+    });
+    consumer_sync();
+    switch (ia.variant) {
+    case VAR_PLUS: up_levels<VAR_PLUS>(ip, nl, lv, tab, cev, internal); break;
+    case VAR_DCFR: up_levels<VAR_DCFR>(ip, nl, lv, tab, cev, internal); break;
+    case VAR_PCFR_PLUS: up_levels<VAR_PCFR_PLUS>(ip, nl, lv, tab, cev, internal); break;
+    default: up_levels<VAR_CFR>(ip, nl, lv, tab, cev, internal); break;
     }
     if (root) root_topdown(nl, lv, tab);
-    // write-back (coalesced)
+}
+
+// Part 3: write-back (coalesced): r, b, the top level's ev, and the root
+// unit's next x (xn).
+__device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab,
+                                              bool root) {
+    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
         const UpView t = view(tab[k]);

@@ -55,7 +55,7 @@ class Layout:
         self.pl = {}
         for p in (0, 1):
             d = {}
-            for name in ("inf_seq", "seq_child", "inf_par", "seq_game", "m_ptr", "m_col", "ranges",
+            for name in ("inf_seq", "seq_child", "inf_par", "seq_game", "m_ptr", "m_col", "ranges", "rwin", "win", "lcol",
                          "up_queue", "down_queue", "game_root", "game_tiers", "ext_inf", "ext_seq0", "units", "dunits",
                          "itd"):
                 m = L.probe_i32(h, p, name.encode(), None)

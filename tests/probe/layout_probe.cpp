@@ -51,6 +51,9 @@ int64_t probe_i32(void *h, int p, const char *name, void *out) {
     if (s == "m_ptr") return copy_out(P.m_ptr, out);
     if (s == "m_col") return copy_out(P.m_col, out);
     if (s == "ranges") return copy_out(P.ranges, out);
+    if (s == "rwin") return copy_out(P.rwin, out);
+    if (s == "win") return copy_out(P.win, out);
+    if (s == "lcol") return copy_out(P.lcol, out);
     if (s == "up_queue") return copy_out(P.up_queue, out);
     if (s == "down_queue") return copy_out(P.down_queue, out);
     if (s == "game_root") return copy_out(P.game_root, out);

@@ -7,7 +7,7 @@ import pytest
 
 from oracle.oracle import Oracle
 from paper_2605_14277_b300 import games as G
-from tests.layout_probe import Layout, down_bytes, up_bytes
+from tests.layout_probe import Layout, down_bytes, span16, up_bytes, work16
 from tests.refimpl import SeqForm
 
 
@@ -354,3 +354,54 @@ def test_schedule_matches_oracle_one_iteration(variant, alt):
             assert np.allclose(st[p]["b"][f], os_["b"], rtol=1e-12, atol=1e-12)
             assert np.allclose(st[p]["xbar"][f], os_["xbar"][1:], rtol=1e-12, atol=1e-12)
             assert abs(st[p]["xbar"][g] - os_["xbar"][0]) < 1e-12
+
+
+def check_windows(lay):
+    """x windows: for every windowed level, the windows are ordered, disjoint,
+    more than the gap apart, few, no larger than per-entry gathers, and each
+    entry's local column points at its own column once the windows are laid
+    out one after another (each at its 16-byte-aligned offset)"""
+    n_win = n_all = 0
+    for p in (0, 1):
+        d = lay.pl[p]
+        rng, rwin, win, lcol, col = d["ranges"], d["rwin"], d["win"], d["lcol"], d["m_col"]
+        assert rwin.shape[0] == 4 * (rng.shape[0] // 6) and lcol.shape == col.shape
+        win = win.reshape(-1, 4)
+        windowed = np.zeros(col.shape[0], bool)
+        for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["units"]:
+            if flags & 1:
+                # the unit's windows are one contiguous run, level by level
+                recs = [r0 // 6 + k for k in range(nlvl)]
+                for a, b in zip(recs[:-1], recs[1:]):
+                    assert rwin[4 * a + 1] == rwin[4 * b]
+            for k in range(nlvl):
+                rec = r0 // 6 + k
+                w0, w1, xb = rwin[4 * rec: 4 * rec + 3]
+                n0, n1 = rng[r0 + 6 * k + 4], rng[r0 + 6 * k + 5]
+                n_all += n1 - n0
+                if w0 == w1:
+                    assert xb == (work16(n1 - n0, 4) if flags & 1 else 0)
+                    continue
+                assert flags & 1, "only staged units carry windows"
+                n_win += n1 - n0
+                W = win[w0:w1]
+                assert len(W) <= 32 and (W[:, 1] > W[:, 0]).all() and (W[:, 3] == k).all()
+                assert (W[1:, 0] - W[:-1, 1] >= 16).all()
+                sizes = [span16(c1 - c0, 4) for c0, c1 in W[:, :2]]
+                assert sum(sizes) == xb <= work16(n1 - n0, 4)
+                assert (W[:, 2] == np.concatenate([[0], np.cumsum(sizes)[:-1]])).all()
+                smem = np.full(xb // 4, -1, np.int64)
+                for c0, c1, off, _ in W:
+                    smem[off // 4 + (c0 & 3): off // 4 + (c0 & 3) + (c1 - c0)] = np.arange(c0, c1)
+                assert (smem[lcol[n0:n1]] == col[n0:n1]).all()
+                windowed[n0:n1] = True
+        assert (lcol[~windowed] == col[~windowed]).all()
+    return n_win, n_all
+
+
+def test_x_windows():
+    t = G.random_game(11, depth=9, chance={0: 4, 4: 3}, actions=(3, 4), payoff="normal")
+    n_win, n_all = check_windows(Layout([t], item_bytes=48 * 1024))
+    assert n_win >= 0.4 * n_all
+    for trees in (small_set(), [G.poker_game()]):
+        check_windows(Layout(trees, item_bytes=48 * 1024))
