@@ -197,6 +197,7 @@ struct DownSmem {
     uint64_t bar[2];
     SLvl lv[2][kMaxStagedLevels];
     DownTab tab[2][kMaxStagedLevels];
+    BulkCmd cmd[kDownArrays * kMaxStagedLevels];   // the producer's staged copies
     ItemParams ip[2];
     int cur, nxt, err, epoch;
 };
@@ -440,13 +441,13 @@ __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
         uint32_t carried = 0;
         if (cur < n) {
             h = P.downq[2 * cur];
-            if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], kDownOwn, 0);
+            if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownOwn, 0);
         }
         if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
         pdl_wait();
         if (cur < n) {
             if (!root_ready(h.x) && tid == 0) S.err = 1;
-            if (h.w & kStaged) issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], kDownB, carried);
+            if (h.w & kStaged) issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownB, carried);
             if (tid == 0) S.ip[0] = unit_params(gm, ia, h.x);
         }
     }
@@ -469,8 +470,8 @@ __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
                 const int4 hn = P.downq[2 * nxt];
                 if (!root_ready(hn.x) && tid == 0) S.err = 1;
                 if (hn.w & kStaged)
-                    issue_down(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], kDownOwn | kDownB,
-                               0);
+                    issue_down(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], S.cmd,
+                               kDownOwn | kDownB, 0);
                 if (tid == 0) S.ip[buf ^ 1] = unit_params(gm, ia, hn.x);
             }
             if (tid == 0) S.nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;

@@ -629,6 +629,17 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 int32_t nl = 0;
                 for (int64_t k = a; k < b; k++) nl = std::max(nl, P.units[k].nlvl);
                 int64_t fd = 0;
+                // the top level's parent sequences (one contiguous range: the
+                // infosets are sorted by parent), whose next x the top-down
+                // pass stages with the unit, as {ps0, ps1} in the first
+                // level's window record; none for the games' roots
+                int32_t ps0 = 0, ps1 = 0;
+                if (lo < hi && P.inf_par[lo] >= 0) {
+                    ps0 = P.inf_par[lo];
+                    ps1 = P.inf_par[hi - 1] + 1;
+                    fd += span16(ps1 - ps0, 4);
+                }
+                const int64_t rec0 = d.rng / kLvl;
                 for (int32_t k = 0; k < nl && lo < hi; k++) {
                     push_level(lo, hi);
                     const int32_t slo = P.inf_seq[lo], shi = P.inf_seq[hi];
@@ -636,6 +647,10 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                     d.nlvl++;
                     lo = P.seq_child[slo];
                     hi = P.seq_child[shi];
+                }
+                if (d.nlvl > 0) {
+                    P.rwin[4 * rec0] = ps0;
+                    P.rwin[4 * rec0 + 1] = ps1;
                 }
                 if (d.nlvl < kMaxStagedLevels && fd <= opt.item_bytes) d.flags |= kStaged;
                 const int32_t up_par = f.parent;
@@ -656,13 +671,20 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 }
                 return fd;
             };
+            // the staged parent x of merged siblings [a, k]: their top levels'
+            // parent range, from the first's first parent to k's last
+            auto parent_bytes = [&](int64_t a, int64_t k) -> int64_t {
+                const int32_t lo = P.ranges[P.units[a].rng], hi = P.ranges[P.units[k].rng + 1];
+                if (lo >= hi || P.inf_par[lo] < 0) return 0;
+                return span16(P.inf_par[hi - 1] + 1 - P.inf_par[lo], 4);
+            };
             int64_t a = 0, acc = 0;
             for (int64_t k = 0; k < nu0; k++) {
                 const Unit &u = P.units[k];
                 const int64_t fk = fdown(u);
                 const bool same = k > a && u.game == P.units[a].game && u.parent == P.units[a].parent &&
                                   u.parent >= 0 && u.lvl0 == P.units[a].lvl0;
-                if (!same || acc + fk > opt.item_bytes) {
+                if (!same || acc + fk + parent_bytes(a, k) > opt.item_bytes) {
                     if (k > a) build(a, k);
                     a = k;
                     acc = 0;

@@ -107,6 +107,9 @@ struct PlayerLayout {
     // the level's x area, level within the unit}; w0 == w1 means gathered.
     // lcol is the staged column array: for a windowed level, the entry's
     // float index into its level's x area; otherwise m_col.
+    // For a top-down unit's first level the record holds instead {ps0, ps1,
+    // 0, 0}: the parent sequences [ps0, ps1) of its infosets (empty for the
+    // games' roots), whose next x is staged with the unit.
     std::vector<int32_t> rwin;          // 4 ints per range record
     std::vector<int32_t> win;           // 4 ints per window
     std::vector<int32_t> lcol;          // [Z]

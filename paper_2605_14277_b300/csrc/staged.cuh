@@ -144,7 +144,10 @@ struct DownTab {
     uint32_t b, x;  // float
     uint32_t xbar;  // float2
     uint32_t ipar, iseq;
+    uint32_t xp;    // first level: next x of the parent sequences [ps0, ps1)
+    int32_t ps0;
 };
+constexpr int kDownArrays = 6;   // commands staged per top-down level
 // an internal unit's staged child values: ev of infosets [c0, c1), brought in
 // by one bulk copy (dst, src, bytes) once all its children are done
 struct ChildEv {
@@ -395,38 +398,56 @@ __device__ __forceinline__ void issue_child_ev(const ChildEv &c, uint64_t *bar) 
 // its own bytes; the return value is this lane's bytes when b is not issued.
 constexpr int kDownOwn = 1, kDownB = 2;
 __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
-                               DownTab *tab, int what, uint32_t carried) {
+                               DownTab *tab, BulkCmd *cmd, int what, uint32_t carried) {
     const int lane = threadIdx.x & 31;
     const int32_t *rng = P.ranges + hdr.z;
     const int nl = hdr.y;
     SLvl L{0, 0, 0, 0, 0, 0};
     int64_t bytes = 0;
+    int4 pr = make_int4(0, 0, 0, 0);   // first level: {ps0, ps1, 0, 0}
     if (lane < nl) {
         const int32_t *d = rng + kLvl * lane;
         L = SLvl{d[0], d[1], d[2], d[3], d[4], d[5]};
         bytes = down_level_bytes(L.s1 - L.s0, L.j1 - L.j0);
+        if (lane == 0) {
+            pr = P.rwin[hdr.z / kLvl];
+            if (pr.y > pr.x) bytes += span16(pr.y - pr.x, 4);
+        }
     }
     unsigned char *cur = buf + level_offset(bytes);
     fence_proxy_async();
-    uint32_t mine = carried;
-    const bool lvl = lane < nl;
-    if (lvl) lv[lane] = L;
-#pragma unroll 1
-    for (int f = 0; f < 5; f++) {
+    // placement by each level's lane, copies staged as commands (a command
+    // of the other phase is staged with no bytes)
+    if (lane < nl) {
+        lv[lane] = L;
+        DownTab &t = tab[lane];
+        BulkCmd *c = cmd + kDownArrays * lane;
         uintptr_t dst = 0, src = 0;
         uint32_t nb = 0;
-        if (lvl) {
-            DownTab &t = tab[lane];
-            switch (f) {
-            case 0: t.b = sh_off(place(cur, P.b, L.s0, L.s1, 4, &dst, &src, &nb)); break;
-            case 1: t.x = sh_off(place(cur, P.x, L.s0, L.s1, 4, &dst, &src, &nb)); break;
-            case 2: t.xbar = sh_off(place(cur, P.xbar, L.s0, L.s1, 8, &dst, &src, &nb)); break;
-            case 3: t.ipar = sh_off(place(cur, P.inf_par, L.j0, L.j1, 4, &dst, &src, &nb)); break;
-            default: t.iseq = sh_off(place(cur, P.inf_seq, L.j0, L.j1 + 1, 4, &dst, &src, &nb)); break;
-            }
+        const bool own = (what & kDownOwn) != 0, late = (what & kDownB) != 0;
+#define CFR_STAGE(field, arr, a, b, e, f, on)                                    \
+    t.field = sh_off(place(cur, arr, a, b, e, &dst, &src, &nb));                \
+    c[f] = BulkCmd{(const void *)src, smem_addr((const void *)dst), (on) ? nb : 0u};
+        CFR_STAGE(b, P.b, L.s0, L.s1, 4, 0, late)
+        CFR_STAGE(x, P.x, L.s0, L.s1, 4, 1, own)
+        CFR_STAGE(xbar, P.xbar, L.s0, L.s1, 8, 2, own)
+        CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 3, own)
+        CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 4, own)
+        if (lane == 0 && pr.y > pr.x) {
+            CFR_STAGE(xp, P.xn, pr.x, pr.y, 4, 5, late)
+        } else {
+            c[5] = BulkCmd{nullptr, 0u, 0u};
         }
-        if (!(what & (f == 0 ? kDownB : kDownOwn))) nb = 0;
-        mine += issue_copy(dst, src, nb, bar);
+#undef CFR_STAGE
+        t.ps0 = pr.x;
+    }
+    __syncwarp();
+    uint32_t mine = carried;
+    for (int k = lane; k < kDownArrays * nl; k += 32) {
+        const BulkCmd c = cmd[k];
+        for (uint32_t o = 0; o < c.bytes; o += kChunk)
+            bulk_g2s_to(c.dst + o, (const char *)c.src + o, min(kChunk, c.bytes - o), bar);
+        mine += c.bytes;
     }
     if (what & kDownB) {
         arm(bar, mine);
@@ -521,6 +542,23 @@ __device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float
     for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? t.V[q] * inv : uni;
 }
 
+// Ordered sums over a short index range, four terms per step: the four
+// terms' loads are issued together (indices past the end are clamped, their
+// terms skipped), then added in index order, so the result is that of the
+// plain left-to-right loop.  term(i) returns the i-th term.
+template <class T>
+__device__ __forceinline__ float ordered_sum(float acc, int i0, int i1, T &&term) {
+    for (int i = i0; i < i1; i += 4) {
+        float t[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) t[k] = term(min(i + k, i1 - 1));
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (i + k < i1) acc = __fadd_rn(acc, t[k]);
+    }
+    return acc;
+}
+
 // the levels of a staged unit, bottom-up, for one variant (the rows are done)
 template <int VAR>
 __device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
@@ -537,12 +575,8 @@ __device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SL
             const float *evc = sh<const float>(deepest ? cev->ev : tab[k + 1].ev);
             const int cj0 = deepest ? cev->c0 : lv[k + 1].j0;
             const int ns = L.s1 - L.s0;
-            for (int q = tid; q < ns; q += nt) {
-                float v = t.V[q];
-                const int c1 = t.sch[q + 1] - cj0;
-                for (int c = t.sch[q] - cj0; c < c1; c++) v += evc[c];
-                t.V[q] = v;
-            }
+            for (int q = tid; q < ns; q += nt)
+                t.V[q] = ordered_sum(t.V[q], t.sch[q] - cj0, t.sch[q + 1] - cj0, [&](int c) { return evc[c]; });
             consumer_sync();
         }
         const int ni = L.j1 - L.j0;
@@ -630,13 +664,13 @@ __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, con
         const int32_t *mptr = sh<const int32_t>(tab[k].mptr);
         const float *val = sh<const float>(tab[k].val);
         const float *gx = sh<const float>(tab[k].gx);
-        float acc = 0.f;
-        const int e1 = mptr[q + 1] - n0;
+        const int e0 = mptr[q] - n0, e1 = mptr[q + 1] - n0;
+        float acc;
         if (tab[k].nwin) {
             const int32_t *col = sh<const int32_t>(tab[k].col);
-            for (int e = mptr[q] - n0; e < e1; e++) acc = __fadd_rn(acc, __fmul_rn(val[e], gx[col[e]]));
+            acc = ordered_sum(0.f, e0, e1, [&](int e) { return __fmul_rn(val[e], gx[col[e]]); });
         } else {
-            for (int e = mptr[q] - n0; e < e1; e++) acc = __fadd_rn(acc, __fmul_rn(val[e], gx[e]));
+            acc = ordered_sum(0.f, e0, e1, [&](int e) { return __fmul_rn(val[e], gx[e]); });
         }
         sh<float>(tab[k].V)[q] = ia.sign * acc;
     });
@@ -680,7 +714,6 @@ __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemP
                              const DownTab *tab) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     const bool avg = ia.average != 0;
-    const float *xtop = P.xn;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
         const DownTab t = tab[k];
@@ -689,14 +722,31 @@ __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemP
         float2 *xbar = sh<float2>(t.xbar);
         const int32_t *ipar = sh<const int32_t>(t.ipar), *iseq = sh<const int32_t>(t.iseq);
         const int ni = L.j1 - L.j0;
-        const int ps0 = (k > 0) ? lv[k - 1].s0 : 0;
-        const float *xpar = (k > 0) ? sh<const float>(tab[k - 1].x) : nullptr;
+        // parents' x: the level above, or (the first level) the staged next
+        // x of the parent sequences
+        const int ps0 = (k > 0) ? lv[k - 1].s0 : t.ps0;
+        const float *xpar = sh<const float>((k > 0) ? tab[k - 1].x : t.xp);
         for (int i = tid; i < ni; i += nt) {
             const int par = ipar[i];
-            const float xp = par < 0 ? 1.f : (k == 0 ? __ldcg(&xtop[par]) : xpar[par - ps0]);
-            for (int q = iseq[i] - L.s0; q < iseq[i + 1] - L.s0; q++) {
-                if (avg) xbar[q] = ff_add(xbar[q], ff_mul_f(ip.w, x[q]));
-                x[q] = xp * b[q];
+            const float xp = par < 0 ? 1.f : xpar[par - ps0];
+            // the infoset's sequences four at a time, loads first
+            const int q1 = iseq[i + 1] - L.s0;
+            for (int q = iseq[i] - L.s0; q < q1; q += 4) {
+                float xo[4], bb[4];
+                float2 xa[4];
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const int qa = min(q + a, q1 - 1);
+                    xo[a] = x[qa];
+                    bb[a] = b[qa];
+                    xa[a] = avg ? xbar[qa] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+                    if (q + a < q1) {
+                        if (avg) xbar[q + a] = ff_add(xa[a], ff_mul_f(ip.w, xo[a]));
+                        x[q + a] = xp * bb[a];
+                    }
             }
         }
         consumer_sync();

@@ -176,6 +176,15 @@ def test_staged_units_fit_their_buffer():
             for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["dunits"]:
                 rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
                 fd = sum(down_bytes(s1 - s0, j1 - j0) for j0, j1, s0, s1, n0, n1 in rng)
+                # the top level's parent sequences, staged with the unit
+                ps0, ps1 = d["rwin"][4 * (r0 // 6): 4 * (r0 // 6) + 2]
+                j0, j1 = rng[0, :2]
+                parents = d["inf_par"][j0:j1]
+                if parents[0] < 0:
+                    assert (parents < 0).all() and ps0 == ps1 == 0
+                else:
+                    assert ps0 == parents.min() and ps1 == parents.max() + 1
+                    fd += span16(ps1 - ps0, 4)
                 if flags & 1:
                     assert fd <= item_bytes and nlvl <= 24
             for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["units"]:
