@@ -99,10 +99,9 @@ int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_strea
  *          top of each game; 0 = several levels per unit (default).
  *   passes: how the alternating schedule launches one player's bottom-up
  *          and top-down passes.  1 = one kernel, in which the top-down units
- *          of a game start as soon as that game's bottom-up pass is complete
- *          (pays off when the games of a batch finish at different times);
- *          2 = two kernels; 0 = the library's choice (one kernel when more
- *          than one game is loaded, two for a single game).
+ *          of a game start as soon as that game's bottom-up pass is complete;
+ *          2 = two kernels; 0 = the library's choice (two kernels, the faster
+ *          on the workloads measured).
  *   reserved: must be zero.
  * Every choice computes the same iteration; they differ only in speed (see
  * the autotuner in the Python package). */

@@ -43,6 +43,22 @@ __device__ __forceinline__ void launch_exit(int32_t *q) {
     }
 }
 
+// the same for the bottom-up queue and the average pass's queue at once (one
+// exit count, kept in q[1]; both epochs advance)
+__device__ __forceinline__ void launch_exit2(int32_t *q, int32_t *qa) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&q[1], 1) == (int)gridDim.x - 1) {
+            q[0] = 0;
+            q[1] = 0;
+            qa[0] = 0;
+            __threadfence();
+            atomicAdd(&qa[2], 1);
+            atomicAdd(&q[2], 1);
+        }
+    }
+}
+
 // Programmatic dependent launch: a pass may start while the previous kernel
 // on the stream finishes.  pdl_wait blocks until that kernel has completed and
 // its memory is visible (it returns at once for an ordinary launch);
@@ -178,6 +194,58 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         if (threadIdx.x == 0 && tr.x < 0 && MODE == MODE_BR) gm.br[d.x] = __ldcg(&P.ev64[d.x]);
     }
     launch_exit(P.qup);
+}
+
+// The average strategy's update xbar += t^gamma x for the strategy x about to
+// be replaced (Alg. 2; the weights of Alg. 3-5), every sequence of games that
+// are advanced.  It needs only x and the iteration counter, so the bottom-up
+// pass's CTAs run it once they run out of units, while the last units finish
+// (the top-down pass, which overwrites x, comes after).  Chunks of kAvgChunk
+// sequences are taken from a queue; the last CTA to leave resets it.
+constexpr int kAvgChunk = 1024;
+constexpr int kAvgU = 4;   // sequences per thread with loads in flight together
+__device__ void average_pass(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, int64_t S) {
+    __shared__ int s_chunk;
+    const int64_t nch = (S + kAvgChunk - 1) / kAvgChunk;
+    // one game: its parameters once (the sequences of several games are
+    // interleaved level by level, so a batch looks them up per sequence,
+    // cached per thread)
+    const bool one = P.G == 1;
+    ItemParams ip = unit_params(gm, ia, 0);
+    int g = 0;
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&P.qavg[0], 1);
+    for (;;) {
+        __syncthreads();
+        const int64_t c = s_chunk;
+        if (c >= nch) break;
+        __syncthreads();   // s_chunk is read: the next fetch (its result lands while this chunk is worked)
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(&P.qavg[0], 1);
+        const int64_t q0 = c * kAvgChunk, q1 = min((int64_t)S, q0 + kAvgChunk);
+        for (int64_t q = q0 + threadIdx.x; q < q1; q += kAvgU * blockDim.x) {
+            float xv[kAvgU];
+            float2 xb[kAvgU];
+            int gq[kAvgU];
+#pragma unroll
+            for (int u = 0; u < kAvgU; u++) {
+                const int64_t s = min(q + u * (int64_t)blockDim.x, q1 - 1);
+                xv[u] = P.x[s];
+                xb[u] = P.xbar[s];
+                gq[u] = one ? g : P.seq_game[s];
+            }
+#pragma unroll
+            for (int u = 0; u < kAvgU; u++) {
+                const int64_t s = q + u * (int64_t)blockDim.x;
+                if (s >= q1) break;
+                if (gq[u] != g) {   // a chunk across games: per-thread cache
+                    g = gq[u];
+                    ip = unit_params(gm, ia, g);
+                }
+                if (ip.active) P.xbar[s] = ff_add(xb[u], ff_mul_f(ip.w, xv[u]));
+            }
+        }
+        if (threadIdx.x == 0) s_chunk = next;
+    }
 }
 
 // Shared state of the bottom-up and top-down loops of a CTA.
@@ -380,29 +448,29 @@ __global__ void __launch_bounds__(NT, MINB)
     unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ UpSmem S;
     up_loop(P, gm, xo, ia, bufs, S, 0);
-    launch_exit(P.qup);
+    if (ia.average) average_pass(P, gm, ia, P.S);
+    __syncthreads();
+    launch_exit2(P.qup, P.qavg);
 }
 
 // one unit top-down from global memory (units too large to stage); the top
 // level's parents' next x is in xn
-__device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nlvl, const int32_t *rng) {
-    const bool avg = ia.average != 0;
+__device__ void run_down(const DevPlayer &P, int nlvl, const int32_t *rng) {
     for (int k = 0; k < nlvl; k++) {
         const float *xpar = (k == 0) ? P.xn : P.x;
         for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
             const int par = P.inf_par[j];
             const float xp = par < 0 ? 1.f : __ldcg(&xpar[par]);
-            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) {
-                if (avg) P.xbar[s] = ff_add(P.xbar[s], ff_mul_f(ip.w, P.x[s]));
-                P.x[s] = xp * P.b[s];
-            }
+            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) P.x[s] = xp * P.b[s];
         }
         __syncthreads();
     }
 }
 
-// Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y) and the average
-// xbar += t^gamma x.  Every unit's top-level parents belong to the root or to
+
+// Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y; the average
+// xbar += t^gamma x was done by the bottom-up pass's CTAs before).  Every
+// unit's top-level parents belong to the root or to
 // internal units, whose next x the bottom-up pass published in xn, so the
 // units are independent of one another.  With `wait_roots` (the loop follows
 // this player's bottom-up loop in the same launch) a unit's b is copied in,
@@ -410,7 +478,7 @@ __device__ void run_down(const DevPlayer &P, const IterArgs &ia, const ItemParam
 // bottom-up pass of that game complete (a bounded wait; the root unit was
 // taken by a running CTA before any top-down unit was).
 __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, unsigned char *const *bufs,
-                          DownSmem &S, bool wait_roots) {
+                          DownSmem &S, bool wait_roots, int avg_flag = 0) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_units;
     if (tid == 0) {
@@ -426,10 +494,12 @@ __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
     int cur = S.cur, buf = 0;
     // warp 0: the game's bottom-up pass must be complete before b is read;
     // every lane then acquires the flag itself, since every lane issues copies
+    bool avg_seen = avg_flag == 0;
     auto root_ready = [&](int g) {
         if (!wait_roots) return true;
         bool ok = true;
-        if ((tid & 31) == 0) ok = flag_wait(&P.root_done[g], flag, P.err);
+        if ((tid & 31) == 0 && !avg_seen) ok = avg_seen = flag_wait(&P.qavg[2], avg_flag, P.err);
+        if ((tid & 31) == 0 && ok) ok = flag_wait(&P.root_done[g], flag, P.err);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (ok) ok = ld_acquire(&P.root_done[g]) == flag;
         return __all_sync(0xffffffffu, ok) != 0;
@@ -476,11 +546,11 @@ __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
             }
             if (tid == 0) S.nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
         } else if (ip.active && staged) {
-            compute_down(P, ia, ip, h.y, S.lv[buf], S.tab[buf]);
+            compute_down(P, h.y, S.lv[buf], S.tab[buf]);
         }
         __syncthreads();
         const int nxt2 = S.nxt;
-        if (ip.active && !staged) run_down(P, ia, ip, h.y, P.ranges + h.z);
+        if (ip.active && !staged) run_down(P, h.y, P.ranges + h.z);
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
@@ -511,12 +581,20 @@ __global__ void __launch_bounds__(NT, MINB)
     // this launch's root flag is the top-down epoch + 1: the previous launch
     // on these queue words finished before this one started (each pass lets
     // the next kernel start only after its own wait on the previous one)
-    if (threadIdx.x == 0) SD.epoch = __ldcg(&P.qdn[2]);
+    // likewise the average pass's: the top-down loop overwrites x only once
+    // every CTA has left the average pass
+    __shared__ int s_avg;
+    if (threadIdx.x == 0) {
+        SD.epoch = __ldcg(&P.qdn[2]);
+        s_avg = __ldcg(&P.qavg[2]) + 1;
+    }
     __syncthreads();
     up_loop(P, gm, xo, up_ia, bufs, SU, SD.epoch + 1);
-    launch_exit(P.qup);
+    if (up_ia.average) average_pass(P, gm, up_ia, P.S);
     __syncthreads();
-    if (!SU.err) down_loop(P, gm, dn_ia, bufs, SD, true);
+    launch_exit2(P.qup, P.qavg);
+    __syncthreads();
+    if (!SU.err) down_loop(P, gm, dn_ia, bufs, SD, true, up_ia.average ? s_avg : 0);
     launch_exit(P.qdn);
 }
 
@@ -935,11 +1013,13 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.xnorm, H.S));
     int32_t *ctr;
     const int64_t nu = (int64_t)H.units.size();
-    TRY(dalloc(c, &ctr, nu + 8));
-    CU(cudaMemsetAsync(ctr, 0, (nu + 8) * sizeof(int32_t), c->stream));
+    TRY(dalloc(c, &ctr, nu + 12));
+    CU(cudaMemsetAsync(ctr, 0, (nu + 12) * sizeof(int32_t), c->stream));
     d.unit_cnt = ctr;
     d.qup = ctr + nu;
     d.qdn = ctr + nu + 4;
+    d.qavg = ctr + nu + 8;
+    d.S = (int32_t)H.S;
     d.err = c->err;
     TRY(dalloc(c, &d.root_done, L.G));
     CU(cudaMemsetAsync(d.root_done, 0, L.G * sizeof(int32_t), c->stream));
@@ -1030,7 +1110,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     c->G = L.G;
     c->Z = L.Z;
     c->cfg = shape;
-    c->split = passes == 2 || (passes == 0 && L.G == 1);
+    c->split = passes != 1;
     c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
     // two unit buffers; a unit too large to stage uses its buffer as the

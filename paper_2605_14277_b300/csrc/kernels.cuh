@@ -58,6 +58,7 @@ struct DevPlayer {
     const int4 *rwin, *win;
     const int64_t *itd_off;         // [G + 1]
     int32_t n_units, n_up, G;       // n_units: top-down units; n_up: bottom-up queue length
+    int32_t S;                      // sequences
     // state
     float2 *r;       // cumulative regret, float-float (hi, lo)
     float *b;        // behavioural strategy to be played next
@@ -73,6 +74,8 @@ struct DevPlayer {
     // last CTA to exit a launch; separate words let one pass start while the
     // previous one finishes); err: nonzero once a bounded wait gave up
     int32_t *unit_cnt, *qup, *qdn, *err;
+    // qavg: the average pass's chunk queue words {head, exit count, launches}
+    int32_t *qavg;
     // root_done[g]: set by the bottom-up loop of a fused half-step once game
     // g's root unit has written b and xn (the launch's top-down epoch + 1)
     int32_t *root_done;

@@ -141,13 +141,13 @@ struct UpTab {
     uint32_t ev;    // float ev per infoset
 };
 struct DownTab {
-    uint32_t b, x;  // float
-    uint32_t xbar;  // float2
+    uint32_t b;     // float, copied in
+    uint32_t x;     // float, the next x (work area)
     uint32_t ipar, iseq;
     uint32_t xp;    // first level: next x of the parent sequences [ps0, ps1)
     int32_t ps0;
 };
-constexpr int kDownArrays = 6;   // commands staged per top-down level
+constexpr int kDownArrays = 4;   // commands staged per top-down level
 // an internal unit's staged child values: ev of infosets [c0, c1), brought in
 // by one bulk copy (dst, src, bytes) once all its children are done
 struct ChildEv {
@@ -429,16 +429,16 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
     t.field = sh_off(place(cur, arr, a, b, e, &dst, &src, &nb));                \
     c[f] = BulkCmd{(const void *)src, smem_addr((const void *)dst), (on) ? nb : 0u};
         CFR_STAGE(b, P.b, L.s0, L.s1, 4, 0, late)
-        CFR_STAGE(x, P.x, L.s0, L.s1, 4, 1, own)
-        CFR_STAGE(xbar, P.xbar, L.s0, L.s1, 8, 2, own)
-        CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 3, own)
-        CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 4, own)
+        CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 1, own)
+        CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 2, own)
         if (lane == 0 && pr.y > pr.x) {
-            CFR_STAGE(xp, P.xn, pr.x, pr.y, 4, 5, late)
+            CFR_STAGE(xp, P.xn, pr.x, pr.y, 4, 3, late)
         } else {
-            c[5] = BulkCmd{nullptr, 0u, 0u};
+            c[3] = BulkCmd{nullptr, 0u, 0u};
         }
 #undef CFR_STAGE
+        t.x = sh_off(cur);
+        cur += work16(L.s1 - L.s0, 4);
         t.ps0 = pr.x;
     }
     __syncwarp();
@@ -710,16 +710,13 @@ __device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const 
 // xbar += w x for the strategy being replaced.  The top level's parents
 // belong to the root or to internal units, whose next x the bottom-up pass
 // published in xn; the roots' parent is the empty sequence (x = 1).
-__device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv,
-                             const DownTab *tab) {
+__device__ void compute_down(const DevPlayer &P, int nl, const SLvl *lv, const DownTab *tab) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
-    const bool avg = ia.average != 0;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
         const DownTab t = tab[k];
         const float *b = sh<const float>(t.b);
         float *x = sh<float>(t.x);
-        float2 *xbar = sh<float2>(t.xbar);
         const int32_t *ipar = sh<const int32_t>(t.ipar), *iseq = sh<const int32_t>(t.iseq);
         const int ni = L.j1 - L.j0;
         // parents' x: the level above, or (the first level) the staged next
@@ -732,21 +729,12 @@ __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemP
             // the infoset's sequences four at a time, loads first
             const int q1 = iseq[i + 1] - L.s0;
             for (int q = iseq[i] - L.s0; q < q1; q += 4) {
-                float xo[4], bb[4];
-                float2 xa[4];
+                float bb[4];
 #pragma unroll
-                for (int a = 0; a < 4; a++) {
-                    const int qa = min(q + a, q1 - 1);
-                    xo[a] = x[qa];
-                    bb[a] = b[qa];
-                    xa[a] = avg ? xbar[qa] : make_float2(0.f, 0.f);
-                }
+                for (int a = 0; a < 4; a++) bb[a] = b[min(q + a, q1 - 1)];
 #pragma unroll
                 for (int a = 0; a < 4; a++)
-                    if (q + a < q1) {
-                        if (avg) xbar[q + a] = ff_add(xa[a], ff_mul_f(ip.w, xo[a]));
-                        x[q + a] = xp * bb[a];
-                    }
+                    if (q + a < q1) x[q + a] = xp * bb[a];
             }
         }
         consumer_sync();
@@ -754,12 +742,8 @@ __device__ void compute_down(const DevPlayer &P, const IterArgs &ia, const ItemP
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
         const float *x = sh<const float>(tab[k].x);
-        const float2 *xbar = sh<const float2>(tab[k].xbar);
         const int ns = L.s1 - L.s0;
-        for (int q = tid; q < ns; q += nt) {
-            P.x[L.s0 + q] = x[q];
-            if (avg) P.xbar[L.s0 + q] = xbar[q];
-        }
+        for (int q = tid; q < ns; q += nt) P.x[L.s0 + q] = x[q];
     }
 }
 

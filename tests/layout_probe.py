@@ -110,4 +110,5 @@ def up_bytes(ns, ni, nz):
 
 
 def down_bytes(ns, ni):
-    return 2 * span16(ns, 4) + span16(ns, 8) + span16(ni, 4) + span16(ni + 1, 4)
+    """shared-memory bytes of one staged level of the down pass (layout.h)"""
+    return span16(ns, 4) + span16(ni, 4) + span16(ni + 1, 4) + work16(ns, 4)
