@@ -711,10 +711,11 @@ struct StagedConfig {
 #define CFR_SHAPE(nt, minb, kb) {nt, minb, kb * 1024, k_up_staged<nt, minb>, k_down_staged<nt, minb>, k_half_step<nt, minb>}
 const StagedConfig kConfigs[] = {
     CFR_SHAPE(512, 1, 96), CFR_SHAPE(256, 2, 48), CFR_SHAPE(256, 3, 32), CFR_SHAPE(512, 2, 48), CFR_SHAPE(256, 4, 24),
+    CFR_SHAPE(384, 2, 48), CFR_SHAPE(320, 2, 48),
 };
 #undef CFR_SHAPE
 constexpr int kNumConfigs = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
-constexpr int kDefaultConfig = 1;
+constexpr int kDefaultConfig = 6;   // 320 threads, 2 CTAs per SM, 48 KB buffers
 
 
 struct PlayerBuf {

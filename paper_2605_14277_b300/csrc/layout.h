@@ -146,7 +146,8 @@ struct CompileOptions {
     int64_t item_bytes = 48 * 1024;    // shared-memory buffer of one staged unit
     int64_t min_item_bytes = 8 * 1024; // smallest unit the packer aims for
     int64_t slots = 296;               // CTAs resident at once (units are sized to give each ~2)
-    int64_t internal_div = 1;          // internal units aim for target / internal_div
+    int64_t internal_div = 2;          // internal units aim for target / internal_div (smaller
+                                       // units shorten the chain above the leaves)
     int leaf_order = 0;                // 0: largest first; 1: tree order (children of one parent together)
     bool flat = false;                 // one level per unit below a root unit that holds the narrow top
 };

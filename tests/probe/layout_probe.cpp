@@ -25,6 +25,7 @@ void *probe_compile(int64_t G, const int64_t *n, const int32_t *const *parent, c
     Layout *L = new Layout();
     CompileOptions o;
     if (const char *f = std::getenv("LAYOUT_PROBE_FLAT")) o.flat = std::atoi(f) != 0;
+    if (const char *f = std::getenv("LAYOUT_PROBE_SLOTS")) o.slots = std::atoll(f);
     if (item_bytes > 0) {
         o.item_bytes = item_bytes;
         o.min_item_bytes = std::min<int64_t>(o.min_item_bytes, item_bytes);
