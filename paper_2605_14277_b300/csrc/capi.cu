@@ -281,7 +281,12 @@ struct DownSmem {
 // running CTAs and never wait themselves).  The game's root unit also
 // publishes the next x of itself and every internal unit (xn) and, when
 // `root_flag` is nonzero, sets the game's root_done word to it.
-__device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__restrict__ xo, const IterArgs &ia,
+// Returns true when the CTA left the queues early: it ended on its game's
+// root with no unit after it, and registered its exit (launch_exit2) as it
+// took the root, so that the launch's last exit (and, for a separate
+// top-down launch, the kernel's end) does not wait for the root's exit path;
+// such a CTA also skips the average pass, which the others complete.
+__device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__restrict__ xo, const IterArgs &ia,
                         unsigned char *const *bufs, UpSmem &S, int root_flag) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_up;
@@ -337,6 +342,7 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
     if (warp == 0 && S.unit[0] < n && (h0.w & kStaged)) issue_up_x(P, xo, h0, q0, S.tab[0], &S.bar[0]);
     int done_par = -1;   // parent of the previous unit, counted by the producer
     int cur = S.unit[0];
+    bool early = false;
     while (cur < n) {
         const int4 h = P.upq[2 * cur];
         const int4 q = P.upq[2 * cur + 1];
@@ -349,6 +355,10 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         }
         __syncthreads();
         if (S.err) break;
+        if (root && S.pre.pos >= n && !early && gridDim.x > 1) {   // another CTA does the average pass
+            launch_exit2(P.qup, P.qavg);
+            early = true;
+        }
         const ItemParams ip = S.ip[buf];
         if (warp == 0) {
             // producer: count the previous unit at its parent (its results
@@ -439,6 +449,7 @@ __device__ void up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         __threadfence();
         atomicAdd(&P.unit_cnt[done_par], 1);
     }
+    return early;
 }
 
 template <int NT, int MINB>
@@ -447,10 +458,11 @@ __global__ void __launch_bounds__(NT, MINB)
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ UpSmem S;
-    up_loop(P, gm, xo, ia, bufs, S, 0);
-    if (ia.average) average_pass(P, gm, ia, P.S);
-    __syncthreads();
-    launch_exit2(P.qup, P.qavg);
+    if (!up_loop(P, gm, xo, ia, bufs, S, 0)) {
+        if (ia.average) average_pass(P, gm, ia, P.S);
+        __syncthreads();
+        launch_exit2(P.qup, P.qavg);
+    }
 }
 
 // one unit top-down from global memory (units too large to stage); the top
@@ -477,7 +489,9 @@ __device__ void run_down(const DevPlayer &P, int nlvl, const int32_t *rng) {
 // and the unit computed, only once its game's root_done word shows the
 // bottom-up pass of that game complete (a bounded wait; the root unit was
 // taken by a running CTA before any top-down unit was).
-__device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, unsigned char *const *bufs,
+// Returns true when the CTA registered its exit (launch_exit) as it took its
+// last unit, as the bottom-up loop does.
+__device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, unsigned char *const *bufs,
                           DownSmem &S, bool wait_roots, int avg_flag = 0) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n = P.n_units;
@@ -525,9 +539,14 @@ __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
     pdl_trigger();
     pdl_wait();
     int nxt = S.nxt;
+    bool early = false;
     while (cur < n && !S.err) {
         const int4 h = P.downq[2 * cur];
         const bool staged = (h.w & kStaged) != 0;
+        if (nxt >= n && !early) {   // the last unit of this CTA: no more queue use
+            launch_exit(P.qdn);
+            early = true;
+        }
         if (staged) {
             if (warp != 0 && !mbar_wait(&S.bar[buf], ph[buf], P.err)) S.err = 1;
             ph[buf] ^= 1u;
@@ -555,6 +574,7 @@ __device__ void down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
         nxt = nxt2;
         buf ^= 1;
     }
+    return early;
 }
 
 template <int NT, int MINB>
@@ -563,8 +583,7 @@ __global__ void __launch_bounds__(NT, MINB) k_down_staged(DevPlayer P, DevGames 
     unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ DownSmem S;
     if (threadIdx.x == 0) S.epoch = 0;
-    down_loop(P, gm, ia, bufs, S, false);
-    launch_exit(P.qdn);
+    if (!down_loop(P, gm, ia, bufs, S, false)) launch_exit(P.qdn);
 }
 
 // One player's whole half-step in one launch (alternating updates): the
@@ -589,13 +608,17 @@ __global__ void __launch_bounds__(NT, MINB)
         s_avg = __ldcg(&P.qavg[2]) + 1;
     }
     __syncthreads();
-    up_loop(P, gm, xo, up_ia, bufs, SU, SD.epoch + 1);
-    if (up_ia.average) average_pass(P, gm, up_ia, P.S);
+    if (!up_loop(P, gm, xo, up_ia, bufs, SU, SD.epoch + 1)) {
+        if (up_ia.average) average_pass(P, gm, up_ia, P.S);
+        __syncthreads();
+        launch_exit2(P.qup, P.qavg);
+    }
     __syncthreads();
-    launch_exit2(P.qup, P.qavg);
-    __syncthreads();
-    if (!SU.err) down_loop(P, gm, dn_ia, bufs, SD, true, up_ia.average ? s_avg : 0);
-    launch_exit(P.qdn);
+    if (!SU.err) {
+        if (!down_loop(P, gm, dn_ia, bufs, SD, true, up_ia.average ? s_avg : 0)) launch_exit(P.qdn);
+    } else {
+        launch_exit(P.qdn);
+    }
 }
 
 // uniform behavioural strategy (regret matching of r = 0)
