@@ -251,7 +251,6 @@ __device__ void average_pass(const DevPlayer &P, const DevGames &gm, const IterA
 // Shared state of the bottom-up and top-down loops of a CTA.
 struct UpSmem {
     uint64_t bar[2];    // a buffer's own arrays
-    uint64_t cbar[2];   // an internal unit's child ev
     SLvl lv[2][kMaxStagedLevels];
     UpTab tab[2][kMaxStagedLevels];
     ChildEv cev[2];
@@ -293,13 +292,11 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
-        mbar_init(&S.cbar[0], 1);
-        mbar_init(&S.cbar[1], 1);
         fence_mbar_init();
         S.err = 0;
     }
     __syncthreads();
-    uint32_t ph[2] = {0u, 0u}, cph[2] = {0u, 0u};
+    uint32_t ph[2] = {0u, 0u};
     int buf = 0;
     // The producer keeps a pipeline a round deep: the unit in each buffer
     // (S.unit), the unit to be issued next with everything its issue reads
@@ -395,17 +392,17 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             else if (tid == 0) S.pre.pos = n;
         } else if (ip.active) {
             if (internal) {
-                // all children done, then their ev
+                // all children done, then their ev, copied by every consumer
+                // thread (the acquire above orders it through the barrier)
                 if (tid == 32) {
                     if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) S.err = 1;
                     P.unit_cnt[u] = 0;
-                    if (staged) issue_child_ev(S.cev[buf], &S.cbar[buf]);
                 }
                 consumer_sync();
                 if (staged && !S.err) {
-                    if (!mbar_wait(&S.cbar[buf], cph[buf], P.err)) S.err = 1;
+                    copy_child_ev(S.cev[buf], tid - kProducerThreads, (int)blockDim.x - kProducerThreads);
+                    cp_async_wait_all();
                 }
-                if (staged) cph[buf] ^= 1u;
                 consumer_sync();
             }
             if (staged && !S.err) {

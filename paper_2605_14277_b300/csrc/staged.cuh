@@ -77,6 +77,10 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+// 16 bytes, through L2 only (data another SM wrote: no stale L1 line)
+__device__ __forceinline__ void cp_async16_cg(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -360,7 +364,7 @@ __device__ void issue_up(const DevPlayer &P, const float *__restrict__ xo, const
         cur += work16(L.s1 - L.s0, 4);
         t.ev = sh_off(cur);
     } else if (internal && lane == nl) {
-        // placed now, copied once the children are done (issue_child_ev)
+        // placed now, copied once the children are done (copy_child_ev)
         uintptr_t dst = 0, src = 0;
         uint32_t nb = 0;
         cev->ev = sh_off(place(cur, P.ev, L.j0, L.j1, 4, &dst, &src, &nb));
@@ -383,12 +387,12 @@ __device__ void issue_up(const DevPlayer &P, const float *__restrict__ xo, const
     arm(bar, mine);
 }
 
-// One thread, once an internal unit's children are all done (acquired through
-// their completion count): copy their top-level ev into the unit's buffer.
-__device__ __forceinline__ void issue_child_ev(const ChildEv &c, uint64_t *bar) {
-    fence_proxy_async();
-    mbar_arrive_expect_tx(bar, c.bytes);
-    if (c.bytes) bulk_g2s(sh<unsigned char>(c.dst), c.src, c.bytes, bar);
+// Once an internal unit's children are all done (acquired through their
+// completion count): consumer thread t of nt copies its 16-byte pieces of the
+// children's top-level ev into the unit's buffer.
+__device__ __forceinline__ void copy_child_ev(const ChildEv &c, int t, int nt) {
+    for (uint32_t k = 16u * (uint32_t)t; k < c.bytes; k += 16u * (uint32_t)nt)
+        cp_async16_cg(sh<unsigned char>(c.dst) + k, (const unsigned char *)c.src + k);
 }
 
 // Warp 0: lay out a down unit in buffer `buf` and start its copies.  `what`
