@@ -516,25 +516,33 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
         return __all_sync(0xffffffffu, ok) != 0;
     };
     // prologue, overlapping the previous kernel (or this launch's bottom-up
-    // loop): the first unit's own arrays first; b once that is done
+    // loop): the first unit's index arrays, by the producer's bulk copies;
+    // then, once that kernel is done, its b and parents' x, copied by every
+    // thread at once (16-byte cp.async through L2)
+    const int4 h0 = cur < n ? P.downq[2 * cur] : make_int4(0, 0, 0, 0);
+    const bool st0 = cur < n && (h0.w & kStaged);
     if (warp == 0) {
-        int4 h = make_int4(0, 0, 0, 0);
-        uint32_t carried = 0;
-        if (cur < n) {
-            h = P.downq[2 * cur];
-            if (h.w & kStaged) carried = issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownOwn, 0);
-        }
+        if (st0) issue_down(P, h0, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownOwn | kDownArm, 0);
         if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
         pdl_wait();
         if (cur < n) {
-            if (!root_ready(h.x) && tid == 0) S.err = 1;
-            if (h.w & kStaged) issue_down(P, h, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownB, carried);
-            if (tid == 0) S.ip[0] = unit_params(gm, ia, h.x);
+            if (!root_ready(h0.x) && tid == 0) S.err = 1;
+            if (tid == 0) S.ip[0] = unit_params(gm, ia, h0.x);
         }
     }
     __syncthreads();
     pdl_trigger();
     pdl_wait();
+    if (st0 && !S.err) {
+        for (int k = 0; k < h0.y; k++)
+            for (int f = 0; f < 4; f += 3) {
+                const BulkCmd c = S.cmd[kDownArrays * k + f];
+                for (uint32_t o = 16u * tid; o < c.bytes; o += 16u * blockDim.x)
+                    cp_async16_cg_to(c.dst + o, (const unsigned char *)c.src + o);
+            }
+        cp_async_wait_all();
+    }
+    __syncthreads();
     int nxt = S.nxt;
     bool early = false;
     while (cur < n && !S.err) {
@@ -557,7 +565,7 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
                 if (!root_ready(hn.x) && tid == 0) S.err = 1;
                 if (hn.w & kStaged)
                     issue_down(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], S.cmd,
-                               kDownOwn | kDownB, 0);
+                               kDownOwn | kDownB | kDownArm, 0);
                 if (tid == 0) S.ip[buf ^ 1] = unit_params(gm, ia, hn.x);
             }
             if (tid == 0) S.nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;

@@ -78,9 +78,10 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 // 16 bytes, through L2 only (data another SM wrote: no stale L1 line)
-__device__ __forceinline__ void cp_async16_cg(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async16_cg_to(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16_cg(void *dst, const void *src) { cp_async16_cg_to(smem_addr(dst), src); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -395,12 +396,14 @@ __device__ __forceinline__ void copy_child_ev(const ChildEv &c, int t, int nt) {
         cp_async16_cg(sh<unsigned char>(c.dst) + k, (const unsigned char *)c.src + k);
 }
 
-// Warp 0: lay out a down unit in buffer `buf` and start its copies.  `what`
-// selects the arrays: kDownOwn (x, xbar and the index arrays, which the
-// previous kernel does not write) and/or kDownB (the strategy b the up pass
-// just wrote).  The call that issues b arms the barrier with `carried` plus
-// its own bytes; the return value is this lane's bytes when b is not issued.
-constexpr int kDownOwn = 1, kDownB = 2;
+// Warp 0: lay out a down unit in buffer `buf`, stage its copies as commands
+// (cmd[kDownArrays * level + f]: f = 0 b, 1 infoset parents, 2 infoset
+// segments, 3 the first level's parents' next x) and issue those `what`
+// selects: kDownOwn (the index arrays, which no pass writes) and/or kDownB
+// (b and the parents' x, which the bottom-up pass writes).  With kDownArm the
+// barrier is armed with `carried` plus the bytes issued here.  Returns this
+// lane's bytes.
+constexpr int kDownOwn = 1, kDownB = 2, kDownArm = 4;
 __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
                                DownTab *tab, BulkCmd *cmd, int what, uint32_t carried) {
     const int lane = threadIdx.x & 31;
@@ -420,23 +423,21 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
     }
     unsigned char *cur = buf + level_offset(bytes);
     fence_proxy_async();
-    // placement by each level's lane, copies staged as commands (a command
-    // of the other phase is staged with no bytes)
+    // placement by each level's lane, copies staged as commands
     if (lane < nl) {
         lv[lane] = L;
         DownTab &t = tab[lane];
         BulkCmd *c = cmd + kDownArrays * lane;
         uintptr_t dst = 0, src = 0;
         uint32_t nb = 0;
-        const bool own = (what & kDownOwn) != 0, late = (what & kDownB) != 0;
-#define CFR_STAGE(field, arr, a, b, e, f, on)                                    \
+#define CFR_STAGE(field, arr, a, b, e, f)                                        \
     t.field = sh_off(place(cur, arr, a, b, e, &dst, &src, &nb));                \
-    c[f] = BulkCmd{(const void *)src, smem_addr((const void *)dst), (on) ? nb : 0u};
-        CFR_STAGE(b, P.b, L.s0, L.s1, 4, 0, late)
-        CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 1, own)
-        CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 2, own)
+    c[f] = BulkCmd{(const void *)src, smem_addr((const void *)dst), nb};
+        CFR_STAGE(b, P.b, L.s0, L.s1, 4, 0)
+        CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 1)
+        CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 2)
         if (lane == 0 && pr.y > pr.x) {
-            CFR_STAGE(xp, P.xn, pr.x, pr.y, 4, 3, late)
+            CFR_STAGE(xp, P.xn, pr.x, pr.y, 4, 3)
         } else {
             c[3] = BulkCmd{nullptr, 0u, 0u};
         }
@@ -448,15 +449,14 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
     __syncwarp();
     uint32_t mine = carried;
     for (int k = lane; k < kDownArrays * nl; k += 32) {
+        const int f = k % kDownArrays;
+        if (!(what & ((f == 0 || f == 3) ? kDownB : kDownOwn))) continue;
         const BulkCmd c = cmd[k];
         for (uint32_t o = 0; o < c.bytes; o += kChunk)
             bulk_g2s_to(c.dst + o, (const char *)c.src + o, min(kChunk, c.bytes - o), bar);
         mine += c.bytes;
     }
-    if (what & kDownB) {
-        arm(bar, mine);
-        return 0;
-    }
+    if (what & kDownArm) arm(bar, mine);
     return mine;
 }
 
