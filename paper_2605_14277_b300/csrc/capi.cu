@@ -256,6 +256,8 @@ struct UpSmem {
     ChildEv cev[2];
     ItemParams ip[2];
     UpPre pre;          // the unit to be issued next
+    int4 win0[kPreWin]; // the first unit's x windows (copied once the previous kernel is done)
+    int nwin0, win0_at; // their number and first record
     BulkCmd cmd[kUpArrays * kMaxStagedLevels];   // the producer's staged copies
     int unit[2];        // queue position of the unit in each buffer (n: none)
     int err;
@@ -323,6 +325,11 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             if (tid == 0) S.ip[0] = S.pre.ip;
             if (h0.w & kStaged)
                 issue_up(P, xo, S.pre, bufs[0], &S.bar[0], S.lv[0], S.tab[0], &S.cev[0], S.cmd, true);
+            for (int w = tid; w < min(unit_nwin(h0), kPreWin); w += 32) S.win0[w] = S.pre.win[w];
+        }
+        if (tid == 0) {
+            S.nwin0 = (p0 < n && (h0.w & kStaged)) ? unit_nwin(h0) : 0;
+            S.win0_at = q0.w;
         }
         if (tid == 0) S.unit[0] = p0 < n ? p0 : n;
         __syncwarp();
@@ -335,8 +342,16 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
     // a running one
     pdl_wait();
     pdl_trigger();
-    // the first unit's x windows (the other player's x is final now)
-    if (warp == 0 && S.unit[0] < n && (h0.w & kStaged)) issue_up_x(P, xo, h0, q0, S.tab[0], &S.bar[0]);
+    // the first unit's x windows (the other player's x is final now), by
+    // every thread; more windows than were kept come from global memory
+    {
+        const int nw = S.nwin0;
+        if (nw > 0) {
+            copy_up_x(xo, nw, nw <= kPreWin ? S.win0 : P.win + S.win0_at, S.tab[0], tid, blockDim.x);
+            cp_async_wait_all();
+        }
+        __syncthreads();
+    }
     int done_par = -1;   // parent of the previous unit, counted by the producer
     int cur = S.unit[0];
     bool early = false;

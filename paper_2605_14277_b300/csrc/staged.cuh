@@ -304,13 +304,17 @@ __device__ __forceinline__ uint32_t issue_windows(const DevPlayer &P, const floa
     return mine;
 }
 
-// Warp 0: the x windows of a unit laid out by issue_up with `defer_x`, once
-// the other player's x may be read (the previous kernel is done).
-__device__ void issue_up_x(const DevPlayer &P, const float *__restrict__ xo, const int4 h, const int4 q,
-                           const UpTab *tab, uint64_t *bar) {
-    if (unit_nwin(h) > 0) {
-        fence_proxy_async();
-        issue_windows(P, xo, h, q, nullptr, tab, bar, true);
+// The x windows of a unit laid out by issue_up with `defer_x`, once the
+// other player's x may be read (the previous kernel is done): thread t of nt
+// copies its 16-byte pieces of each window (d: the unit's window records).
+__device__ void copy_up_x(const float *__restrict__ xo, int nw, const int4 *d, const UpTab *tab, int t, int nt) {
+    for (int w = 0; w < nw; w++) {
+        unsigned char *cur = sh<unsigned char>(tab[d[w].w].gx) + d[w].z;
+        uintptr_t dst = 0, src = 0;
+        uint32_t nb = 0;
+        place(cur, xo, d[w].x, d[w].y, 4, &dst, &src, &nb);
+        for (uint32_t k = 16u * (uint32_t)t; k < nb; k += 16u * (uint32_t)nt)
+            cp_async16_cg((void *)(dst + k), (const void *)(src + k));
     }
 }
 
@@ -384,7 +388,8 @@ __device__ void issue_up(const DevPlayer &P, const float *__restrict__ xo, const
             bulk_g2s_to(c.dst + o, (const char *)c.src + o, min(kChunk, c.bytes - o), bar);
         mine += c.bytes;
     }
-    if (unit_nwin(hdr) > 0) mine += issue_windows(P, xo, hdr, pre.q, pre.win, tab, bar, !defer_x);
+    // deferred windows are copied by the whole CTA later, outside the barrier
+    if (unit_nwin(hdr) > 0 && !defer_x) mine += issue_windows(P, xo, hdr, pre.q, pre.win, tab, bar, true);
     arm(bar, mine);
 }
 
