@@ -91,18 +91,19 @@ def alg_bytes(sz):
 
     up(p):   8 Z (payoff col + val) + 4 S_p (row pointers) + 16 S_p (regret
              float-float read + write) + 8 S_p (strategy read + write)
-             + 4 S_p (child pointers) + 4 J_p (segment pointers) + 4 S_o (gather
-             of the other player's x, each entry once)
-    down(p): 16 S_p (average sums read + write) + 8 S_p (x read + write)
-             + 4 S_p (strategy) + 8 J_p (parent and segment pointers)
+             + 4 S_p (child pointers) + 4 J_p (segment pointers) + 4 S_o (the
+             other player's x, each entry once); then the average update in
+             the same launch: 16 S_p (average sums read + write) + 4 S_p (x)
+    down(p): 4 S_p (strategy) + 4 S_p (x written) + 8 J_p (parent and
+             segment pointers)
     """
     S1, S2 = sz["S1"] + 1, sz["S2"] + 1
     J1, J2 = sz["J1"] + 1, sz["J2"] + 1
     Z = sz["nnz"]
-    up1 = 8 * Z + 32 * S1 + 4 * J1 + 4 * S2
-    up2 = 8 * Z + 32 * S2 + 4 * J2 + 4 * S1
-    dn1 = 28 * S1 + 8 * J1
-    dn2 = 28 * S2 + 8 * J2
+    up1 = 8 * Z + 52 * S1 + 4 * J1 + 4 * S2
+    up2 = 8 * Z + 52 * S2 + 4 * J2 + 4 * S1
+    dn1 = 8 * S1 + 8 * J1
+    dn2 = 8 * S2 + 8 * J2
     return {"up_p1": up1, "down_p1": dn1, "up_p2": up2, "down_p2": dn2}
 
 
@@ -421,8 +422,8 @@ def batch_alg_bytes(sizes):
     tot = {k: sum(z[k] for z in sizes) for k in ("S1", "S2", "J1", "J2", "nnz")}
     G_ = len(sizes)
     S1, S2, J1, J2, Z = tot["S1"] + G_, tot["S2"] + G_, tot["J1"] + G_, tot["J2"] + G_, tot["nnz"]
-    return (8 * Z + 32 * S1 + 4 * J1 + 4 * S2) + (28 * S1 + 8 * J1) + (8 * Z + 32 * S2 + 4 * J2 + 4 * S1) + \
-        (28 * S2 + 8 * J2)
+    return (8 * Z + 52 * S1 + 4 * J1 + 4 * S2) + (8 * S1 + 8 * J1) + (8 * Z + 52 * S2 + 4 * J2 + 4 * S1) + \
+        (8 * S2 + 8 * J2)
 
 
 def run_batch(args):
