@@ -145,14 +145,19 @@ __global__ void k_root_topdown(DevPlayer P) {
 }
 
 // Per-game parameters of iterations t = t_done + k, k = 0..kParamSpan, for the
-// passes that follow (one thread per entry).
+// passes that follow (one thread per entry).  A game whose counter or active
+// flag differs from game 0's marks the table mixed (the flag is cleared before
+// the launch).
 __global__ void k_params(DevGames gm, IterArgs ia, int G) {
     const int64_t n = (int64_t)G * (kParamSpan + 1);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int g = (int)(e / (kParamSpan + 1)), k = (int)(e % (kParamSpan + 1));
         const int32_t t0 = gm.t_done[g];
         params_of_t(gm, ia, g, t0 + k, &gm.par[e]);
-        if (k == 0) gm.pbase[g] = t0;
+        if (k == 0) {
+            gm.pbase[g] = t0;
+            if (t0 != gm.t_done[0] || gm.active[g] != gm.active[0]) *gm.mixed = 1;
+        }
     }
 }
 
@@ -204,15 +209,49 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
 // sequences are taken from a queue; the last CTA to leave resets it.
 constexpr int kAvgChunk = 1024;
 constexpr int kAvgU = 4;   // sequences per thread with loads in flight together
+// One chunk's sequences [q0, q1).  UNIFORM: every game has game 0's
+// parameters; otherwise each sequence looks up its game's weight (the
+// sequences of several games are interleaved level by level), all kAvgU
+// lookups of a thread in flight together.
+template <bool UNIFORM>
+__device__ __forceinline__ void average_chunk(const DevPlayer &P, const DevGames &gm, const IterArgs &ia,
+                                              const ItemParams &ip0, int64_t q0, int64_t q1) {
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += kAvgU * blockDim.x) {
+        float xv[kAvgU];
+        float2 xb[kAvgU], w[kAvgU];
+        int gq[kAvgU], act[kAvgU];
+#pragma unroll
+        for (int u = 0; u < kAvgU; u++) {
+            const int64_t s = min(q + u * (int64_t)blockDim.x, q1 - 1);
+            xv[u] = P.x[s];
+            xb[u] = P.xbar[s];
+            if (!UNIFORM) gq[u] = P.seq_game[s];
+        }
+#pragma unroll
+        for (int u = 0; u < kAvgU; u++) {
+            if (UNIFORM) {
+                w[u] = ip0.w;
+                act[u] = ip0.active;
+            } else {
+                const ItemParams *pp = &gm.par[(int64_t)gq[u] * (kParamSpan + 1) + ia.pslot];
+                w[u] = pp->w;
+                act[u] = pp->active;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kAvgU; u++) {
+            const int64_t s = q + u * (int64_t)blockDim.x;
+            if (s < q1 && act[u]) P.xbar[s] = ff_add(xb[u], ff_mul_f(w[u], xv[u]));
+        }
+    }
+}
+
 __device__ void average_pass(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, int64_t S) {
     __shared__ int s_chunk;
     const int64_t nch = (S + kAvgChunk - 1) / kAvgChunk;
-    // one game: its parameters once (the sequences of several games are
-    // interleaved level by level, so a batch looks them up per sequence,
-    // cached per thread)
-    const bool one = P.G == 1;
-    ItemParams ip = unit_params(gm, ia, 0);
-    int g = 0;
+    // one game, or a batch advanced in step: one set of parameters
+    const bool uniform = P.G == 1 || __ldcg(gm.mixed) == 0;
+    const ItemParams ip0 = unit_params(gm, ia, 0);
     if (threadIdx.x == 0) s_chunk = atomicAdd(&P.qavg[0], 1);
     for (;;) {
         __syncthreads();
@@ -222,28 +261,10 @@ __device__ void average_pass(const DevPlayer &P, const DevGames &gm, const IterA
         int next = 0;
         if (threadIdx.x == 0) next = atomicAdd(&P.qavg[0], 1);
         const int64_t q0 = c * kAvgChunk, q1 = min((int64_t)S, q0 + kAvgChunk);
-        for (int64_t q = q0 + threadIdx.x; q < q1; q += kAvgU * blockDim.x) {
-            float xv[kAvgU];
-            float2 xb[kAvgU];
-            int gq[kAvgU];
-#pragma unroll
-            for (int u = 0; u < kAvgU; u++) {
-                const int64_t s = min(q + u * (int64_t)blockDim.x, q1 - 1);
-                xv[u] = P.x[s];
-                xb[u] = P.xbar[s];
-                gq[u] = one ? g : P.seq_game[s];
-            }
-#pragma unroll
-            for (int u = 0; u < kAvgU; u++) {
-                const int64_t s = q + u * (int64_t)blockDim.x;
-                if (s >= q1) break;
-                if (gq[u] != g) {   // a chunk across games: per-thread cache
-                    g = gq[u];
-                    ip = unit_params(gm, ia, g);
-                }
-                if (ip.active) P.xbar[s] = ff_add(xb[u], ff_mul_f(ip.w, xv[u]));
-            }
-        }
+        if (uniform)
+            average_chunk<true>(P, gm, ia, ip0, q0, q1);
+        else
+            average_chunk<false>(P, gm, ia, ip0, q0, q1);
         if (threadIdx.x == 0) s_chunk = next;
     }
 }
@@ -278,15 +299,19 @@ struct DownSmem {
 // shared memory, it fetches the next unit, loads its parameters and starts its
 // bulk copies into the other buffer.  An internal unit's own arrays are
 // staged at once; its children's ev is copied in when its completion count
-// shows all children done (a bounded wait: the children were taken earlier by
-// running CTAs and never wait themselves).  The game's root unit also
+// shows all children done (a bounded wait: the children come earlier in the
+// queue, every CTA works its units in queue order, and a child never waits
+// for a later unit; a child at a static position of a CTA that is not yet
+// resident is done once that CTA runs).  The game's root unit also
 // publishes the next x of itself and every internal unit (xn) and, when
 // `root_flag` is nonzero, sets the game's root_done word to it.
-// Returns true when the CTA left the queues early: it ended on its game's
-// root with no unit after it, and registered its exit (launch_exit2) as it
-// took the root, so that the launch's last exit (and, for a separate
-// top-down launch, the kernel's end) does not wait for the root's exit path;
-// such a CTA also skips the average pass, which the others complete.
+// Returns true when the CTA left the queues early: with a single game, it
+// ended on the root with no unit after it, and registered its exit
+// (launch_exit2) as it took the root, so that the launch's last exit (and,
+// for a separate top-down launch, the kernel's end) does not wait for the
+// root's exit path; such a CTA also skips the average pass, which the
+// others complete.  With several games every CTA may end on a root, so none
+// leaves early.
 __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__restrict__ xo, const IterArgs &ia,
                         unsigned char *const *bufs, UpSmem &S, int root_flag) {
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -303,19 +328,21 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
     // The producer keeps a pipeline a round deep: the unit in each buffer
     // (S.unit), the unit to be issued next with everything its issue reads
     // (S.pre), and the queue position after that (pend, lane 0), whose
-    // fetch was started a round earlier.  A CTA's first three positions are
-    // blockIdx, + grid, + 2 grid (every CTA has work before any has a fourth
-    // unit); later ones come from the queue counter, past those.  Positions
-    // only grow along a CTA's pipeline.
-    const int G3 = 3 * (int)gridDim.x;
-    auto fetch = [&]() { return G3 + atomicAdd(&P.qup[0], 1); };
+    // fetch was started a round earlier.  Every position comes from the
+    // queue counter, so only a running CTA ever holds a unit (a unit that
+    // another CTA waits for is never held by a CTA that is not yet resident);
+    // a CTA claims its second position only once its first is issued, so
+    // that the CTAs running at the start each hold one unit before any holds
+    // two.  Positions only grow along a CTA's pipeline.
+    auto fetch = [&]() { return atomicAdd(&P.qup[0], 1); };
     int pend = n;
     int4 h0 = make_int4(0, 0, 0, 0), q0 = h0;
     // prologue, overlapping the previous kernel: nothing read here is written
     // by it (the other player's x waits)
     if (warp == 0) {
-        const int p0 = blockIdx.x, p1 = blockIdx.x + gridDim.x;
-        if (tid == 0) pend = blockIdx.x + 2 * gridDim.x;
+        int p0 = n, p1 = n;
+        if (tid == 0) p0 = fetch();
+        p0 = __shfl_sync(0xffffffffu, p0, 0);
         if (p0 < n) {
             h0 = P.upq[2 * p0];
             q0 = P.upq[2 * p0 + 1];
@@ -332,7 +359,9 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             S.win0_at = q0.w;
         }
         if (tid == 0) S.unit[0] = p0 < n ? p0 : n;
-        __syncwarp();
+        if (tid == 0 && p0 < n) p1 = fetch();
+        p1 = __shfl_sync(0xffffffffu, p1, 0);
+        if (tid == 0) pend = p1 < n ? fetch() : n;
         if (p1 < n) up_prefetch(P, gm, ia, p1, P.upq[2 * p1], P.upq[2 * p1 + 1], S.pre);
         else if (tid == 0) S.pre.pos = n;
     }
@@ -367,7 +396,7 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         }
         __syncthreads();
         if (S.err) break;
-        if (root && S.pre.pos >= n && !early && gridDim.x > 1) {   // another CTA does the average pass
+        if (root && S.pre.pos >= n && !early && gridDim.x > 1 && P.G == 1) {   // another CTA does the average pass
             launch_exit2(P.qup, P.qavg);
             early = true;
         }
@@ -792,6 +821,7 @@ struct cfr_ctx {
     uint8_t *active = nullptr;
     ItemParams *par = nullptr;      // per-game parameter table (kParamSpan + 1 entries)
     int32_t *pbase = nullptr;
+    int32_t *mixed = nullptr;   // set by k_params when the games' parameters differ
     double *br[2] = {nullptr, nullptr};
     double *scratch = nullptr;   // FP64 transfer area: 3 * (max S + 1)
     int64_t scratch_n = 0;
@@ -852,12 +882,13 @@ int upload(cfr_ctx *c, T **p, const std::vector<T> &v) {
     return CFR_OK;
 }
 
-DevGames dev_games(const cfr_ctx *c) { return DevGames{c->t_done, c->active, nullptr, c->par, c->pbase}; }
+DevGames dev_games(const cfr_ctx *c) { return DevGames{c->t_done, c->active, nullptr, c->par, c->pbase, c->mixed}; }
 
 // the parameter table for the next kParamSpan iterations of every game
 int launch_params(cfr_ctx *c, int variant, double alpha, double beta, double gamma) {
     IterArgs ia{variant, 0, 0.f, alpha, beta, gamma, 0, 0};
     const int64_t n = c->G * (kParamSpan + 1);
+    CU(cudaMemsetAsync(c->mixed, 0, sizeof(int32_t), c->stream));
     k_params<<<(unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096), kThreads, 0, c->stream>>>(
         dev_games(c), ia, (int)c->G);
     CU(cudaGetLastError());
@@ -1075,14 +1106,16 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     CU(cudaMemsetAsync(d.xn, 0, H.S * sizeof(float), c->stream));
     B.smem_br = (size_t)(kThreads / 32) * 32 * kStage * sizeof(double);
     const StagedConfig &cf = kConfigs[c->cfg];
-    CU(cudaFuncSetAttribute((const void *)cf.up, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
-    CU(cudaFuncSetAttribute((const void *)cf.down, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)c->smem_staged));
+    // the pass kernels overlap one another's tails: one shared-memory carve-out
+    // for all of them, so that an SM that ran one kernel's CTAs takes the next
+    // kernel's full count without first draining
+    for (const void *fn : {(const void *)cf.up, (const void *)cf.down, (const void *)cf.half}) {
+        CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_staged));
+        CU(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    }
     TRY(occupancy_grid((const void *)cf.up, c->threads, c->smem_staged, B.n_up, &B.grid_up));
     TRY(occupancy_grid((const void *)k_up<MODE_BR>, kThreads, B.smem_br, B.n_up, &B.grid_up_br));
     TRY(occupancy_grid((const void *)cf.down, c->threads, c->smem_staged, B.n_units, &B.grid_down));
-    CU(cudaFuncSetAttribute((const void *)cf.half, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)c->smem_staged));
     TRY(occupancy_grid((const void *)cf.half, c->threads, c->smem_staged, std::max(B.n_up, B.n_units),
                        &B.grid_half));
     k_uniform<<<(unsigned)std::min<int64_t>((H.J + kThreads - 1) / kThreads, 65535), kThreads, 0, c->stream>>>(d,
@@ -1171,6 +1204,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     if ((rc = dalloc(c, &c->active, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->par, L.G * (kParamSpan + 1)))) return bail(rc);
     if ((rc = dalloc(c, &c->pbase, L.G))) return bail(rc);
+    if ((rc = dalloc(c, &c->mixed, 1))) return bail(rc);
     if ((rc = dalloc(c, &c->br[0], L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->br[1], L.G))) return bail(rc);
     int64_t smax = 0;

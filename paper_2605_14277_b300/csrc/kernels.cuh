@@ -88,6 +88,7 @@ struct DevGames {
     double *br;             // best-response value per game (BR pass output)
     ItemParams *par;        // [G][kParamSpan + 1] parameters of t = pbase[g] + k
     int32_t *pbase;         // [G]
+    int32_t *mixed;         // 0: every game has game 0's parameters in every slot of the table
 };
 constexpr int kParamSpan = 64;   // iterations covered by one parameter table
 

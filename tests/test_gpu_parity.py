@@ -275,6 +275,21 @@ def test_batch_game_is_identical_alone_and_in_mix(cfr):
             assert np.array_equal(a["b"], b["b"])
 
 
+def test_many_small_games_keep_their_averages(cfr):
+    # more game roots than CTAs: every CTA may end its bottom-up queue on a
+    # root, and the average update (Alg. 2) must still cover every sequence
+    trees = [G.sized_random_game(5000 + k, 120) for k in range(1500)]
+    s = cfr.Solver(trees)
+    s.iterate(6, "cfr+")
+    for g in (0, 749, 1499):
+        alone = cfr.Solver(trees[g])
+        alone.iterate(6, "cfr+")
+        for p in (1, 2):
+            a = alone.get_state(p)
+            b = s.get_state(p, game=g)
+            assert np.array_equal(a["xbar"], b["xbar"]) and np.array_equal(a["r"], b["r"])
+
+
 def test_active_mask_freezes_games(cfr):
     trees = [G.sized_random_game(2000 + k, 500) for k in range(4)]
     s = cfr.Solver(trees)
@@ -282,6 +297,23 @@ def test_active_mask_freezes_games(cfr):
     assert [s.sizes(g)["t"] for g in range(4)] == [10, 0, 10, 0]
     st = s.get_state(1, game=1)
     assert np.all(st["r"] == 0.0)
+
+
+def test_games_at_different_iterations_advance_independently(cfr):
+    # a table whose games hold different counters (each game's own weights
+    # t^gamma in the average update, Alg. 4) against each game run alone
+    trees = [G.sized_random_game(3000 + k, 10 ** (2 + (k % 3))) for k in range(4)]
+    s = cfr.Solver(trees)
+    s.iterate(7, "dcfr", active=[1, 1, 0, 0])
+    s.iterate(20, "dcfr")
+    assert [s.sizes(g)["t"] for g in range(4)] == [27, 27, 20, 20]
+    for g, n in ((1, 27), (2, 20)):
+        alone = cfr.Solver(trees[g])
+        alone.iterate(n, "dcfr")
+        for p in (1, 2):
+            a = alone.get_state(p)
+            b = s.get_state(p, game=g)
+            assert np.array_equal(a["r"], b["r"]) and np.array_equal(a["xbar"], b["xbar"])
 
 
 def test_graph_length_does_not_change_results(cfr):
