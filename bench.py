@@ -43,7 +43,15 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def workload(name):
+def workload(name, variant=None):
+    """(tree, variant) of a single-game workload; `variant` overrides the
+    workload's own (DCFR for the large game and poker, vanilla CFR for the
+    small game)."""
+    tree, v = _workload(name)
+    return tree, (variant or v)
+
+
+def _workload(name):
     if name == "large":
         return G.large_random_game(3), "dcfr"
     if name == "poker":
@@ -281,7 +289,7 @@ def run_reference(args):
         return run_reference_batch(args)
     if args.workload == "serve":
         return run_reference_serve(args)
-    tree, variant = workload(args.workload)
+    tree, variant = workload(args.workload, args.variant)
     from oracle.oracle import Oracle
     o = Oracle(tree)
     t0 = time.perf_counter()
@@ -316,7 +324,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2605_14277_b300 import cfr as C
 
-    tree, variant = workload(args.workload)
+    tree, variant = workload(args.workload, args.variant)
     stream = torch.cuda.Stream()
     s = C.Solver(tree, stream=stream)
     sz = s.sizes()
@@ -349,7 +357,12 @@ def run_ours(args):
     n_prof = max(50, min(2000, args.steps // 5))
     kms = s.profile(n_prof, variant)
     kbytes = alg_bytes(sz)
-    names = ["up_p1", "down_p1", "up_p2", "down_p2"]
+    # launch slots in schedule order: alternating p1 up, p1 down, p2 up, p2
+    # down; simultaneous (vanilla CFR's default) both up passes first
+    if variant == "cfr":
+        names = ["up_p1", "up_p2", "down_p1", "down_p2"]
+    else:
+        names = ["up_p1", "down_p1", "up_p2", "down_p2"]
     avg_ms = {n: kms[i] / n_prof for i, n in enumerate(names)}
     dom = max(names, key=lambda n: avg_ms[n])
     hbm, src = peaks()
@@ -636,6 +649,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "poker", "small", "batch", "serve"])
+    ap.add_argument("--variant", default=None, choices=["cfr", "cfr+", "dcfr", "pcfr+", "pcfr"],
+                    help="regret minimiser for the single-game workloads (default: the workload's own)")
     ap.add_argument("--serve-rate", type=float, default=1000.0)
     ap.add_argument("--serve-seconds", type=float, default=0.25)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)

@@ -48,7 +48,8 @@ typedef enum {
     CFR_VANILLA = 0,    /* regret matching */
     CFR_PLUS = 1,       /* regret matching+ : r := r^+ after ObserveUtility (Alg. 3) */
     CFR_DCFR = 2,       /* discounted: r *= t^a/(t^a+1) where r>0, t^b/(t^b+1) where r<0 (Alg. 4) */
-    CFR_PCFR_PLUS = 3   /* predictive RM+ with prediction m^t = u^(t-1) (Alg. 5) */
+    CFR_PCFR_PLUS = 3,  /* predictive RM+ with prediction m^t = u^(t-1) (Alg. 5) */
+    CFR_PCFR = 4        /* predictive RM, regrets never floored (Alg. 5, Sec. 3.5.4) */
 } cfr_variant;
 
 /* update schedule (Sec. 3.5.1) */

@@ -26,6 +26,8 @@
  *   - PCFR+ (Alg. 5): NextStrategy*(m) with m = the last utility: back up r,
  *     keep the previous behavioural strategy, ObserveUtility(m), regret
  *     matching, restore r.  Regrets are floored as in CFR+.
+ *   - PCFR (Sec. 3.5.4, the predictive counterpart of CFR): the same
+ *     NextStrategy*(m), with regrets never floored (no post-op).
  *   - alternating updates (Sec. 3.5.1): player 2's half-step sees player 1's
  *     strategy recomputed after player 1's update.
  *   - average strategy: xbar += t^gamma x^t for the strategy played at t.
@@ -45,7 +47,7 @@
 #define ERR_STATE (-5)
 
 enum { K_CHANCE = 0, K_P1 = 1, K_P2 = 2, K_TERM = 3 };
-enum { V_CFR = 0, V_CFRPLUS = 1, V_DCFR = 2, V_PCFRPLUS = 3 };
+enum { V_CFR = 0, V_CFRPLUS = 1, V_DCFR = 2, V_PCFRPLUS = 3, V_PCFR = 4 };
 
 typedef struct {
     int64_t J;          /* infosets */
@@ -352,7 +354,7 @@ static void update_player(oracle_game *g, int p, const double *u, const double *
     for (int64_t s = 0; s <= P->S; s++) P->xbar[s] += w * xplayed[s];
     observe_utility(P, u, P->b, P->r, sc->V, sc->ev);
     post_op(P, variant, t, alpha, beta, P->r);
-    if (variant == V_PCFRPLUS) {
+    if (variant == V_PCFRPLUS || variant == V_PCFR) {
         /* NextStrategy*(m = u): back up r, observe the prediction with the
          * previous behavioural strategy, regret-match, restore r */
         memcpy(sc->rho, P->r, (size_t)(P->S + 1) * sizeof(double));
@@ -366,7 +368,7 @@ static void update_player(oracle_game *g, int p, const double *u, const double *
 
 int oracle_iterate(oracle_game *g, int64_t n, int variant, double alpha, double beta,
                    double gamma, int alternating) {
-    if (variant < 0 || variant > 3 || n < 0) return ERR_INVALID;
+    if (variant < 0 || variant > 4 || n < 0) return ERR_INVALID;
     int64_t Smax = g->pl[1].S > g->pl[2].S ? g->pl[1].S : g->pl[2].S;
     int64_t Jmax = g->pl[1].J > g->pl[2].J ? g->pl[1].J : g->pl[2].J;
     double *x = (double *)xcalloc(g->pl[1].S + 1, sizeof(double));

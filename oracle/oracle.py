@@ -22,10 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cfr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-VARIANTS = {"cfr": 0, "cfr+": 1, "dcfr": 2, "pcfr+": 3}
+VARIANTS = {"cfr": 0, "cfr+": 1, "dcfr": 2, "pcfr+": 3, "pcfr": 4}
 # per-variant defaults: (alternating, alpha, beta, gamma)
 DEFAULTS = {0: (False, 0.0, 0.0, 0.0), 1: (True, 0.0, 0.0, 1.0),
-            2: (True, 1.5, 0.0, 2.0), 3: (True, 0.0, 0.0, 2.0)}
+            2: (True, 1.5, 0.0, 2.0), 3: (True, 0.0, 0.0, 2.0), 4: (True, 0.0, 0.0, 0.0)}
 
 
 def build(force: bool = False) -> str:

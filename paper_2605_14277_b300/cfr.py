@@ -15,10 +15,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcfr.so")
 
-VARIANTS = {"cfr": 0, "vanilla": 0, "cfr+": 1, "dcfr": 2, "pcfr+": 3}
+VARIANTS = {"cfr": 0, "vanilla": 0, "cfr+": 1, "dcfr": 2, "pcfr+": 3, "pcfr": 4}
 # default (alpha, beta, gamma) per variant: DCFR (1.5, 0) with quadratic
 # averaging; CFR+ linear averaging; PCFR+ quadratic; vanilla uniform
-DEFAULT_PARAMS = {0: (0.0, 0.0, 0.0), 1: (0.0, 0.0, 1.0), 2: (1.5, 0.0, 2.0), 3: (0.0, 0.0, 2.0)}
+DEFAULT_PARAMS = {0: (0.0, 0.0, 0.0), 1: (0.0, 0.0, 1.0), 2: (1.5, 0.0, 2.0), 3: (0.0, 0.0, 2.0), 4: (0.0, 0.0, 0.0)}
 UPDATES = {"default": 0, "simultaneous": 1, "alternating": 2}
 
 

@@ -1244,7 +1244,7 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
     if (!c) return set_err(CFR_ERR_ARG, "ctx is NULL");
     if (c->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
     if (n < 0) return set_err(CFR_ERR_ARG, "negative iteration count");
-    if (variant < 0 || variant > 3) return set_err(CFR_ERR_ARG, "unknown variant");
+    if (variant < 0 || variant > 4) return set_err(CFR_ERR_ARG, "unknown variant");
     if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(gamma))
         return set_err(CFR_ERR_ARG, "alpha, beta, gamma must be finite");
     const bool alt = c->update_mode == CFR_UPDATES_DEFAULT ? default_alternating(variant)
@@ -1563,7 +1563,7 @@ int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha,
                            float *host_ms) {
     if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
     if (!host_ms || n < 1) return set_err(CFR_ERR_ARG, "need n >= 1 and an output array");
-    if ((int)v < 0 || (int)v > 3) return set_err(CFR_ERR_ARG, "unknown variant");
+    if ((int)v < 0 || (int)v > 4) return set_err(CFR_ERR_ARG, "unknown variant");
     const bool alt = ctx->update_mode == CFR_UPDATES_DEFAULT ? default_alternating((int)v)
                                                              : ctx->update_mode == CFR_UPDATES_ALTERNATING;
     cudaEvent_t ev[5];

@@ -33,7 +33,10 @@ namespace cfrb {
 constexpr int kThreads = 256;      // threads of a global-path CTA
 constexpr int kStage = 8;          // products staged per lane per pass of the payoff SpMV
 
-enum { VAR_CFR = 0, VAR_PLUS = 1, VAR_DCFR = 2, VAR_PCFR_PLUS = 3 };
+enum { VAR_CFR = 0, VAR_PLUS = 1, VAR_DCFR = 2, VAR_PCFR_PLUS = 3, VAR_PCFR = 4 };
+// predictive variants: the next strategy is regret matching of r + the
+// instantaneous regret just observed (Alg. 5 with m^(t+1) = u^t)
+__host__ __device__ constexpr bool predictive(int v) { return v == VAR_PCFR_PLUS || v == VAR_PCFR; }
 enum { MODE_CFR = 0, MODE_BR = 1 };
 
 struct DevPlayer {
@@ -279,7 +282,7 @@ __device__ __forceinline__ float value_of(const DevPlayer &P, int s) {
 __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const ItemParams &ip) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     const int na = s1 - s0;
-    const bool pred = (variant == VAR_PCFR_PLUS);
+    const bool pred = predictive(variant);
     float ev = 0.f;
     for (int s = s0; s < s1; s++) {
         const float v = value_of(P, s);

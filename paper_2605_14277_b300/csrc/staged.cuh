@@ -518,7 +518,7 @@ __device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int 
         const float d = V[a] - ev;
         const float2 r = post_op_v<VAR>(ff_add_f(rr[a], d), fpos, fneg);
         if (a < na) t.r[q0 + a] = r;
-        const float x = VAR == VAR_PCFR_PLUS ? r.x + d : r.x;
+        const float x = predictive(VAR) ? r.x + d : r.x;
         qv[a] = (a < na && x > 0.f) ? x : 0.f;
         pos += qv[a];
     }
@@ -541,7 +541,7 @@ __device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float
         const float d = t.V[q] - ev;
         const float2 r = post_op_v<VAR>(ff_add_f(t.r[q], d), fpos, fneg);
         t.r[q] = r;
-        const float rr = VAR == VAR_PCFR_PLUS ? r.x + d : r.x;
+        const float rr = predictive(VAR) ? r.x + d : r.x;
         const float qq = rr > 0.f ? rr : 0.f;
         t.V[q] = qq;   // V is no longer needed: keep the clipped regret
         pos += qq;
@@ -688,6 +688,7 @@ __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, con
     case VAR_PLUS: up_levels<VAR_PLUS>(ip, nl, lv, tab, cev, internal); break;
     case VAR_DCFR: up_levels<VAR_DCFR>(ip, nl, lv, tab, cev, internal); break;
     case VAR_PCFR_PLUS: up_levels<VAR_PCFR_PLUS>(ip, nl, lv, tab, cev, internal); break;
+    case VAR_PCFR: up_levels<VAR_PCFR>(ip, nl, lv, tab, cev, internal); break;
     default: up_levels<VAR_CFR>(ip, nl, lv, tab, cev, internal); break;
     }
     if (root) root_topdown(nl, lv, tab);

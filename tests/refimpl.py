@@ -199,7 +199,7 @@ def brute_force(sf: SeqForm):
 class ClassicalCFR:
     """Tree-walk CFR over histories (regret/average tables per infoset).
 
-    variant: 'cfr', 'cfr+', 'dcfr', 'pcfr+'; the predictive step uses the
+    variant: 'cfr', 'cfr+', 'dcfr', 'pcfr+', 'pcfr'; the predictive step uses the
     instantaneous counterfactual regret of the last traversal (the prediction
     m = last utility valued under the last strategy)."""
 
@@ -269,7 +269,7 @@ class ClassicalCFR:
                 r = np.where(r > 0, r * fp, np.where(r < 0, r * fn, r))
             self.R[key] = r
         for key, d in inst.items():
-            if variant == "pcfr+":
+            if variant in ("pcfr+", "pcfr"):
                 self.sigma[key] = self.rm(self.R[key] + d)
             else:
                 self.sigma[key] = self.rm(self.R[key])
@@ -302,7 +302,7 @@ class ClassicalCFR:
                         self.R[key] = r
                 for p in (P1, P2):
                     for key, d in inst[p].items():
-                        self.sigma[key] = self.rm(self.R[key] + d if variant == "pcfr+" else self.R[key])
+                        self.sigma[key] = self.rm(self.R[key] + d if variant in ("pcfr+", "pcfr") else self.R[key])
                 del saved
 
     def regrets(self, p, sf: SeqForm):

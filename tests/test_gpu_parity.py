@@ -21,7 +21,7 @@ from tests.parity_util import EXPL_RTOL, ONE_STEP_RTOL, random_state, rel, strat
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["cfr", "cfr+", "dcfr", "pcfr+"]
+VARIANTS = ["cfr", "cfr+", "dcfr", "pcfr+", "pcfr"]
 
 
 @pytest.fixture(scope="module")
@@ -225,7 +225,7 @@ def check_step_from_gpu_state(s, tree, variant):
     return e_g
 
 
-@pytest.mark.parametrize("variant", ["cfr+", "dcfr", "pcfr+"])
+@pytest.mark.parametrize("variant", ["cfr+", "dcfr", "pcfr+", "pcfr"])
 def test_poker_trajectory_10k(cfr, variant):
     """Poker, 10^4 iterations: one iteration from the GPU's state at t = 1000,
     5000 and 9999 matches the oracle (1e-5) and both compute the same FP64

@@ -94,7 +94,7 @@ def test_brute_force_equals_sequence_form_lp():
         assert abs(v - vb) < 1e-9, t.name
 
 
-@pytest.mark.parametrize("variant", ["cfr", "cfr+", "dcfr", "pcfr+"])
+@pytest.mark.parametrize("variant", ["cfr", "cfr+", "dcfr", "pcfr+", "pcfr"])
 def test_oracle_brackets_lp_value(variant):
     games = tiny_games() + [G.small_random_game(1)]
     for t in games:
@@ -150,7 +150,8 @@ def test_payoff_matrix_products():
 
 @pytest.mark.parametrize("variant,alt,gamma", [("cfr", False, 0.0), ("cfr+", True, 1.0),
                                                ("dcfr", True, 2.0), ("pcfr+", True, 2.0),
-                                               ("cfr+", False, 1.0), ("dcfr", False, 2.0)])
+                                               ("cfr+", False, 1.0), ("dcfr", False, 2.0),
+                                               ("pcfr", True, 0.0), ("pcfr", False, 1.0)])
 def test_classical_cfr_same_iterates(variant, alt, gamma):
     # continuous payoffs: with integer payoffs, mathematically-zero regrets come
     # out as +-1e-17 in one formulation and 0 in the other, and regret matching's
