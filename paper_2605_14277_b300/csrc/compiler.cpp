@@ -14,6 +14,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <numeric>
 #include <thread>
 
@@ -152,6 +153,13 @@ bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
     }
     // terminals
     double mn = INFINITY, mx = -INFINITY;
+    {
+        int64_t nt = 0;
+        for (int64_t i = 0; i < n; i++) nt += t.kind[i] == K_TERM;
+        g->ts1.reserve(nt);
+        g->ts2.reserve(nt);
+        g->tw.reserve(nt);
+    }
     for (int64_t i = 0; i < n; i++) {
         if (t.kind[i] != K_TERM) continue;
         g->ts1.push_back(seq1[i]);
@@ -335,24 +343,33 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 col[k] = fseq(1, g, gs[g].ts2[z]);
                 val[k] = gs[g].tw[z];
             }
-        // merge duplicates within each row (sorted by column, stable)
+        // merge duplicates within each row (sorted by column, stable: the
+        // entries of one column are added in terminal order).  Rows are
+        // short, so each is sorted in place by insertion (stable).
         A.m_ptr.assign(A.S + 1, 0);
         A.m_col.clear();
         A.m_val64.clear();
-        std::vector<std::pair<int32_t, double>> row;
+        A.m_col.reserve(Z0);
+        A.m_val64.reserve(Z0);
         for (int64_t r = 0; r < A.S; r++) {
-            row.clear();
-            for (int32_t k = cnt[r]; k < cnt[r + 1]; k++) row.push_back({col[k], val[k]});
-            std::stable_sort(row.begin(), row.end(),
-                             [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
-                                 return a.first < b.first;
-                             });
-            for (size_t k = 0; k < row.size(); k++) {
-                if ((int64_t)A.m_col.size() > A.m_ptr[r] && A.m_col.back() == row[k].first)
-                    A.m_val64.back() += row[k].second;
+            const int32_t k0 = cnt[r], k1 = cnt[r + 1];
+            for (int32_t k = k0 + 1; k < k1; k++) {
+                const int32_t c = col[k];
+                const double v = val[k];
+                int32_t m = k;
+                for (; m > k0 && col[m - 1] > c; m--) {
+                    col[m] = col[m - 1];
+                    val[m] = val[m - 1];
+                }
+                col[m] = c;
+                val[m] = v;
+            }
+            for (int32_t k = k0; k < k1; k++) {
+                if ((int64_t)A.m_col.size() > A.m_ptr[r] && A.m_col.back() == col[k])
+                    A.m_val64.back() += val[k];
                 else {
-                    A.m_col.push_back(row[k].first);
-                    A.m_val64.push_back(row[k].second);
+                    A.m_col.push_back(col[k]);
+                    A.m_val64.push_back(val[k]);
                 }
             }
             A.m_ptr[r + 1] = (int32_t)A.m_col.size();
@@ -379,7 +396,8 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
     }
     // ---- units: per game and player, a tree of units, each of which fits one
     // shared-memory buffer ----------------------------------------------------
-    for (int p = 0; p < 2; p++) {
+    // (the two players are independent: player 2 on a second thread)
+    auto player_units = [&](int p) {
         PlayerLayout &P = L.pl[p];
         const auto &glv = glvs[p];
         const int64_t J = P.J;
@@ -735,6 +753,25 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             if (P.dunits[a].depth != P.dunits[b].depth) return P.dunits[a].depth < P.dunits[b].depth;
             return dsz[a] > dsz[b];
         });
+    };
+    {
+        std::exception_ptr e2;
+        std::thread t2([&]() {
+            try {
+                player_units(1);
+            } catch (...) {
+                e2 = std::current_exception();
+            }
+        });
+        std::exception_ptr e1;
+        try {
+            player_units(0);
+        } catch (...) {
+            e1 = std::current_exception();
+        }
+        t2.join();
+        if (e1) std::rethrow_exception(e1);
+        if (e2) std::rethrow_exception(e2);
     }
     L.game_nnz.assign(G, 0);
     for (int64_t r = 0; r < L.pl[0].S; r++)
