@@ -14,7 +14,6 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
-#include <exception>
 #include <numeric>
 #include <thread>
 
@@ -396,8 +395,7 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
     }
     // ---- units: per game and player, a tree of units, each of which fits one
     // shared-memory buffer ----------------------------------------------------
-    // (the two players are independent: player 2 on a second thread)
-    auto player_units = [&](int p) {
+    for (int p = 0; p < 2; p++) {
         PlayerLayout &P = L.pl[p];
         const auto &glv = glvs[p];
         const int64_t J = P.J;
@@ -753,25 +751,6 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             if (P.dunits[a].depth != P.dunits[b].depth) return P.dunits[a].depth < P.dunits[b].depth;
             return dsz[a] > dsz[b];
         });
-    };
-    {
-        std::exception_ptr e2;
-        std::thread t2([&]() {
-            try {
-                player_units(1);
-            } catch (...) {
-                e2 = std::current_exception();
-            }
-        });
-        std::exception_ptr e1;
-        try {
-            player_units(0);
-        } catch (...) {
-            e1 = std::current_exception();
-        }
-        t2.join();
-        if (e1) std::rethrow_exception(e1);
-        if (e2) std::rethrow_exception(e2);
     }
     L.game_nnz.assign(G, 0);
     for (int64_t r = 0; r < L.pl[0].S; r++)
