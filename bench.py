@@ -585,7 +585,14 @@ def run_serve(args):
     sampler = ClockSampler(gpu_uuid(local))
     sampler.start()
     from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max_workers=2, initializer=torch.cuda.set_device, initargs=(local,)) as pool:
+    with ThreadPoolExecutor(max_workers=args.serve_loaders, initializer=torch.cuda.set_device,
+                            initargs=(local,)) as pool:
+        # every loader thread, with its device set-up, before the server
+        # starts: a thread's first CUDA calls can invalidate a graph capture
+        # running on another thread
+        import threading
+        gate = threading.Barrier(args.serve_loaders)
+        list(pool.map(lambda _: gate.wait(timeout=60), range(args.serve_loaders)))
         srv = SV.Server(factory, hbm_budget=args.serve_budget_gb * 1e9, round_iters=64, variant="dcfr",
                         target_rel=1e-3, max_cohort_nodes=args.serve_cohort_nodes,
                         stream_factory=torch.cuda.Stream, loader=pool.submit)
@@ -606,7 +613,7 @@ def run_serve(args):
             "dtype": "f32 passes, f32+f32 (Kahan) accumulators, f64 best response", "data": "synthetic",
             "config": {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s, nodes log-uniform in [1e3, 1e6]",
                        "nodes": nodes, "variant": "dcfr(1.5,0,2)", "round_iterations": 64,
-                       "cohort_nodes_max": args.serve_cohort_nodes, "loader_threads": 2,
+                       "cohort_nodes_max": args.serve_cohort_nodes, "loader_threads": args.serve_loaders,
                        "hbm_budget_gb": args.serve_budget_gb, "parallelism": f"replicas x{world}"},
             "latency": {"p50_s": st["p50_latency_s"], "p99_s": st["p99_latency_s"]},
             "serving": st,
@@ -657,6 +664,9 @@ def main():
     ap.add_argument("--serve-time-limit", type=float, default=120.0)
     ap.add_argument("--serve-baseline", type=int, default=16)
     ap.add_argument("--serve-cohort-nodes", type=float, default=4e6)
+    ap.add_argument("--serve-loaders", type=int, default=max(2, min(8, (os.cpu_count() or 4) // 2)),
+                    help="host threads compiling and uploading admitted cohorts (default: half the cores, "
+                         "at most 8)")
     ap.add_argument("--batch-games", type=int, default=4096)
     ap.add_argument("--per-game-sample", type=int, default=128)
     ap.add_argument("--tune-budget", type=float, default=60.0)

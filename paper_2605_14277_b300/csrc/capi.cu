@@ -858,6 +858,18 @@ namespace {
         if (rc_) return rc_; \
     } while (0)
 
+// The CUDA set-up work of every context -- loading (allocations, uploads,
+// first kernels), graph capture and instantiation, and freeing -- runs under
+// one process-wide lock.  A graph capture in one thread then never overlaps
+// another thread's allocation, free or kernel-module load through this
+// library, any of which can invalidate the capture (contexts loaded on
+// worker threads while another thread iterates).  The host compile of a load
+// runs outside the lock.
+std::recursive_mutex &setup_mutex() {
+    static std::recursive_mutex m;
+    return m;
+}
+
 template <class T>
 int dalloc(cfr_ctx *c, T **p, size_t n) {
     void *q = nullptr;
@@ -1169,6 +1181,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
         return set_err(CFR_ERR_INVALID, e.what());
     }
     if (rc != ST_OK) return set_err(rc == ST_OOM ? CFR_ERR_OOM : CFR_ERR_INVALID, err);
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
     cfr_ctx *c = new (std::nothrow) cfr_ctx();
     if (!c) return set_err(CFR_ERR_OOM, "context allocation");
     auto bail = [&](int code) {
@@ -1256,6 +1269,7 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
         auto f = c->graphs.find(key);
         cudaGraphExec_t exec = nullptr;
         if (f == c->graphs.end()) {
+            std::lock_guard<std::recursive_mutex> setup(setup_mutex());
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = CFR_OK;
@@ -1598,6 +1612,7 @@ int cfr_sync(cfr_ctx *ctx) {
 
 void cfr_free(cfr_ctx *ctx) {
     if (!ctx) return;
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     for (void *p : ctx->allocs) cudaFree(p);

@@ -88,7 +88,10 @@ class Server:
         self.max_cohort_nodes = float(max_cohort_nodes)
         self.stream_factory = stream_factory or (lambda: None)
         # loader(fn) -> a future-like object with done() and result(); None
-        # loads synchronously in the scheduling loop
+        # loads synchronously in the scheduling loop.  A thread pool's threads
+        # should all exist, with their device set up, before run(): a
+        # thread's first CUDA calls can invalidate a CUDA-graph capture that
+        # the scheduling loop has in progress
         self.loader = loader
         self.clock = clock
         self.max_iterations = int(max_iterations)
