@@ -51,6 +51,13 @@ def workload(name, variant=None):
     return tree, (variant or v)
 
 
+def workload_config(tree, variant):
+    """The keys that name a single-game workload, shared by both arms' lines."""
+    return {"workload": tree.name, "nodes": tree.n_nodes, "terminals": int((tree.kind == 3).sum()),
+            "variant": variant + "(1.5,0,2)" if variant == "dcfr" else variant,
+            "updates": "alternating" if variant != "cfr" else "simultaneous"}
+
+
 def _workload(name):
     if name == "large":
         return G.large_random_game(3), "dcfr"
@@ -233,7 +240,8 @@ def run_reference_batch(args):
     line = {"metric": "node-updates/s per CFR iteration (CFR+, 4096-game batch)", "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / k,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": f"batch of {args.batch_games} random games", "variant": "cfr+"},
+            "impl": "reference", "config": {"workload": f"batch of {args.batch_games} random games, nodes log-uniform in [1e2, 1e5]",
+                                               "games": args.batch_games, "variant": "cfr+", "updates": "alternating"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -270,7 +278,8 @@ def run_reference_serve(args):
             "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": done, "warmup": 0,
             "ms_per_step": 1e3 * el / max(done, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s", "variant": "dcfr(1.5,0,2)"},
+            "config": {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s, nodes log-uniform in [1e3, 1e6]",
+                       "variant": "dcfr(1.5,0,2)"},
             "latency": {"p50_s": float(np.percentile(lat, 50)) if lat else None,
                         "p99_s": float(np.percentile(lat, 99)) if lat else None},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -304,7 +313,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": tree.name, "nodes": tree.n_nodes, "variant": variant},
+            "config": workload_config(tree, variant),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -395,10 +404,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 passes, f32+f32 (Kahan) accumulators, f64 best response",
             "data": "synthetic",
-            "config": {"workload": tree.name, "nodes": tree.n_nodes, "terminals": int((tree.kind == 3).sum()),
+            "config": {**workload_config(tree, variant),
                        "S1": sz["S1"], "S2": sz["S2"], "J1": sz["J1"], "J2": sz["J2"], "nnz": sz["nnz"],
-                       "variant": variant + "(1.5,0,2)" if variant == "dcfr" else variant,
-                       "updates": "alternating" if variant != "cfr" else "simultaneous",
                        "l2": f"inputs larger than L2: {sz['device_bytes'] / 2**20:.0f} MiB resident vs 126 MiB L2",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": 4 * args.steps,
