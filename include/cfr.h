@@ -119,10 +119,16 @@ typedef struct {
 int cfr_load_batch_opts(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream,
                         const cfr_load_options *options, cfr_ctx **out);
 
-/* Number of launch shapes (shape indices 1..cfr_num_shapes()), and the shape
- * that options.shape = 0 selects. */
+/* Number of launch shapes (shape indices 1..cfr_num_shapes()); the shape that
+ * options.shape = 0 selects for a single game of at least 1M nodes
+ * (cfr_default_shape); and the shape it selects for any load of n_games games
+ * of total_nodes nodes in all (cfr_pick_shape: the default shape for one
+ * game of at least 1M nodes, else the 256-thread, 3-CTA, 32 KB shape, which
+ * runs batches and small games faster; CFR_ERR_ARG unless both counts are
+ * positive). */
 int cfr_num_shapes(void);
 int cfr_default_shape(void);
+int cfr_pick_shape(int64_t n_games, int64_t total_nodes);
 
 /* Launch shape k: host_out3 = {threads per CTA, CTAs per SM, unit buffer
  * bytes}.  CFR_ERR_ARG for k outside 1..cfr_num_shapes(). */

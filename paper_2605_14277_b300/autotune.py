@@ -29,7 +29,8 @@ def tune(trees, variant="cfr+", iterations=64, repeats=3, candidates=None, strea
 
     if candidates is None:
         shapes = sorted(C.shapes())
-        default = C.default_shape()
+        ts = trees if isinstance(trees, (list, tuple)) else [trees]
+        default = C.pick_shape(len(ts), sum(t.n_nodes for t in ts))
         order = [default] + [k for k in shapes if k != default]
         candidates = [(k, flat, passes) for k in order for flat in (False, True) for passes in (1, 2)]
     st = stream if stream is not None else torch.cuda.Stream()

@@ -55,6 +55,7 @@ def lib():
                                           ctypes.POINTER(P)]
         L.cfr_num_shapes.argtypes = []
         L.cfr_default_shape.argtypes = []
+        L.cfr_pick_shape.argtypes = [ctypes.c_int64, ctypes.c_int64]
         L.cfr_shape_info.argtypes = [i, P]
         L.cfr_iterate.argtypes = [P, i64, i, d, d, d]
         L.cfr_iterate_batch.argtypes = [P, i64, i, d, d, d, P]
@@ -80,8 +81,16 @@ def lib():
 
 
 def default_shape() -> int:
-    """The launch shape the library uses when none is chosen."""
+    """The launch shape the library uses for a single large game when none is chosen."""
     return int(lib().cfr_default_shape())
+
+
+def pick_shape(n_games: int, total_nodes: int) -> int:
+    """The launch shape the library uses, when none is chosen, for a load of
+    n_games games of total_nodes nodes in all."""
+    k = int(lib().cfr_pick_shape(int(n_games), int(total_nodes)))
+    _check(min(k, 0), "cfr_pick_shape")
+    return k
 
 
 def shapes():

@@ -57,6 +57,16 @@ def test_calls_that_need_no_device(lib):
         assert per_sm * (2 * buf + 8 * 1024) <= 228 * 1024
     assert lib.cfr_shape_info(0, out) == -6
     assert lib.cfr_shape_info(n + 1, out) == -6
+    # the shape chosen when none is given: the default for one game of at
+    # least 1M nodes, the 256-thread, 3-CTA, 32 KB shape otherwise
+    lib.cfr_pick_shape.argtypes = [ctypes.c_int64, ctypes.c_int64]
+    d = lib.cfr_default_shape()
+    assert lib.cfr_pick_shape(1, 6_000_000) == d
+    many = lib.cfr_pick_shape(64, 2_000_000)
+    assert lib.cfr_pick_shape(1, 10_000) == many and many != d
+    out3 = (ctypes.c_int32 * 3)()
+    assert lib.cfr_shape_info(many, out3) == 0 and list(out3) == [256, 3, 32768]
+    assert lib.cfr_pick_shape(0, 10) == -6 and lib.cfr_pick_shape(1, 0) == -6
 
 
 class _Opts(ctypes.Structure):
