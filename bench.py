@@ -591,15 +591,8 @@ def run_serve(args):
     reqs = SV.make_requests(trees, arrivals)
     sampler = ClockSampler(gpu_uuid(local))
     sampler.start()
-    from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max_workers=args.serve_loaders, initializer=torch.cuda.set_device,
-                            initargs=(local,)) as pool:
-        # every loader thread, with its device set-up, before the server
-        # starts: a thread's first CUDA calls can invalidate a graph capture
-        # running on another thread
-        import threading
-        gate = threading.Barrier(args.serve_loaders)
-        list(pool.map(lambda _: gate.wait(timeout=60), range(args.serve_loaders)))
+    # every loader thread started, with its device set, before the server runs
+    with SV.loader_pool(args.serve_loaders, initializer=torch.cuda.set_device, initargs=(local,)) as pool:
         srv = SV.Server(factory, hbm_budget=args.serve_budget_gb * 1e9, round_iters=64, variant="dcfr",
                         target_rel=1e-3, max_cohort_nodes=args.serve_cohort_nodes,
                         stream_factory=torch.cuda.Stream, loader=pool.submit)

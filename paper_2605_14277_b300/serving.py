@@ -89,9 +89,9 @@ class Server:
         self.stream_factory = stream_factory or (lambda: None)
         # loader(fn) -> a future-like object with done() and result(); None
         # loads synchronously in the scheduling loop.  A thread pool's threads
-        # should all exist, with their device set up, before run(): a
-        # thread's first CUDA calls can invalidate a CUDA-graph capture that
-        # the scheduling loop has in progress
+        # should all exist, with their device set up, before run() (see
+        # loader_pool): a thread's first CUDA calls can invalidate a CUDA-graph
+        # capture that the scheduling loop has in progress
         self.loader = loader
         self.clock = clock
         self.max_iterations = int(max_iterations)
@@ -217,6 +217,28 @@ class Server:
             "cohorts": self.n_cohorts, "peak_bytes": self.peak_in_use, "budget_bytes": self.budget,
             "rejected": len(self.rejected),
         }
+
+
+def loader_pool(n_threads: int, initializer: Optional[Callable] = None, initargs=(), timeout: float = 60.0):
+    """A thread pool for ``Server(loader=pool.submit)`` whose threads all
+    exist, each past ``initializer(*initargs)`` (e.g. selecting the device),
+    when it is returned.  A pool thread that starts later, while the
+    scheduling loop is capturing a cohort's CUDA graph, can invalidate that
+    capture with its first CUDA calls.  The caller shuts the pool down (or
+    uses it as a context manager)."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    n = max(1, int(n_threads))
+    pool = ThreadPoolExecutor(max_workers=n, initializer=initializer, initargs=tuple(initargs))
+    gate = threading.Barrier(n)
+    try:
+        # n tasks that wait for one another can only finish on n threads
+        list(pool.map(lambda _: gate.wait(timeout=timeout), range(n)))
+    except BaseException:
+        pool.shutdown(wait=False)
+        raise
+    return pool
 
 
 def serve_one_at_a_time(solver_factory: Callable, requests: List[Request], round_iters: int = 64,

@@ -128,3 +128,25 @@ def test_background_loader():
     assert st["completed"] == len(rq)
     assert st["cohorts"] >= 2          # the node cap splits the arrivals
     assert srv.in_use == 0
+
+
+def test_loader_pool_starts_every_thread_first():
+    # every pool thread exists and has run its initializer before the pool is
+    # handed to the server (a late-starting thread's first CUDA calls could
+    # invalidate a graph capture in progress)
+    import threading
+    seen = []
+    lock = threading.Lock()
+
+    def init(tag):
+        with lock:
+            seen.append((tag, threading.get_ident()))
+
+    pool = S.loader_pool(5, initializer=init, initargs=("dev0",))
+    try:
+        assert len(seen) == 5 and len({t for _, t in seen}) == 5 and all(tag == "dev0" for tag, _ in seen)
+        # later work reuses those threads
+        ids = set(pool.map(lambda _: threading.get_ident(), range(20)))
+        assert ids <= {t for _, t in seen}
+    finally:
+        pool.shutdown()
