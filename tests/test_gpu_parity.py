@@ -345,6 +345,56 @@ def test_checkpoint_resume(cfr):
         assert x["t"] == y["t"] == 100
 
 
+def _tree(parent, kind, infoset, action, prob, payoff):
+    return G.Tree(np.array(parent, np.int32), np.array(kind, np.int8), np.array(infoset, np.int32),
+                  np.array(action, np.int32), np.array(prob, np.float64), np.array(payoff, np.float64))
+
+
+def degenerate_games():
+    return {
+        # the root is a terminal: no sequence but the empty one for either player
+        "terminal_root": _tree([-1], [3], [-1], [0], [1.0], [2.5]),
+        # chance alone decides
+        "chance_only": _tree([-1, 0, 0], [0, 3, 3], [-1, -1, -1], [0, 0, 1], [1.0, 0.3, 0.7], [0.0, 1.0, -2.0]),
+        # only player 1 decides (player 2 has the empty sequence only)
+        "p1_only": _tree([-1, 0, 0, 0], [1, 3, 3, 3], [0, -1, -1, -1], [0, 0, 1, 2], [1.0] * 4, [0.0, 1.0, -2.0, 0.5]),
+        # only player 2 decides, below a chance node
+        "p2_only": _tree([-1, 0, 0, 1, 1, 2, 2], [0, 2, 2, 3, 3, 3, 3], [-1, 0, 0, -1, -1, -1, -1],
+                         [0, 0, 1, 0, 1, 0, 1], [1.0, 0.5, 0.5, 1.0, 1.0, 1.0, 1.0],
+                         [0.0, 0.0, 0.0, 1.0, -1.0, 2.0, 0.0]),
+    }
+
+
+@pytest.mark.parametrize("variant", ["cfr", "cfr+", "dcfr", "pcfr+"])
+def test_degenerate_games_match_oracle(cfr, variant):
+    games = degenerate_games()
+    trees = list(games.values()) + [G.poker_game()]
+    batch = cfr.Solver(trees)
+    batch.iterate(12, variant)
+    eb, b1b, b2b = batch.exploitability_batch()
+    for k, (name, t) in enumerate(games.items()):
+        o = Oracle(t)
+        o.iterate(12, variant)
+        s = cfr.Solver(t)
+        s.iterate(12, variant)
+        e_o, b1_o, b2_o = o.exploitability()
+        e_g, b1_g, b2_g = s.exploitability()
+        # FP32 strategies against the FP64 oracle: exploitability to the
+        # suite's relative bar, best-response values to the one-step bar
+        for got in ((e_g, b1_g, b2_g), (eb[k], b1b[k], b2b[k])):
+            assert abs(got[0] - e_o) <= EXPL_RTOL * abs(e_o) + 1e-9, (name, got, (e_o, b1_o, b2_o))
+            assert np.allclose(got[1:], (b1_o, b2_o), rtol=ONE_STEP_RTOL, atol=1e-9), (name, got, (e_o, b1_o, b2_o))
+        for p in (1, 2):
+            g_, o_ = s.get_state(p), o.get_state(p)
+            assert g_["t"] == o_["t"] == 12
+            assert np.allclose(g_["r"], o_["r"], rtol=1e-5, atol=1e-6), (name, p)
+            assert np.allclose(g_["xbar"], o_["xbar"], rtol=1e-5, atol=1e-6), (name, p)
+            a = batch.get_state(p, game=k)
+            assert np.array_equal(a["r"], g_["r"]) and np.array_equal(a["xbar"], g_["xbar"]), (name, p)
+        s.close()
+    batch.close()
+
+
 def test_invalid_trees_rejected(cfr):
     base = G.small_random_game(1)
     bad = G.Tree(base.parent.copy(), base.kind.copy(), base.infoset.copy(), base.action.copy(),
