@@ -165,7 +165,7 @@ class Solver:
         self._h = h
         self.n_games = len(trees)
         self.batch = batch
-        self._sizes = [self.sizes(g) for g in range(self.n_games)]
+        self._sizes = {}   # per game, read on first use (each read waits for the stream)
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
@@ -173,6 +173,11 @@ class Solver:
             self._h = None
 
     __del__ = close
+
+    def _game_sizes(self, game: int) -> dict:
+        if game not in self._sizes:
+            self._sizes[game] = self.sizes(game)
+        return self._sizes[game]
 
     def sizes(self, game: int = 0) -> dict:
         out = np.zeros(10, dtype=np.int64)
@@ -226,13 +231,13 @@ class Solver:
                "cfr_exploitability_batch_noalloc")
 
     def average_strategy(self, player: int, game: int = 0):
-        S = self._sizes[game]["S1" if player == 1 else "S2"]
+        S = self._game_sizes(game)["S1" if player == 1 else "S2"]
         out = np.zeros(S)
         _check(lib().cfr_get_average_strategy(self._h, game, player, _ptr(out), S), "cfr_get_average_strategy")
         return out
 
     def get_state(self, player: int, game: int = 0):
-        S = self._sizes[game]["S1" if player == 1 else "S2"]
+        S = self._game_sizes(game)["S1" if player == 1 else "S2"]
         r, b, xb = np.zeros(S), np.zeros(S), np.zeros(S + 1)
         t = ctypes.c_int64()
         _check(lib().cfr_get_state(self._h, game, player, _ptr(r), _ptr(b), _ptr(xb), ctypes.byref(t)),
@@ -240,7 +245,7 @@ class Solver:
         return {"r": r, "b": b, "xbar": xb, "t": t.value}
 
     def set_state(self, player: int, r, b, xbar, t: int, game: int = 0):
-        S = self._sizes[game]["S1" if player == 1 else "S2"]
+        S = self._game_sizes(game)["S1" if player == 1 else "S2"]
         r = np.ascontiguousarray(r, np.float64)
         b = np.ascontiguousarray(b, np.float64)
         xbar = np.ascontiguousarray(xbar, np.float64)
