@@ -81,6 +81,31 @@ def test_one_iteration_from_identical_state(cfr, name, variant, mode):
         assert strategy_mismatch_ok(g_["b"], o_["b"], o_["r"], na) == 0, ("b", p)
 
 
+@pytest.mark.parametrize("variant,alpha,beta,gamma", [("dcfr", 1.0, 0.5, 3.0), ("dcfr", 2.0, -0.5, 0.0),
+                                                      ("pcfr", 0.0, 0.0, 1.5), ("cfr+", 0.0, 0.0, 2.0)])
+@pytest.mark.parametrize("mode", ["alternating", "simultaneous"])
+def test_one_iteration_other_parameters(cfr, variant, alpha, beta, gamma, mode):
+    # non-default discount and averaging exponents (the per-iteration
+    # parameter table), one iteration from identical state
+    tree = G.random_game(11, depth=8, chance={0: 4, 4: 3}, actions=(2, 3, 4), payoff="normal")
+    o = Oracle(tree)
+    s = cfr.Solver(tree)
+    s.set_update_mode(mode)
+    rng = np.random.default_rng(zlib.crc32(f"{variant}/{alpha}/{beta}/{gamma}/{mode}".encode()))
+    for p in (1, 2):
+        r, b, xb, t = random_state(o, p, rng)
+        o.set_state(p, r, b, xb, t)
+        s.set_state(p, r, b, xb, t)
+    o.iterate(1, variant, alpha=alpha, beta=beta, gamma=gamma, alternating=(mode == "alternating"))
+    s.iterate(1, variant, alpha=alpha, beta=beta, gamma=gamma)
+    for p in (1, 2):
+        g_, o_ = s.get_state(p), o.get_state(p)
+        assert rel(g_["r"], o_["r"]) <= ONE_STEP_RTOL, ("r", p)
+        assert rel(g_["xbar"], o_["xbar"]) <= ONE_STEP_RTOL, ("xbar", p)
+        _, na = o.infosets(p)
+        assert strategy_mismatch_ok(g_["b"], o_["b"], o_["r"], na) == 0, ("b", p)
+
+
 def test_one_iteration_inside_a_batch(cfr):
     others = [G.sized_random_game(40 + k, 10 ** (2 + k % 3)) for k in range(5)]
     tree = G.poker_game()

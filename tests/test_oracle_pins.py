@@ -171,6 +171,22 @@ def test_classical_cfr_same_iterates(variant, alt, gamma):
             assert np.allclose(o.average_strategy(p), c.average(p, sf), rtol=1e-10, atol=1e-12)
 
 
+@pytest.mark.parametrize("alt", [True, False])
+def test_classical_cfr_same_iterates_dcfr_other_parameters(alt):
+    # DCFR with beta != 0 (the negative-regret factor t^b/(t^b+1) then varies
+    # with t) and a cubic average, against the tree walk
+    t = G.random_game(2, depth=6, chance={0: 3}, actions=(2, 3), payoff="normal")
+    sf = SeqForm(t)
+    o = Oracle(t)
+    o.iterate(30, "dcfr", alpha=1.0, beta=0.5, gamma=3.0, alternating=alt)
+    c = ClassicalCFR(t)
+    c.iterate(30, "dcfr", alternating=alt, alpha=1.0, beta=0.5, gamma=3.0)
+    for p in (1, 2):
+        r_c = c.regrets(p, sf)
+        assert np.allclose(o.get_state(p)["r"], r_c, rtol=1e-10, atol=1e-10 * max(1.0, np.abs(r_c).max()))
+        assert np.allclose(o.average_strategy(p), c.average(p, sf), rtol=1e-10, atol=1e-12)
+
+
 def test_alg2_literal_matches_oracle_steps():
     rng = np.random.default_rng(3)
     for t in [G.small_random_game(1), G.poker_game()] + tiny_games()[:2]:
