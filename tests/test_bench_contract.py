@@ -47,3 +47,11 @@ def test_reference_arm_other_ranks_do_nothing():
                   {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+
+
+def test_reference_arm_variant_flag():
+    r = run_bench(["--impl", "reference", "--workload", "poker", "--variant", "pcfr", "--steps", "3", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")][0])
+    assert d["config"]["variant"] == "pcfr" and d["config"]["updates"] == "alternating"
+    assert "pcfr iterations" in d["cpu_baseline"]["sample"]
