@@ -101,6 +101,14 @@ def profiled_traffic(kernel_slot):
     return None
 
 
+def graph_length(steps, warmup, cap=64):
+    """Iterations per CUDA graph for the timed run: the largest k <= cap that
+    divides both step counts."""
+    import math
+    g = math.gcd(max(1, steps), max(1, warmup))
+    return max(d for d in range(1, min(cap, g) + 1) if g % d == 0)
+
+
 def alg_bytes(sz):
     """Algorithmic bytes per launch (forest totals include one root per game).
 
@@ -337,7 +345,12 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     s = C.Solver(tree, stream=stream)
     sz = s.sizes()
-    s.iterate(args.warmup, variant)   # untimed: graphs captured, caches warm
+    # the product path: CUDA graphs of k iterations, k dividing both the
+    # warm-up and the timed step counts (so the warm-up captures the graph the
+    # timed region replays; every k computes the same iterations)
+    k_graph = graph_length(args.steps, args.warmup)
+    s.set_graph_iterations(k_graph)
+    s.iterate(args.warmup, variant)   # untimed: graph captured, caches warm
     s.sync()
     props = torch.cuda.get_device_properties(local)
     gpu_id = local
@@ -352,11 +365,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    n_launch0 = s.kernel_launches()
     e0.record(stream)
     s.iterate(args.steps, variant)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
+    n_launch = s.kernel_launches() - n_launch0
     if dist:
         dist.barrier()
     clocks = sampler.stop()
@@ -376,6 +391,7 @@ def run_ours(args):
     dom = max(names, key=lambda n: avg_ms[n])
     hbm, src = peaks()
     achieved = kbytes[dom] / (avg_ms[dom] * 1e-3) / 1e9
+    traffic = profiled_traffic(dom)
     iter_bytes = sum(kbytes.values())
     value = sum_over_ranks(tree.n_nodes * args.steps, dist) / (ms * 1e-3)
     if rank == 0:
@@ -407,10 +423,13 @@ def run_ours(args):
             "config": {**workload_config(tree, variant),
                        "S1": sz["S1"], "S2": sz["S2"], "J1": sz["J1"], "J2": sz["J2"], "nnz": sz["nnz"],
                        "l2": f"inputs larger than L2: {sz['device_bytes'] / 2**20:.0f} MiB resident vs 126 MiB L2",
-                       "parallelism": f"replicas x{world}"},
-            "gpu_launches": 4 * args.steps,
+                       "parallelism": f"replicas x{world}",
+                       "cuda_graph_iterations": k_graph},
+            "gpu_launches": n_launch,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": profiled_traffic(dom),
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "dram_GBps": (traffic / (avg_ms[dom] * 1e-3) / 1e9) if traffic else None,
+                         "dram_frac": (traffic / (avg_ms[dom] * 1e-3) / 1e9 / hbm) if traffic else None,
                          "kernel": f"{'k_up_staged' if dom.startswith('up') else 'k_down_staged'} ({dom})",
                          "alg_bytes_per_launch": kbytes[dom], "avg_launch_us": avg_ms[dom] * 1e3,
                          "peak_source": src},
@@ -483,11 +502,13 @@ def run_batch(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    n_launch0 = s.kernel_launches()
     e0.record(stream)
     s.iterate(args.steps, variant)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
+    n_launch = s.kernel_launches() - n_launch0
     if dist:
         dist.barrier()
     clocks = sampler.stop()
@@ -546,7 +567,8 @@ def run_batch(args):
                        "launches_per_player": 1 if tuned["passes"] == 1 else 2,
                        "shape_info": C.shapes()[tuned["shape"]],
                        "l2": f"inputs larger than L2: {iter_bytes / 2**20:.0f} MiB streamed per iteration vs 126 MiB L2",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "cuda_graph_iterations": k_graph},
             "gpu_launches": (2 if tuned["passes"] == 1 else 4) * args.steps + (args.steps + 63) // 64,
             "roofline": {"bound": "hbm", "achieved": iter_bytes / (ms / args.steps * 1e-3) / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": iter_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm, "traffic": None,

@@ -103,6 +103,14 @@ int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_strea
  *          of a game start as soon as that game's bottom-up pass is complete;
  *          2 = two kernels; 0 = the library's choice (two kernels, the faster
  *          on the workloads measured).
+ *   values: 1 = every bottom-up pass also stores the expected counterfactual
+ *          value ev_j of every infoset (Alg. 1 ObserveUtility), so that
+ *          cfr_get_values can return them; 0 = only what the iteration needs
+ *          (default; about 4 bytes per infoset less traffic per pass).
+ *   wait_us: longest time, in microseconds, that a unit of work waits on the
+ *          GPU for the units it depends on before giving up (the wait is
+ *          bounded so that a fault elsewhere cannot hang the device; the
+ *          context then reports CFR_ERR_TIMEOUT); 0 = the default, 1 s.
  *   reserved: must be zero.
  * Every choice computes the same iteration; they differ only in speed (see
  * the autotuner in the Python package). */
@@ -110,12 +118,14 @@ typedef struct {
     int32_t shape;
     int32_t flat;
     int32_t passes;
-    int32_t reserved[5];
+    int32_t values;
+    int32_t wait_us;
+    int32_t reserved[3];
 } cfr_load_options;
 
 /* cfr_load_batch with load options (NULL = defaults).  CFR_ERR_ARG on an
- * unknown shape, a flat value other than 0/1, passes outside 0..2 or a
- * nonzero reserved field. */
+ * unknown shape, a flat or values field other than 0/1, passes outside 0..2,
+ * a negative wait_us or a nonzero reserved field. */
 int cfr_load_batch_opts(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream,
                         const cfr_load_options *options, cfr_ctx **out);
 
@@ -192,7 +202,10 @@ int cfr_exploitability_batch(cfr_ctx *ctx, double *host_expl, double *host_br1, 
  *     (cudaGetSymbolAddress) with the context's device current; make that
  *     first call before any stream capture.
  *   - Asynchronous on the context's stream: dev_expl is valid once the stream
- *     has reached this point (e.g. after cfr_sync).  All calls share the one
+ *     has reached this point (e.g. after cfr_sync).  A game whose
+ *     best-response pass gave up on a bounded wait reads as NaN; the timeout
+ *     status itself is reported only by the next synchronising call
+ *     (cfr_sync and the calls that return data).  All calls share the one
  *     array, so calls whose work overlaps on the GPU (different streams or
  *     contexts) race; calls on one stream are ordered. */
 int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl);
@@ -207,6 +220,18 @@ int cfr_get_state(cfr_ctx *ctx, int64_t game, int player, double *host_r, double
 int cfr_set_state(cfr_ctx *ctx, int64_t game, int player, const double *host_r, const double *host_b,
                   const double *host_xbar, int64_t t);
 
+/* Intermediate values of game g, player p (1 or 2), FP64, for inspection:
+ *   host_x:  S_p + 1 entries, the sequence-form strategy x of Sec. 2.1 that
+ *            the player plays next (x[0] = 1 for the empty sequence, then
+ *            x[(j,a)] = x[p_j] b_j[a], Alg. 1 NextStrategy), in the caller's
+ *            sequence order;
+ *   host_ev: J_p entries, ev_j = sum_a b_j[a] V[(j,a)] of each caller infoset
+ *            j from this player's last bottom-up pass (Alg. 1 ObserveUtility;
+ *            0 before the first iteration or after cfr_set_state).
+ * Either pointer may be NULL.  CFR_ERR_STATE unless the context was loaded
+ * with the `values` load option. */
+int cfr_get_values(cfr_ctx *ctx, int64_t game, int player, double *host_x, double *host_ev);
+
 /* Tracing: run n iterations without CUDA graphs, with a CUDA event recorded
  * between consecutive kernel launches on the context's stream, and return the
  * summed device time (ms) of each launch slot of an iteration in host_ms[4]:
@@ -216,6 +241,11 @@ int cfr_set_state(cfr_ctx *ctx, int64_t game, int player, const double *host_r, 
  * iterations are real: state and counters advance as in cfr_iterate. */
 int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double beta, double gamma,
                            float *host_ms);
+
+/* Number of kernels the context's iteration calls (cfr_iterate,
+ * cfr_iterate_batch, cfr_profile_iterations) have launched so far; each
+ * kernel of a replayed CUDA graph counts once per replay. */
+int cfr_kernel_launches(cfr_ctx *ctx, int64_t *host_count);
 
 /* Block until all work issued on the context's stream has finished
  * (CFR_ERR_TIMEOUT if a bounded device wait gave up). */

@@ -30,7 +30,7 @@ class CFRError(RuntimeError):
 
 class LoadOptions(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("passes", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("values", ctypes.c_int32), ("wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class TreeDesc(ctypes.Structure):
@@ -67,9 +67,11 @@ def lib():
         L.cfr_exploitability_batch.argtypes = [P, P, P, P]
         L.cfr_get_state.argtypes = [P, i64, i, P, P, P, P]
         L.cfr_set_state.argtypes = [P, i64, i, P, P, P, i64]
+        L.cfr_get_values.argtypes = [P, i64, i, P, P]
         L.cfr_profile_iterations.argtypes = [P, i64, i, d, d, d, P]
         L.cfr_exploitability_batch_noalloc.argtypes = [P, P]
         L.cfr_sync.argtypes = [P]
+        L.cfr_kernel_launches.argtypes = [P, P]
         L.cfr_free.argtypes = [P]
         L.cfr_free.restype = None
         L.cfr_strerror.argtypes = [i]
@@ -149,16 +151,19 @@ class Solver:
     advanced together by every launch.  ``shape``, ``flat`` and ``passes`` are
     the load options of the C ABI (launch shape, unit layout, one or two
     launches per player and half-iteration; 0 / False = the library's
-    choice); every choice computes the same iterations."""
+    choice); every choice computes the same iterations.  ``values`` keeps every
+    infoset's counterfactual value for ``get_values``; ``wait_us`` bounds a
+    unit's wait for the units it depends on (0 = the library's 1 s)."""
 
-    def __init__(self, trees, stream=None, shape: int = 0, flat: bool = False, passes: int = 0):
+    def __init__(self, trees, stream=None, shape: int = 0, flat: bool = False, passes: int = 0,
+                 values: bool = False, wait_us: int = 0):
         L = lib()
         batch = isinstance(trees, (list, tuple))
         trees = list(trees) if batch else [trees]
         keep = []
         descs = (TreeDesc * len(trees))(*[_desc(t, keep) for t in trees])
         h = ctypes.c_void_p()
-        opts = LoadOptions(int(shape), int(bool(flat)), int(passes))
+        opts = LoadOptions(int(shape), int(bool(flat)), int(passes), int(bool(values)), int(wait_us))
         _check(L.cfr_load_batch_opts(descs, len(trees), _stream_handle(stream), ctypes.byref(opts), ctypes.byref(h)),
                "cfr_load_batch_opts")
         self.shape, self.flat, self.passes = int(shape), bool(flat), int(passes)
@@ -212,6 +217,12 @@ class Solver:
     def sync(self):
         _check(lib().cfr_sync(self._h), "cfr_sync")
 
+    def kernel_launches(self) -> int:
+        """Kernels launched so far by this solver's iteration calls."""
+        n = ctypes.c_int64()
+        _check(lib().cfr_kernel_launches(self._h, ctypes.byref(n)), "cfr_kernel_launches")
+        return int(n.value)
+
     def exploitability(self):
         e, b1, b2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().cfr_exploitability(self._h, ctypes.byref(e), ctypes.byref(b1), ctypes.byref(b2)),
@@ -243,6 +254,16 @@ class Solver:
         _check(lib().cfr_get_state(self._h, game, player, _ptr(r), _ptr(b), _ptr(xb), ctypes.byref(t)),
                "cfr_get_state")
         return {"r": r, "b": b, "xbar": xb, "t": t.value}
+
+    def get_values(self, player: int, game: int = 0):
+        """The sequence-form strategy to be played next (S + 1 entries, empty
+        sequence first) and each infoset's ev from the player's last bottom-up
+        pass (J entries), caller order; needs ``Solver(..., values=True)``."""
+        sz = self._game_sizes(game)
+        S, J = sz["S1" if player == 1 else "S2"], sz["J1" if player == 1 else "J2"]
+        x, ev = np.zeros(S + 1), np.zeros(J)
+        _check(lib().cfr_get_values(self._h, game, player, _ptr(x), _ptr(ev)), "cfr_get_values")
+        return {"x": x, "ev": ev}
 
     def set_state(self, player: int, r, b, xbar, t: int, game: int = 0):
         S = self._game_sizes(game)["S1" if player == 1 else "S2"]

@@ -79,71 +79,6 @@ __device__ __forceinline__ void unit_done(const DevPlayer &P, int u) {
     }
 }
 
-// the root unit's next x, top-down from global memory, into xn (level 0's
-// parent is the empty sequence, x = 1)
-__device__ void root_topdown_global(const DevPlayer &P, int nlvl, const int32_t *rng) {
-    for (int k = 0; k < nlvl; k++) {
-        for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
-            const int par = P.inf_par[j];
-            const float xp = par < 0 ? 1.f : P.xn[par];
-            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) P.xn[s] = xp * P.b[s];
-        }
-        __syncthreads();
-    }
-}
-
-// The next x of game g's internal units below the root (their b is final once
-// the root is done), top down from the root's xn into xn, by the threads
-// [t0, t0 + nt) of the CTA; `sync` separates the levels.
-// Each thread takes kTdU infosets at a time and issues all their loads before
-// using any (the work is a few dependent global loads per infoset: one CTA
-// must keep many in flight).
-constexpr int kTdU = 4;
-template <class Sync>
-__device__ void internal_topdown(const DevPlayer &P, int g, int t0, int nt, Sync sync) {
-    const int64_t e0 = P.itd_off[g], e1 = P.itd_off[g + 1];
-    for (int64_t e = e0; e < e1; e++) {
-        const int32_t j0 = P.itd[3 * e], j1 = P.itd[3 * e + 1];
-        for (int base = j0 + (int)threadIdx.x - t0; base < j1; base += kTdU * nt) {
-            int par[kTdU], sa[kTdU], sb[kTdU];
-            float xp[kTdU], bv[kTdU][kRegA];
-#pragma unroll
-            for (int u = 0; u < kTdU; u++) {
-                const int j = base + u * nt;
-                par[u] = -1;
-                sa[u] = sb[u] = 0;
-                if (j < j1) {
-                    par[u] = P.inf_par[j];
-                    sa[u] = P.inf_seq[j];
-                    sb[u] = P.inf_seq[j + 1];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kTdU; u++) {
-                xp[u] = par[u] >= 0 ? __ldcg(&P.xn[par[u]]) : 0.f;
-#pragma unroll
-                for (int a = 0; a < kRegA; a++) bv[u][a] = sa[u] + a < sb[u] ? __ldcg(&P.b[sa[u] + a]) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < kTdU; u++) {
-#pragma unroll
-                for (int a = 0; a < kRegA; a++)
-                    if (sa[u] + a < sb[u]) P.xn[sa[u] + a] = xp[u] * bv[u][a];
-                for (int q = sa[u] + kRegA; q < sb[u]; q++) P.xn[q] = xp[u] * __ldcg(&P.b[q]);
-            }
-        }
-        if (P.itd[3 * e + 2]) sync();
-    }
-}
-
-// xn of every game's root unit and internal units from the current b (one
-// CTA per game), when x is rebuilt outside an iteration
-__global__ void k_root_topdown(DevPlayer P) {
-    const int4 h = P.units[P.game_root[blockIdx.x]];
-    root_topdown_global(P, h.y, P.ranges + h.z);
-    internal_topdown(P, blockIdx.x, 0, blockDim.x, []() { __syncthreads(); });
-}
-
 // Per-game parameters of iterations t = t_done + k, k = 0..kParamSpan, for the
 // passes that follow (one thread per entry).  A game whose counter or active
 // flag differs from game 0's marks the table mixed (the flag is cleared before
@@ -185,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         if (threadIdx.x == 0) {
             item_params(gm, ia, d.x, &s_ip);
             if (s_ip.active && tr.y > 0) {
-                if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) s_err = 1;
+                if (!flag_wait(&P.unit_cnt[u], tr.y, P.err, P.wait_ns)) s_err = 1;
                 P.unit_cnt[u] = 0;
                 __threadfence();
             }
@@ -281,6 +216,7 @@ struct UpSmem {
     int nwin0, win0_at; // their number and first record
     BulkCmd cmd[kUpArrays * kMaxStagedLevels];   // the producer's staged copies
     int unit[2];        // queue position of the unit in each buffer (n: none)
+    int armed[2];       // times each buffer's barrier was armed (bulk copies issued)
     int err;
 };
 struct DownSmem {
@@ -289,8 +225,18 @@ struct DownSmem {
     DownTab tab[2][kMaxStagedLevels];
     BulkCmd cmd[kDownArrays * kMaxStagedLevels];   // the producer's staged copies
     ItemParams ip[2];
+    int armed[2];       // times each buffer's barrier was armed (bulk copies issued)
     int cur, nxt, err, epoch;
 };
+
+// Before a CTA leaves a pass loop (normally or after a bounded wait gave up),
+// thread 0 waits, bounded, for the last armed phase of each buffer's barrier:
+// no bulk copy into this CTA's shared memory is then still in flight.
+__device__ __forceinline__ void drain_copies(uint64_t *bar, const int *armed, int32_t *err) {
+    if (threadIdx.x == 0)
+        for (int b = 0; b < 2; b++)
+            if (armed[b] > 0) mbar_wait(&bar[b], (uint32_t)(armed[b] - 1) & 1u, err);
+}
 
 // Up pass of one player (Alg. 2 ObserveUtility with the variant post-op of
 // Alg. 3-5, and NextStrategy's regret matching).  Persistent CTAs take units
@@ -302,9 +248,9 @@ struct DownSmem {
 // shows all children done (a bounded wait: the children come earlier in the
 // queue, every CTA works its units in queue order, and a child never waits
 // for a later unit; a child at a static position of a CTA that is not yet
-// resident is done once that CTA runs).  The game's root unit also
-// publishes the next x of itself and every internal unit (xn) and, when
-// `root_flag` is nonzero, sets the game's root_done word to it.
+// resident is done once that CTA runs).  When `root_flag` is nonzero, the
+// game's root unit sets the game's root_done word to it once every b of the
+// game is final.
 // Returns true when the CTA left the queues early: with a single game, it
 // ended on the root with no unit after it, and registered its exit
 // (launch_exit2) as it took the root, so that the launch's last exit (and,
@@ -320,9 +266,13 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
-        S.err = 0;
+        // a context whose earlier wait gave up does no more work (its
+        // results are void): the remaining launches of a graph finish at once
+        S.err = __ldcg(P.err) != 0;
+        S.armed[0] = S.armed[1] = 0;
     }
     __syncthreads();
+    if (S.err) return false;
     uint32_t ph[2] = {0u, 0u};
     int buf = 0;
     // The producer keeps a pipeline a round deep: the unit in each buffer
@@ -350,8 +300,10 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             cp_async_wait_all();
             __syncwarp();
             if (tid == 0) S.ip[0] = S.pre.ip;
-            if (h0.w & kStaged)
+            if (h0.w & kStaged) {
                 issue_up(P, xo, S.pre, bufs[0], &S.bar[0], S.lv[0], S.tab[0], &S.cev[0], S.cmd, true);
+                if (tid == 0) S.armed[0]++;
+            }
             for (int w = tid; w < min(unit_nwin(h0), kPreWin); w += 32) S.win0[w] = S.pre.win[w];
         }
         if (tid == 0) {
@@ -425,9 +377,11 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             const int nx = S.pre.pos;
             if (nx < n) {
                 if (tid == 0) S.ip[buf ^ 1] = S.pre.ip;
-                if (S.pre.h.w & kStaged)
+                if (S.pre.h.w & kStaged) {
                     issue_up(P, xo, S.pre, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1],
                              &S.cev[buf ^ 1], S.cmd, false);
+                    if (tid == 0) S.armed[buf ^ 1]++;
+                }
             }
             if (tid == 0) S.unit[buf ^ 1] = nx;
             __syncwarp();   // S.pre is read: the next one may overwrite it
@@ -439,7 +393,7 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
                 // all children done, then their ev, copied by every consumer
                 // thread (the acquire above orders it through the barrier)
                 if (tid == 32) {
-                    if (!flag_wait(&P.unit_cnt[u], tr.y, P.err)) S.err = 1;
+                    if (!flag_wait(&P.unit_cnt[u], tr.y, P.err, P.wait_ns)) S.err = 1;
                     P.unit_cnt[u] = 0;
                 }
                 consumer_sync();
@@ -451,29 +405,18 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             }
             if (staged && !S.err) {
                 up_gather(xo, h.y, S.lv[buf], S.tab[buf]);
-                compute_up(ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal, root);
-                up_write_back(P, h.y, S.lv[buf], S.tab[buf], root);
-                if (root) {
-                    consumer_sync();
-                    internal_topdown(P, h.x, kProducerThreads, (int)blockDim.x - kProducerThreads,
-                                     []() { consumer_sync(); });
-                }
+                compute_up(ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal);
+                up_write_back(P, h.y, S.lv[buf], S.tab[buf], ia.keep_values != 0);
             }
         }
         __syncthreads();
         if (S.err) break;
         if (ip.active) {
-            if (!staged) {
-                run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
-                if (root) {
-                    root_topdown_global(P, h.y, P.ranges + h.z);
-                    internal_topdown(P, h.x, 0, blockDim.x, []() { __syncthreads(); });
-                }
-            }
+            if (!staged) run_up<MODE_CFR>(P, xo, ia, ip, h.y, P.ranges + h.z, bufs[buf]);
             if (tid == 0 && root && ia.first_of_iter) gm.t_done[h.x] = ip.t;
         }
         if (tid == 0 && root && root_flag) {
-            // the game's bottom-up pass is complete: b and xn final (set for
+            // the game's bottom-up pass is complete: every b final (set for
             // games masked off too, whose top-down units then do nothing)
             __threadfence();
             st_release(&P.root_done[h.x], root_flag);
@@ -483,13 +426,16 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         buf ^= 1;
     }
     // the last unit's count (nothing else of this CTA is pending; records
-    // prefetched for a unit not taken after an error land first)
+    // prefetched for a unit not taken after an error land first, and so do
+    // bulk copies into a buffer whose unit was not computed)
     cp_async_wait_all();
     __syncthreads();
+    drain_copies(S.bar, S.armed, P.err);
     if (tid == 0 && done_par >= 0) {
         __threadfence();
         atomicAdd(&P.unit_cnt[done_par], 1);
     }
+    __syncthreads();
     return early;
 }
 
@@ -500,32 +446,45 @@ __global__ void __launch_bounds__(NT, MINB)
     unsigned char *bufs[2] = {smem, smem + item_bytes};
     __shared__ UpSmem S;
     if (!up_loop(P, gm, xo, ia, bufs, S, 0)) {
-        if (ia.average) average_pass(P, gm, ia, P.S);
+        if (ia.average && !S.err) average_pass(P, gm, ia, P.S);
         __syncthreads();
         launch_exit2(P.qup, P.qavg);
     }
 }
 
-// one unit top-down from global memory (units too large to stage); the top
-// level's parents' next x is in xn
-__device__ void run_down(const DevPlayer &P, int nlvl, const int32_t *rng) {
+// one unit top-down from global memory (units too large to stage): its
+// ancestor chain (the first n_anc levels, from the game's root) into its own
+// scratch area xa, then its own levels into x
+__device__ void run_down(const DevPlayer &P, int nlvl, int n_anc, const int32_t *rng, float *xa) {
+    int aoff = 0, poff = 0;   // scratch offset of this level / of the level above
     for (int k = 0; k < nlvl; k++) {
-        const float *xpar = (k == 0) ? P.xn : P.x;
+        const int s0 = rng[kLvl * k + 2];
+        const int ps0 = k > 0 ? rng[kLvl * (k - 1) + 2] : 0;
+        // parents: the level above, in the scratch area while it is an ancestor level
+        const bool par_anc = k > 0 && k - 1 < n_anc, anc = k < n_anc;
         for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
             const int par = P.inf_par[j];
-            const float xp = par < 0 ? 1.f : __ldcg(&xpar[par]);
-            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) P.x[s] = xp * P.b[s];
+            const float xp = par < 0 ? 1.f : par_anc ? __ldcg(&xa[poff + (par - ps0)]) : __ldcg(&P.x[par]);
+            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) {
+                const float v = xp * P.b[s];
+                if (anc) xa[aoff + (s - s0)] = v;
+                else P.x[s] = v;
+            }
         }
         __syncthreads();
+        if (anc) {
+            poff = aoff;
+            aoff += rng[kLvl * k + 3] - s0;
+        }
     }
 }
 
 
 // Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y; the average
 // xbar += t^gamma x was done by the bottom-up pass's CTAs before).  Every
-// unit's top-level parents belong to the root or to
-// internal units, whose next x the bottom-up pass published in xn, so the
-// units are independent of one another.  With `wait_roots` (the loop follows
+// unit recomputes the next x of its ancestor chain (the infosets above its
+// top level, up to the game's root) from the final b, so the units are
+// independent of one another.  With `wait_roots` (the loop follows
 // this player's bottom-up loop in the same launch) a unit's b is copied in,
 // and the unit computed, only once its game's root_done word shows the
 // bottom-up pass of that game complete (a bounded wait; the root unit was
@@ -540,8 +499,9 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
-        S.cur = atomicAdd(&P.qdn[0], 1);
-        S.err = 0;
+        S.err = __ldcg(P.err) != 0;   // see up_loop
+        S.cur = S.err ? n : atomicAdd(&P.qdn[0], 1);
+        S.armed[0] = S.armed[1] = 0;
     }
     __syncthreads();
     const int flag = S.epoch + 1;
@@ -553,8 +513,8 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
     auto root_ready = [&](int g) {
         if (!wait_roots) return true;
         bool ok = true;
-        if ((tid & 31) == 0 && !avg_seen) ok = avg_seen = flag_wait(&P.qavg[2], avg_flag, P.err);
-        if ((tid & 31) == 0 && ok) ok = flag_wait(&P.root_done[g], flag, P.err);
+        if ((tid & 31) == 0 && !avg_seen) ok = avg_seen = flag_wait(&P.qavg[2], avg_flag, P.err, P.wait_ns);
+        if ((tid & 31) == 0 && ok) ok = flag_wait(&P.root_done[g], flag, P.err, P.wait_ns);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (ok) ok = ld_acquire(&P.root_done[g]) == flag;
         return __all_sync(0xffffffffu, ok) != 0;
@@ -566,7 +526,10 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
     const int4 h0 = cur < n ? P.downq[2 * cur] : make_int4(0, 0, 0, 0);
     const bool st0 = cur < n && (h0.w & kStaged);
     if (warp == 0) {
-        if (st0) issue_down(P, h0, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownOwn | kDownArm, 0);
+        if (st0) {
+            issue_down(P, h0, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownOwn | kDownArm, 0);
+            if (tid == 0) S.armed[0]++;
+        }
         if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
         pdl_wait();
         if (cur < n) {
@@ -578,12 +541,11 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
     pdl_trigger();
     pdl_wait();
     if (st0 && !S.err) {
-        for (int k = 0; k < h0.y; k++)
-            for (int f = 0; f < 4; f += 3) {
-                const BulkCmd c = S.cmd[kDownArrays * k + f];
-                for (uint32_t o = 16u * tid; o < c.bytes; o += 16u * blockDim.x)
-                    cp_async16_cg_to(c.dst + o, (const unsigned char *)c.src + o);
-            }
+        for (int k = 0; k < h0.y; k++) {
+            const BulkCmd c = S.cmd[kDownArrays * k];   // b
+            for (uint32_t o = 16u * tid; o < c.bytes; o += 16u * blockDim.x)
+                cp_async16_cg_to(c.dst + o, (const unsigned char *)c.src + o);
+        }
         cp_async_wait_all();
     }
     __syncthreads();
@@ -607,22 +569,28 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
             if (nxt < n) {
                 const int4 hn = P.downq[2 * nxt];
                 if (!root_ready(hn.x) && tid == 0) S.err = 1;
-                if (hn.w & kStaged)
+                if (hn.w & kStaged) {
                     issue_down(P, hn, bufs[buf ^ 1], &S.bar[buf ^ 1], S.lv[buf ^ 1], S.tab[buf ^ 1], S.cmd,
                                kDownOwn | kDownB | kDownArm, 0);
+                    if (tid == 0) S.armed[buf ^ 1]++;
+                }
                 if (tid == 0) S.ip[buf ^ 1] = unit_params(gm, ia, hn.x);
             }
             if (tid == 0) S.nxt = nxt < n ? atomicAdd(&P.qdn[0], 1) : n;
         } else if (ip.active && staged) {
-            compute_down(P, h.y, S.lv[buf], S.tab[buf]);
+            compute_down(P, h.y, h.w >> kAncShift, S.lv[buf], S.tab[buf]);
         }
         __syncthreads();
         const int nxt2 = S.nxt;
-        if (ip.active && !staged) run_down(P, h.y, P.ranges + h.z);
+        if (ip.active && !staged)
+            run_down(P, h.y, h.w >> kAncShift, P.ranges + h.z, P.xanc + P.downq[2 * cur + 1].w);
         cur = nxt;
         nxt = nxt2;
         buf ^= 1;
     }
+    cp_async_wait_all();
+    drain_copies(S.bar, S.armed, P.err);
+    __syncthreads();
     return early;
 }
 
@@ -658,7 +626,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     if (!up_loop(P, gm, xo, up_ia, bufs, SU, SD.epoch + 1)) {
-        if (up_ia.average) average_pass(P, gm, up_ia, P.S);
+        if (up_ia.average && !SU.err) average_pass(P, gm, up_ia, P.S);
         __syncthreads();
         launch_exit2(P.qup, P.qavg);
     }
@@ -746,6 +714,20 @@ __global__ void k_average(DevPlayer P, const int32_t *ext_inf, const int32_t *ex
 
 __global__ void k_set_t(int32_t *t_done, int g, int32_t t) { t_done[g] = t; }
 
+// current sequence-form strategy (empty sequence first) and per-infoset ev of
+// one game in caller order (FP64)
+__global__ void k_get_values(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
+                             double *out_x, double *out_ev) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) out_x[0] = (double)P.x[g];
+    if (k >= Jg) return;
+    const int j = ext_inf[k];
+    const int base = ext_seq0[k];
+    out_ev[k] = (double)P.ev[j];
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    for (int s = s0; s < s1; s++) out_x[1 + base + (s - s0)] = (double)P.x[s];
+}
+
 }  // namespace cfrb
 
 // ---------------------------------------------------------------------------
@@ -829,6 +811,8 @@ struct cfr_ctx {
     PlayerBuf pl[2];
     int32_t *t_done = nullptr;
     uint8_t *active = nullptr;
+    uint8_t *active_keep = nullptr; // device copy of the caller's mask, restored after a
+                                    // best-response pass (which runs every game)
     ItemParams *par = nullptr;      // per-game parameter table (kParamSpan + 1 entries)
     int32_t *pbase = nullptr;
     int32_t *mixed = nullptr;   // set by k_params when the games' parameters differ
@@ -850,6 +834,10 @@ struct cfr_ctx {
     size_t smem_staged = 0;
     int32_t *err = nullptr;         // device error word (bounded waits)
     bool poisoned = false;
+    bool values = false;            // up passes store every infoset's ev (cfr_get_values)
+    uint64_t wait_ns = kFlagWaitNs; // longest wait of a unit for the units it depends on
+    int64_t launches = 0;           // kernels launched so far (graph replays count their kernels)
+    std::map<GraphKey, int64_t> graph_kernels;   // kernels in each captured graph
 };
 
 namespace {
@@ -909,7 +897,7 @@ DevGames dev_games(const cfr_ctx *c) { return DevGames{c->t_done, c->active, nul
 
 // the parameter table for the next kParamSpan iterations of every game
 int launch_params(cfr_ctx *c, int variant, double alpha, double beta, double gamma) {
-    IterArgs ia{variant, 0, 0.f, alpha, beta, gamma, 0, 0};
+    IterArgs ia{variant, 0, 0.f, alpha, beta, gamma, 0, 0, 0};
     const int64_t n = c->G * (kParamSpan + 1);
     CU(cudaMemsetAsync(c->mixed, 0, sizeof(int32_t), c->stream));
     k_params<<<(unsigned)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096), kThreads, 0, c->stream>>>(
@@ -924,7 +912,6 @@ int launch_rebuild_x(cfr_ctx *c, int p) {
     TRY(launch_params(c, 0, 0.0, 0.0, 0.0));
     IterArgs ia{};
     ia.average = 0;
-    k_root_topdown<<<(unsigned)c->G, kThreads, 0, c->stream>>>(B.d);
     kConfigs[c->cfg].down<<<B.grid_down, c->threads, c->smem_staged, c->stream>>>(B.d, dev_games(c), ia,
                                                                                    c->item_bytes);
     CU(cudaGetLastError());
@@ -954,16 +941,18 @@ cudaError_t launch_pass(void (*fn)(P...), int grid, int threads, size_t smem, cu
 // the previous one's tail (not when timing the passes one by one, and not
 // right after the parameter table is refilled).
 int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double gamma, bool alternating,
-                     int k, cudaEvent_t *ev = nullptr) {
+                     int k, int64_t *nlaunch, cudaEvent_t *ev = nullptr) {
     const bool params = (k % kParamSpan) == 0;
     const int pslot = k % kParamSpan + 1;
     if (params) TRY(launch_params(c, variant, alpha, beta, gamma));
+    *nlaunch += params ? 1 : 0;
     const DevGames gm = dev_games(c);
     // every pass of the k-th iteration since the table was filled runs at
     // t = t_done + k + 1 of that moment
-    IterArgs up1{variant, 1, +1.f, alpha, beta, gamma, 1, pslot};
-    IterArgs up2{variant, 0, -1.f, alpha, beta, gamma, 1, pslot};
-    IterArgs dn{variant, 0, 0.f, alpha, beta, gamma, 1, pslot};
+    const int keep = c->values ? 1 : 0;
+    IterArgs up1{variant, 1, +1.f, alpha, beta, gamma, 1, pslot, keep};
+    IterArgs up2{variant, 0, -1.f, alpha, beta, gamma, 1, pslot, keep};
+    IterArgs dn{variant, 0, 0.f, alpha, beta, gamma, 1, pslot, keep};
     PlayerBuf &A = c->pl[0], &B = c->pl[1];
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], c->stream);
@@ -980,6 +969,7 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
         const HalfFn half = kConfigs[c->cfg].half;
         CU(launch_pass(half, A.grid_half, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, dn, ib));
         CU(launch_pass(half, B.grid_half, nt, sm, c->stream, pdl, B.d, gm, x1, up2, dn, ib));
+        *nlaunch += 2;
     } else if (alternating) {
         CU(launch_pass(up, A.grid_up, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, ib));
         mark(1);
@@ -988,6 +978,7 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
         CU(launch_pass(up, B.grid_up, nt, sm, c->stream, pdl, B.d, gm, x1, up2, ib));
         mark(3);
         CU(launch_pass(down, B.grid_down, nt, sm, c->stream, pdl, B.d, gm, dn, ib));
+        *nlaunch += 4;
     } else {
         CU(launch_pass(up, A.grid_up, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, ib));
         mark(1);
@@ -996,6 +987,7 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
         CU(launch_pass(down, A.grid_down, nt, sm, c->stream, pdl, A.d, gm, dn, ib));
         mark(3);
         CU(launch_pass(down, B.grid_down, nt, sm, c->stream, pdl, B.d, gm, dn, ib));
+        *nlaunch += 4;
     }
     mark(4);
     CU(cudaGetLastError());
@@ -1077,6 +1069,7 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
                 w0 = H.rwin[4 * rec];
                 nw = H.rwin[4 * (rec + u.nlvl - 1) + 1] - w0;
             }
+            if (!up) w0 = H.danc_off[qv[k]];   // top-down: the unit's ancestor scratch
             q[2 * k] = make_int4(u.game, u.nlvl, u.rng, u.flags | (nw << 8));
             q[2 * k + 1] = make_int4(qv[k], u.parent, u.nchild, w0);
         }
@@ -1089,11 +1082,6 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(queue(H.down_queue, H.dunits, false, &d.downq));
     TRY(upload(c, &p32, H.game_root));
     d.game_root = p32;
-    TRY(upload(c, &p32, H.itd));
-    d.itd = p32;
-    int64_t *p64;
-    TRY(upload(c, &p64, H.itd_off));
-    d.itd_off = p64;
     TRY(upload(c, &B.ext_inf, H.ext_inf));
     TRY(upload(c, &B.ext_seq0, H.ext_seq0));
     d.n_units = (int32_t)H.dunits.size();
@@ -1102,7 +1090,7 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.r, H.S));
     TRY(dalloc(c, &d.b, H.S));
     TRY(dalloc(c, &d.x, H.S));
-    TRY(dalloc(c, &d.xn, H.S));
+    TRY(dalloc(c, &d.xanc, H.xanc_size));
     TRY(dalloc(c, &d.xbar, H.S));
     TRY(dalloc(c, &d.u, H.S));
     TRY(dalloc(c, &d.ev, H.J));
@@ -1119,6 +1107,7 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     d.qavg = ctr + nu + 8;
     d.S = (int32_t)H.S;
     d.err = c->err;
+    d.wait_ns = c->wait_ns;
     TRY(dalloc(c, &d.root_done, L.G));
     CU(cudaMemsetAsync(d.root_done, 0, L.G * sizeof(int32_t), c->stream));
     CU(cudaMemsetAsync(d.r, 0, H.S * sizeof(float2), c->stream));
@@ -1126,7 +1115,6 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     CU(cudaMemsetAsync(d.ev, 0, H.J * sizeof(float), c->stream));
     CU(cudaMemsetAsync(d.ev64, 0, H.J * sizeof(double), c->stream));
     CU(cudaMemsetAsync(d.x, 0, H.S * sizeof(float), c->stream));
-    CU(cudaMemsetAsync(d.xn, 0, H.S * sizeof(float), c->stream));
     B.smem_br = (size_t)(kThreads / 32) * 32 * kStage * sizeof(double);
     const StagedConfig &cf = kConfigs[c->cfg];
     // the pass kernels overlap one another's tails: one shared-memory carve-out
@@ -1153,15 +1141,21 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     int shape = -1;   // the library's choice, once the games are known
     bool flat = false;
     int passes = 0;
+    bool values = false;
+    uint64_t wait_ns = kFlagWaitNs;
     if (lo) {
         if (lo->shape < 0 || lo->shape > kNumConfigs) return set_err(CFR_ERR_ARG, "unknown launch shape");
         if (lo->flat != 0 && lo->flat != 1) return set_err(CFR_ERR_ARG, "flat must be 0 or 1");
         if (lo->passes < 0 || lo->passes > 2) return set_err(CFR_ERR_ARG, "passes must be 0, 1 or 2");
-        for (int k = 0; k < 5; k++)
+        if (lo->values != 0 && lo->values != 1) return set_err(CFR_ERR_ARG, "values must be 0 or 1");
+        if (lo->wait_us < 0) return set_err(CFR_ERR_ARG, "wait_us must not be negative");
+        for (int k = 0; k < 3; k++)
             if (lo->reserved[k] != 0) return set_err(CFR_ERR_ARG, "reserved load options must be zero");
         if (lo->shape > 0) shape = lo->shape - 1;
         flat = lo->flat != 0;
         passes = lo->passes;
+        values = lo->values != 0;
+        if (lo->wait_us > 0) wait_ns = 1000ull * (uint64_t)lo->wait_us;
     }
     if (!games || n < 1) return set_err(CFR_ERR_ARG, "no games");
     std::vector<TreeView> tv(n);
@@ -1217,6 +1211,8 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     c->Z = L.Z;
     c->cfg = shape;
     c->split = passes != 1;
+    c->values = values;
+    c->wait_ns = wait_ns;
     c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
     // two unit buffers; a unit too large to stage uses its buffer as the
@@ -1231,6 +1227,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
         if ((rc = build_player(c, L, p))) return bail(rc);
     if ((rc = dalloc(c, &c->t_done, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->active, L.G))) return bail(rc);
+    if ((rc = dalloc(c, &c->active_keep, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->par, L.G * (kParamSpan + 1)))) return bail(rc);
     if ((rc = dalloc(c, &c->pbase, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->mixed, 1))) return bail(rc);
@@ -1243,7 +1240,8 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     if ((rc = dalloc(c, &c->scratch, 3 * c->scratch_n))) return bail(rc);
     c->active_host.assign(L.G, 1);
     if (cudaMemsetAsync(c->t_done, 0, L.G * sizeof(int32_t), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->active, 1, L.G, c->stream) != cudaSuccess)
+        cudaMemsetAsync(c->active, 1, L.G, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->active_keep, 1, L.G, c->stream) != cudaSuccess)
         return bail(set_err(CFR_ERR_CUDA, "memset"));
     for (int p = 0; p < 2; p++)
         if ((rc = launch_rebuild_x(c, p))) return bail(rc);
@@ -1289,8 +1287,9 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             int rc = CFR_OK;
+            int64_t nk = 0;
             for (int k = 0; k < K && rc == CFR_OK; k++)
-                rc = launch_iteration(c, variant, alpha, beta, gamma, alt, k);
+                rc = launch_iteration(c, variant, alpha, beta, gamma, alt, k, &nk);
             cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
@@ -1302,13 +1301,18 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
             if (ee != cudaSuccess)
                 return set_err(CFR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
             c->graphs[key] = exec;
+            c->graph_kernels[key] = nk;
         } else {
             exec = f->second;
         }
-        for (; done + K <= n; done += K) CU(cudaGraphLaunch(exec, c->stream));
+        const int64_t nk = c->graph_kernels[key];
+        for (; done + K <= n; done += K) {
+            CU(cudaGraphLaunch(exec, c->stream));
+            c->launches += nk;
+        }
     }
     for (int64_t k = 0; done < n; done++, k++)
-        TRY(launch_iteration(c, variant, alpha, beta, gamma, alt, (int)k));
+        TRY(launch_iteration(c, variant, alpha, beta, gamma, alt, (int)k, &c->launches));
     return CFR_OK;
 }
 
@@ -1375,9 +1379,11 @@ int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl) {
     double *br = nullptr;
     TRY(noalloc_scratch(dev, &br));
     double *br1 = br, *br2 = br + kNoAllocMaxGames;
-    // the scratch keeps the previous call's values: start every game from zero
-    if (cudaMemsetAsync(br1, 0, ctx->G * sizeof(double), ctx->stream) != cudaSuccess ||
-        cudaMemsetAsync(br2, 0, ctx->G * sizeof(double), ctx->stream) != cudaSuccess)
+    // the scratch keeps the previous call's values: start every game from NaN
+    // (all bits set), so a game whose pass did not finish reads as NaN, never
+    // as a stale or zero exploitability
+    if (cudaMemsetAsync(br1, 0xFF, ctx->G * sizeof(double), ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(br2, 0xFF, ctx->G * sizeof(double), ctx->stream) != cudaSuccess)
         return set_err_static(CFR_ERR_CUDA, "clearing the exploitability scratch failed");
     const bool masked = std::find(ctx->active_host.begin(), ctx->active_host.end(), 0) != ctx->active_host.end();
     if (masked && cudaMemsetAsync(ctx->active, 1, ctx->G, ctx->stream) != cudaSuccess)
@@ -1398,7 +1404,8 @@ int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl) {
     k_expl_combine<<<(unsigned)std::min<int64_t>((ctx->G + 255) / 256, 65535), 256, 0, ctx->stream>>>(br1, br2,
                                                                                                     ctx->G, dev_expl);
     if (cudaGetLastError() != cudaSuccess) return set_err_static(CFR_ERR_CUDA, "kernel launch failed");
-    if (masked && cudaMemcpyAsync(ctx->active, ctx->active_host.data(), ctx->G, cudaMemcpyHostToDevice,
+    // the caller's mask back, from its device copy (no host memory involved)
+    if (masked && cudaMemcpyAsync(ctx->active, ctx->active_keep, ctx->G, cudaMemcpyDeviceToDevice,
                                   ctx->stream) != cudaSuccess)
         return set_err_static(CFR_ERR_CUDA, "cudaMemcpyAsync failed");
     return CFR_OK;
@@ -1441,6 +1448,7 @@ int cfr_iterate(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, double bet
     if (ctx && std::find(ctx->active_host.begin(), ctx->active_host.end(), 0) != ctx->active_host.end()) {
         std::fill(ctx->active_host.begin(), ctx->active_host.end(), 1);
         CU(cudaMemsetAsync(ctx->active, 1, ctx->G, ctx->stream));
+        CU(cudaMemsetAsync(ctx->active_keep, 1, ctx->G, ctx->stream));
     }
     return iterate(ctx, n, (int)v, alpha, beta, gamma);
 }
@@ -1456,6 +1464,7 @@ int cfr_iterate_batch(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, doub
         ctx->active_host = act;
         // pageable source: the copy is staged before the call returns
         CU(cudaMemcpyAsync(ctx->active, ctx->active_host.data(), ctx->G, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->active_keep, ctx->active, ctx->G, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     return iterate(ctx, n, (int)v, alpha, beta, gamma);
 }
@@ -1531,8 +1540,7 @@ int cfr_exploitability_batch(cfr_ctx *ctx, double *host_expl, double *host_br1, 
         k_up<MODE_BR><<<B.grid_up_br, kThreads, B.smem_br, ctx->stream>>>(B.d, gm, ctx->pl[1 - p].d.xnorm, ia);
     }
     CU(cudaGetLastError());
-    if (masked)
-        CU(cudaMemcpyAsync(ctx->active, ctx->active_host.data(), ctx->G, cudaMemcpyHostToDevice, ctx->stream));
+    if (masked) CU(cudaMemcpyAsync(ctx->active, ctx->active_keep, ctx->G, cudaMemcpyDeviceToDevice, ctx->stream));
     std::vector<double> b1(ctx->G), b2(ctx->G);
     CU(cudaMemcpyAsync(b1.data(), ctx->br[0], ctx->G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(b2.data(), ctx->br[1], ctx->G * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1579,6 +1587,25 @@ int cfr_get_state(cfr_ctx *ctx, int64_t game, int player, double *host_r, double
     return CFR_OK;
 }
 
+int cfr_get_values(cfr_ctx *ctx, int64_t game, int player, double *host_x, double *host_ev) {
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
+    TRY(check_game(ctx, game, player));
+    if (!ctx->values) return set_err(CFR_ERR_STATE, "load the context with the values option to read values");
+    PlayerBuf &B = ctx->pl[player - 1];
+    const int Jg = B.game_J[game];
+    const int64_t Sg = B.game_S[game];
+    // the transfer area holds 3 (max S + 1) doubles: x in the first part, ev
+    // (J <= S) in the second
+    double *dx = ctx->scratch, *de = ctx->scratch + ctx->scratch_n;
+    k_get_values<<<(Jg + kThreads) / kThreads, kThreads, 0, ctx->stream>>>(
+        B.d, B.ext_inf + B.game_jbase[game], B.ext_seq0 + B.game_jbase[game], (int)game, Jg, dx, de);
+    CU(cudaGetLastError());
+    if (host_x) CU(cudaMemcpyAsync(host_x, dx, (Sg + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (host_ev && Jg) CU(cudaMemcpyAsync(host_ev, de, Jg * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_err(ctx);
+}
+
 int cfr_set_state(cfr_ctx *ctx, int64_t game, int player, const double *host_r, const double *host_b,
                   const double *host_xbar, int64_t t) {
     std::lock_guard<std::recursive_mutex> setup(setup_mutex());
@@ -1616,7 +1643,7 @@ int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha,
     double tot[4] = {0, 0, 0, 0};
     int rc = CFR_OK;
     for (int64_t i = 0; i < n && rc == CFR_OK; i++) {
-        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, (int)i, ev);
+        rc = launch_iteration(ctx, (int)v, alpha, beta, gamma, alt, (int)i, &ctx->launches, ev);
         if (rc) break;
         cudaError_t e = cudaEventSynchronize(ev[4]);
         if (e != cudaSuccess) {
@@ -1633,6 +1660,12 @@ int cfr_profile_iterations(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha,
     for (int k = 0; k < 4; k++) host_ms[k] = (float)tot[k];
     if (rc) return rc;
     return check_err(ctx);
+}
+
+int cfr_kernel_launches(cfr_ctx *ctx, int64_t *host_count) {
+    if (!ctx || !host_count) return set_err(CFR_ERR_ARG, "ctx and host_count must not be NULL");
+    *host_count = ctx->launches;
+    return CFR_OK;
 }
 
 int cfr_sync(cfr_ctx *ctx) {

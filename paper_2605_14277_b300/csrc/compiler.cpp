@@ -592,70 +592,52 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 spans.swap(next);
             }
         }
-        // internal ranges below each game's root unit, by absolute level,
-        // adjacent ranges of one level merged
-        {
-            P.itd.clear();
-            P.itd_off.assign(G + 1, 0);
-            std::vector<std::vector<std::pair<int32_t, int32_t>>> bylevel;
-            int64_t gcur = -1;
-            auto flush = [&]() {
-                for (auto &lvr : bylevel) {
-                    std::sort(lvr.begin(), lvr.end());
-                    std::vector<std::pair<int32_t, int32_t>> merged;
-                    for (auto &r : lvr) {
-                        if (!merged.empty() && merged.back().second == r.first) merged.back().second = r.second;
-                        else merged.push_back(r);
-                    }
-                    for (size_t k = 0; k < merged.size(); k++) {
-                        P.itd.push_back(merged[k].first);
-                        P.itd.push_back(merged[k].second);
-                        P.itd.push_back(k + 1 == merged.size() ? 1 : 0);
-                    }
-                }
-                bylevel.clear();
-            };
-            for (size_t k = 0; k < P.units.size(); k++) {
-                const Unit &u = P.units[k];
-                if (u.game != gcur) {
-                    flush();
-                    for (int64_t g2 = gcur + 1; g2 <= u.game; g2++) P.itd_off[g2] = (int64_t)P.itd.size() / 3;
-                    gcur = u.game;
-                }
-                if (u.parent < 0 || u.nchild == 0) continue;   // the root itself, and leaves
-                for (int32_t d = 0; d < u.nlvl; d++) {
-                    const int32_t lvl = u.lvl0 + d;
-                    if ((int32_t)bylevel.size() <= lvl) bylevel.resize(lvl + 1);
-                    bylevel[lvl].push_back({P.ranges[u.rng + kLvl * d], P.ranges[u.rng + kLvl * d + 1]});
-                }
-            }
-            flush();
-            for (int64_t g2 = gcur + 1; g2 <= G; g2++) P.itd_off[g2] = (int64_t)P.itd.size() / 3;
-        }
         // top-down units: consecutive siblings (same parent, so adjacent
-        // ranges at every level) merged while their top-down footprint fits
+        // ranges at every level) merged while their top-down footprint fits.
+        // A top-down unit also carries its ancestor chain: the infosets above
+        // its top level, one contiguous range per level up to the game's root
+        // (the parents of a contiguous range of infosets are one contiguous
+        // range of sequences, since infosets are sorted by parent), staged
+        // first as levels that are computed but not written back.  So the
+        // unit rebuilds the next x of its top level's parents itself and
+        // depends on no other top-down unit.
         {
+            std::vector<int32_t> seq_inf(P.S);
+            for (int64_t j = 0; j < J; j++)
+                for (int32_t q = P.inf_seq[j]; q < P.inf_seq[j + 1]; q++) seq_inf[q] = (int32_t)j;
+            std::vector<std::pair<int32_t, int32_t>> chain;
+            auto ancestors = [&](int32_t lo, int32_t hi) {
+                chain.clear();
+                while (lo < hi && P.inf_par[lo] >= 0) {
+                    const int32_t ps0 = P.inf_par[lo], ps1 = P.inf_par[hi - 1] + 1;
+                    lo = seq_inf[ps0];
+                    hi = seq_inf[ps1 - 1] + 1;
+                    chain.push_back({lo, hi});
+                }
+                std::reverse(chain.begin(), chain.end());
+                int64_t bytes = 0;
+                for (auto &c : chain) bytes += down_level_bytes(P.inf_seq[c.second] - P.inf_seq[c.first], c.second - c.first);
+                return bytes;
+            };
             const int64_t nu0 = (int64_t)P.units.size();
             std::vector<int32_t> down_of(nu0, -1);
             P.dunits.clear();
+            P.danc_off.clear();
+            P.xanc_size = 0;
             auto build = [&](int64_t a, int64_t b) {   // up units [a, b), all siblings
                 const Unit &f = P.units[a];
                 Unit d{f.game, f.lvl0, 0, (int32_t)P.ranges.size(), 0, -1, 0, f.depth};
                 int32_t lo = P.ranges[f.rng], hi = P.ranges[P.units[b - 1].rng + 1];
                 int32_t nl = 0;
                 for (int64_t k = a; k < b; k++) nl = std::max(nl, P.units[k].nlvl);
-                int64_t fd = 0;
-                // the top level's parent sequences (one contiguous range: the
-                // infosets are sorted by parent), whose next x the top-down
-                // pass stages with the unit, as {ps0, ps1} in the first
-                // level's window record; none for the games' roots
-                int32_t ps0 = 0, ps1 = 0;
-                if (lo < hi && P.inf_par[lo] >= 0) {
-                    ps0 = P.inf_par[lo];
-                    ps1 = P.inf_par[hi - 1] + 1;
-                    fd += span16(ps1 - ps0, 4);
+                int64_t fd = ancestors(lo, hi);
+                int64_t anc_seqs = 0;
+                for (auto &c : chain) {
+                    push_level(c.first, c.second);
+                    anc_seqs += P.inf_seq[c.second] - P.inf_seq[c.first];
                 }
-                const int64_t rec0 = d.rng / kLvl;
+                const int32_t n_anc = (int32_t)chain.size();
+                d.nlvl = n_anc;
                 for (int32_t k = 0; k < nl && lo < hi; k++) {
                     push_level(lo, hi);
                     const int32_t slo = P.inf_seq[lo], shi = P.inf_seq[hi];
@@ -664,11 +646,12 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                     lo = P.seq_child[slo];
                     hi = P.seq_child[shi];
                 }
-                if (d.nlvl > 0) {
-                    P.rwin[4 * rec0] = ps0;
-                    P.rwin[4 * rec0 + 1] = ps1;
-                }
                 if (d.nlvl < kMaxStagedLevels && fd <= opt.item_bytes) d.flags |= kStaged;
+                d.flags |= n_anc << kAncShift;
+                // a unit worked from global memory keeps its ancestors' x in
+                // a scratch area of its own
+                P.danc_off.push_back((d.flags & kStaged) ? 0 : (int32_t)P.xanc_size);
+                if (!(d.flags & kStaged)) P.xanc_size += anc_seqs;
                 const int32_t up_par = f.parent;
                 if (up_par >= 0) {
                     d.parent = down_of[up_par];
@@ -687,12 +670,9 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 }
                 return fd;
             };
-            // the staged parent x of merged siblings [a, k]: their top levels'
-            // parent range, from the first's first parent to k's last
-            auto parent_bytes = [&](int64_t a, int64_t k) -> int64_t {
-                const int32_t lo = P.ranges[P.units[a].rng], hi = P.ranges[P.units[k].rng + 1];
-                if (lo >= hi || P.inf_par[lo] < 0) return 0;
-                return span16(P.inf_par[hi - 1] + 1 - P.inf_par[lo], 4);
+            // the ancestor chain of merged siblings [a, k]
+            auto chain_bytes = [&](int64_t a, int64_t k) -> int64_t {
+                return ancestors(P.ranges[P.units[a].rng], P.ranges[P.units[k].rng + 1]);
             };
             int64_t a = 0, acc = 0;
             for (int64_t k = 0; k < nu0; k++) {
@@ -700,7 +680,7 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 const int64_t fk = fdown(u);
                 const bool same = k > a && u.game == P.units[a].game && u.parent == P.units[a].parent &&
                                   u.parent >= 0 && u.lvl0 == P.units[a].lvl0;
-                if (!same || acc + fk + parent_bytes(a, k) > opt.item_bytes) {
+                if (!same || acc + fk + chain_bytes(a, k) > opt.item_bytes) {
                     if (k > a) build(a, k);
                     a = k;
                     acc = 0;

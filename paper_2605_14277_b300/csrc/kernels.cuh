@@ -1,6 +1,7 @@
 // Device building blocks of one sequence-form CFR iteration (sm_103a).
 //
-// One player's half-step is two launches over the forest layout (layout.h):
+// One player's half-step is two persistent launches over the forest layout
+// (layout.h), each taking units of work from a queue:
 //
 //   up   : per unit (a range of subtrees, a few levels deep), deepest level
 //          first:
@@ -8,20 +9,21 @@
 //            - V[s] = u[s] + sum of the child infosets' ev       (Alg. 2: v += L w + L v; q = B^T(w+v))
 //            - ev_j = sum_a b_j[a] V[(j,a)]                       (C (b . q))
 //            - r += V - ev_j, variant post-op, next strategy     (Alg. 2 regret update; Alg. 3-5)
-//          Leaf units come from a queue; the CTA that completes the last
-//          child of an internal unit runs that unit next, up to the game's
-//          root unit.
+//          The queue holds every leaf unit, then the internal units deepest
+//          first; an internal unit waits (bounded) until its children have
+//          counted themselves done, then copies in their top-level ev.  Once a
+//          CTA finds the queue empty it joins the average update
+//          xbar += t^gamma x for the strategy x about to be replaced.
 //   down : per unit, top-down: x[(j,a)] = x[p_j] b_j[a]          (Alg. 2: y += L^T y; x = A^T y)
-//          and the average xbar += t^gamma x (for the x being replaced).
-//          The up pass's root unit published the next x of every internal
-//          unit (xn), so the units are independent.
+//          Each unit first recomputes the next x of its ancestor chain (the
+//          infosets above its top level, up to the game's root) from the
+//          final b, so the units are independent of one another.
 //
 // Completion is counted with one atomic per unit (threadfence-reduction
-// pattern); an internal unit waits, bounded in time, for its children, which
-// come earlier in the queue and are held by running CTAs.  Cumulative regrets and
-// average sums are float-float pairs (Kahan-compensated FP32): B300's FP64
-// rate is far below its FP32 rate, so the hot path does no FP64 arithmetic.
-// The best-response pass (MODE_BR) runs in FP64.
+// pattern).  Cumulative regrets and average sums are float-float pairs
+// (Kahan-compensated FP32): B300's FP64 rate is far below its FP32 rate, so
+// the hot path does no FP64 arithmetic.  The best-response pass (MODE_BR)
+// runs in FP64.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -52,23 +54,21 @@ struct DevPlayer {
     // reads an entry with two independent loads
     const int4 *upq, *downq;
     const int32_t *ranges, *game_root;
-    const int32_t *itd;             // internal ranges below each root: {j0, j1, last of level}
     // the other player's x for a staged level: per-entry gathers, or copied
     // windows of it (rwin: {w0, w1, x-area bytes, 0} per range record; win:
     // {c0, c1, byte offset, level} per window; lcol: the staged columns,
     // local to the level's x area where it has windows)
     const int32_t *lcol;
     const int4 *rwin, *win;
-    const int64_t *itd_off;         // [G + 1]
     int32_t n_units, n_up, G;       // n_units: top-down units; n_up: bottom-up queue length
     int32_t S;                      // sequences
     // state
     float2 *r;       // cumulative regret, float-float (hi, lo)
     float *b;        // behavioural strategy to be played next
     float *x;        // sequence-form strategy of the last NextStrategy
-    float *xn;       // next x of each root unit's sequences (written by the up pass)
     float2 *xbar;    // weighted sum of played x, float-float
     // scratch
+    float *xanc;     // top-down units worked from global memory: their ancestors' x
     float *u, *ev;
     double *u64, *ev64, *xnorm;
     // unit_cnt: children completed in the current bottom-up pass (reset by
@@ -80,8 +80,9 @@ struct DevPlayer {
     // qavg: the average pass's chunk queue words {head, exit count, launches}
     int32_t *qavg;
     // root_done[g]: set by the bottom-up loop of a fused half-step once game
-    // g's root unit has written b and xn (the launch's top-down epoch + 1)
+    // g's root unit has written b (the launch's top-down epoch + 1)
     int32_t *root_done;
+    uint64_t wait_ns;               // longest wait of a unit for the units it depends on
 };
 
 struct ItemParams;
@@ -103,6 +104,7 @@ struct IterArgs {
     int average;            // down pass: accumulate xbar (0 when only rebuilding x)
     int pslot;              // parameter-table entry of this pass: iteration t = t_done + pslot
                             // at the time the table was filled
+    int keep_values;        // up pass: store the ev of every infoset (not only each unit's top level)
 };
 
 // ---------------------------------------------------------------------------
@@ -265,6 +267,20 @@ __device__ __forceinline__ float rm_inverse(float pos) {
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(pos));
     return r;
 }
+// Regrets scale with the opponent's reach, which can fall below FP32's
+// normal range deep in a game once the strategies sharpen; the reciprocal of a
+// positive sum below 2^-128 would overflow to infinity (and q * inf = NaN for
+// the other actions).  So sums below 2^-64 are first scaled by 2^64, exactly,
+// and so is each clipped regret q: b = (q sc) / (pos sc) = q / pos, with a
+// finite normaliser (pos sc >= 2^-85).  Sums at or above 2^-64 take sc = 1.
+struct RmNorm {
+    float inv, sc;
+};
+__device__ __forceinline__ RmNorm rm_norm(float pos) {
+    const float sc = pos < 0x1p-64f ? 0x1p64f : 1.f;
+    return RmNorm{pos > 0.f ? rm_inverse(pos * sc) : 0.f, sc};
+}
+__device__ __forceinline__ float rm_prob(float q, const RmNorm &n) { return (q * n.sc) * n.inv; }
 // the uniform probability 1/na, correctly rounded (the constants are the
 // compiler's correctly rounded quotients)
 __device__ __forceinline__ float uniform_prob(int na) {
@@ -301,9 +317,9 @@ __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const Ite
         P.u[s] = q;
         pos += q;
     }
-    const float inv = pos > 0.f ? rm_inverse(pos) : 0.f;
+    const RmNorm nrm = rm_norm(pos);
     const float uni = uniform_prob(na);
-    for (int s = s0; s < s1; s++) P.b[s] = pos > 0.f ? P.u[s] * inv : uni;
+    for (int s = s0; s < s1; s++) P.b[s] = pos > 0.f ? rm_prob(P.u[s], nrm) : uni;
 }
 
 // best-response step (MODE_BR, FP64): V = u + sum children, ev = max_a V

@@ -60,6 +60,8 @@ constexpr int kInternal = 2;     // the deepest level's child infosets are other
                                  // their range [c0, c1) follows the unit's levels as one more
                                  // kLvl record {c0, c1, 0, 0, 0, 0}
 constexpr int kChildOfRoot = 4;  // the parent is the game's root unit (informational)
+constexpr int kAncShift = 16;    // top-down units: flags >> kAncShift = levels of the ancestor chain
+                                 // staged before the unit's own levels (computed, not written back)
 constexpr int kMaxStagedLevels = 24;
 constexpr int32_t kWinGap = 16;   // x windows: columns further apart than this start a new window
 constexpr int64_t kMaxWin = 32;   // x windows: at most this many per staged level
@@ -107,24 +109,20 @@ struct PlayerLayout {
     // the level's x area, level within the unit}; w0 == w1 means gathered.
     // lcol is the staged column array: for a windowed level, the entry's
     // float index into its level's x area; otherwise m_col.
-    // For a top-down unit's first level the record holds instead {ps0, ps1,
-    // 0, 0}: the parent sequences [ps0, ps1) of its infosets (empty for the
-    // games' roots), whose next x is staged with the unit.
     std::vector<int32_t> rwin;          // 4 ints per range record
     std::vector<int32_t> win;           // 4 ints per window
     std::vector<int32_t> lcol;          // [Z]
     std::vector<int32_t> up_queue;      // leaves largest first, then internal units deepest first
     std::vector<Unit> dunits;           // top-down units: runs of sibling units merged up to the
                                         // buffer (the top-down pass moves ~5x fewer bytes per
-                                        // sequence); parent / nchild / depth in this tree
+                                        // sequence); parent / nchild / depth in this tree.  Their
+                                        // range records start with the ancestor chain (flags >>
+                                        // kAncShift levels, from level 0 down), then their own levels
+    std::vector<int32_t> danc_off;      // [dunits] a unit worked from global memory: offset of its
+                                        // ancestors' x in the scratch area (xanc_size floats)
+    int64_t xanc_size = 0;
     std::vector<int32_t> down_queue;    // all top-down units by tree depth, then largest first
     std::vector<int32_t> game_root;     // [G] root unit of each game
-    // Per game, the infoset ranges of its internal units below the root unit,
-    // top down: {j0, j1, last range of its level} triples.  The bottom-up
-    // pass's root unit runs the top-down pass over them, so every unit's
-    // parents have their next x published before the top-down pass starts.
-    std::vector<int32_t> itd;           // 3 ints per range
-    std::vector<int64_t> itd_off;       // [G + 1] range offsets
     std::vector<int32_t> game_tiers;    // [G] depth of the game's unit tree + 1
     // caller order: game g's caller infoset k is ext_inf[game_jbase[g] + k]; its
     // sequences start at caller index ext_seq0[game_jbase[g] + k]

@@ -15,7 +15,7 @@
 namespace cfrb {
 
 constexpr uint32_t kWaitLimit = 1u << 26;          // polls of an mbarrier before giving up
-constexpr uint64_t kFlagWaitNs = 1000000000ull;    // longest wait for a parent unit (1 s)
+constexpr uint64_t kFlagWaitNs = 1000000000ull;    // default longest wait for another unit (1 s)
 constexpr int kErrTimeout = 1;
 constexpr uint32_t kChunk = 4096;                  // bulk copies above this size are split across the warp
 
@@ -97,14 +97,14 @@ __device__ __forceinline__ void st_release(int32_t *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 // bounded wait for *flag == want (one thread): false (and the error word set)
-// if it does not happen within kFlagWaitNs
-__device__ __forceinline__ bool flag_wait(const int32_t *flag, int want, int32_t *err) {
+// if it does not happen within limit_ns
+__device__ __forceinline__ bool flag_wait(const int32_t *flag, int want, int32_t *err, uint64_t limit_ns) {
     if (ld_acquire(flag) == want) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t k = 0;; k++) {
         __nanosleep(k < 16 ? 32 : 256);
         if (ld_acquire(flag) == want) return true;
-        if ((k & 63) == 63 && globaltimer() - t0 > kFlagWaitNs) break;
+        if ((k & 15) == 15 && globaltimer() - t0 > limit_ns) break;
     }
     atomicExch(err, kErrTimeout);
     return false;
@@ -149,10 +149,8 @@ struct DownTab {
     uint32_t b;     // float, copied in
     uint32_t x;     // float, the next x (work area)
     uint32_t ipar, iseq;
-    uint32_t xp;    // first level: next x of the parent sequences [ps0, ps1)
-    int32_t ps0;
 };
-constexpr int kDownArrays = 4;   // commands staged per top-down level
+constexpr int kDownArrays = 3;   // commands staged per top-down level: b, infoset parents, infoset segments
 // an internal unit's staged child values: ev of infosets [c0, c1), brought in
 // by one bulk copy (dst, src, bytes) once all its children are done
 struct ChildEv {
@@ -401,13 +399,12 @@ __device__ __forceinline__ void copy_child_ev(const ChildEv &c, int t, int nt) {
         cp_async16_cg(sh<unsigned char>(c.dst) + k, (const unsigned char *)c.src + k);
 }
 
-// Warp 0: lay out a down unit in buffer `buf`, stage its copies as commands
-// (cmd[kDownArrays * level + f]: f = 0 b, 1 infoset parents, 2 infoset
-// segments, 3 the first level's parents' next x) and issue those `what`
+// Warp 0: lay out a down unit in buffer `buf` (its ancestor chain first, then
+// its own levels), stage its copies as commands (cmd[kDownArrays * level + f]:
+// f = 0 b, 1 infoset parents, 2 infoset segments) and issue those `what`
 // selects: kDownOwn (the index arrays, which no pass writes) and/or kDownB
-// (b and the parents' x, which the bottom-up pass writes).  With kDownArm the
-// barrier is armed with `carried` plus the bytes issued here.  Returns this
-// lane's bytes.
+// (b, which the bottom-up pass writes).  With kDownArm the barrier is armed
+// with `carried` plus the bytes issued here.  Returns this lane's bytes.
 constexpr int kDownOwn = 1, kDownB = 2, kDownArm = 4;
 __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char *buf, uint64_t *bar, SLvl *lv,
                                DownTab *tab, BulkCmd *cmd, int what, uint32_t carried) {
@@ -416,15 +413,10 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
     const int nl = hdr.y;
     SLvl L{0, 0, 0, 0, 0, 0};
     int64_t bytes = 0;
-    int4 pr = make_int4(0, 0, 0, 0);   // first level: {ps0, ps1, 0, 0}
     if (lane < nl) {
         const int32_t *d = rng + kLvl * lane;
         L = SLvl{d[0], d[1], d[2], d[3], d[4], d[5]};
         bytes = down_level_bytes(L.s1 - L.s0, L.j1 - L.j0);
-        if (lane == 0) {
-            pr = P.rwin[hdr.z / kLvl];
-            if (pr.y > pr.x) bytes += span16(pr.y - pr.x, 4);
-        }
     }
     unsigned char *cur = buf + level_offset(bytes);
     fence_proxy_async();
@@ -441,21 +433,15 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
         CFR_STAGE(b, P.b, L.s0, L.s1, 4, 0)
         CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 1)
         CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 2)
-        if (lane == 0 && pr.y > pr.x) {
-            CFR_STAGE(xp, P.xn, pr.x, pr.y, 4, 3)
-        } else {
-            c[3] = BulkCmd{nullptr, 0u, 0u};
-        }
 #undef CFR_STAGE
         t.x = sh_off(cur);
         cur += work16(L.s1 - L.s0, 4);
-        t.ps0 = pr.x;
     }
     __syncwarp();
     uint32_t mine = carried;
     for (int k = lane; k < kDownArrays * nl; k += 32) {
         const int f = k % kDownArrays;
-        if (!(what & ((f == 0 || f == 3) ? kDownB : kDownOwn))) continue;
+        if (!(what & (f == 0 ? kDownB : kDownOwn))) continue;
         const BulkCmd c = cmd[k];
         for (uint32_t o = 0; o < c.bytes; o += kChunk)
             bulk_g2s_to(c.dst + o, (const char *)c.src + o, min(kChunk, c.bytes - o), bar);
@@ -467,10 +453,8 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
 
 // Up pass of a staged unit (consumer warps only): gathers of the other
 // player's x, payoff rows, bottom-up values, regret update, variant post-op
-// and next strategy, all in shared memory; then write-back.  An internal unit's deepest level finds its
-// children's ev in the staged child range.  The game's root unit also runs
-// its top-down pass with the new strategy (x of its sequences into xn), so
-// the top-down pass below it need not wait for it.
+// and next strategy, all in shared memory; then write-back.  An internal
+// unit's deepest level finds its children's ev in the staged child range.
 constexpr int kRegA = 4;    // infosets with at most kRegA actions keep their values in registers
 
 // shared-memory views of one staged up level
@@ -522,11 +506,11 @@ __device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int 
         qv[a] = (a < na && x > 0.f) ? x : 0.f;
         pos += qv[a];
     }
-    const float inv = pos > 0.f ? rm_inverse(pos) : 0.f;
+    const RmNorm nrm = rm_norm(pos);
     const float uni = uniform_prob(na);
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
-        if (a < na) t.b[q0 + a] = pos > 0.f ? qv[a] * inv : uni;
+        if (a < na) t.b[q0 + a] = pos > 0.f ? rm_prob(qv[a], nrm) : uni;
 }
 
 // the same for infosets with more actions, through shared memory
@@ -546,9 +530,9 @@ __device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float
         t.V[q] = qq;   // V is no longer needed: keep the clipped regret
         pos += qq;
     }
-    const float inv = pos > 0.f ? rm_inverse(pos) : 0.f;
+    const RmNorm nrm = rm_norm(pos);
     const float uni = uniform_prob(q1 - q0);
-    for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? t.V[q] * inv : uni;
+    for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? rm_prob(t.V[q], nrm) : uni;
 }
 
 // Ordered sums over a short index range, four terms per step: the four
@@ -598,35 +582,6 @@ __device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SL
     }
 }
 
-// the root's next x, top-down, into each level's V (no longer needed); level
-// 0's parent is the empty sequence (x = 1)
-__device__ __noinline__ void root_topdown(int nl, const SLvl *lv, const UpTab *tab) {
-    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
-    for (int k = 0; k < nl; k++) {
-        const SLvl L = lv[k];
-        const UpView t = view(tab[k]);
-        const int ni = L.j1 - L.j0;
-        for (int i = tid; i < ni; i += nt) {
-            float xp = 1.f;
-            if (k > 0) {
-                // the parent sequence: the one of level k-1 whose child range
-                // holds infoset j (child ranges are ascending)
-                const UpView pt = view(tab[k - 1]);
-                const int j = L.j0 + i;
-                int lo = 0, hi = lv[k - 1].s1 - lv[k - 1].s0;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (pt.sch[mid] <= j) lo = mid;
-                    else hi = mid;
-                }
-                xp = pt.V[lo];
-            }
-            for (int q = t.iseq[i] - L.s0; q < t.iseq[i + 1] - L.s0; q++) t.V[q] = xp * t.b[q];
-        }
-        consumer_sync();
-    }
-}
-
 // The payoff rows of a staged unit are worked by one consumer thread per
 // sequence, every level of the unit in one numbering (the thread index runs on
 // across levels, so a short level does not idle a round).  f(k, q) is called
@@ -663,10 +618,9 @@ __device__ __forceinline__ void up_gather(const float *__restrict__ xo, int nl, 
 
 // Part 2: the row sums V[s] = sign * sum_e val[e] x[col[e]] (products rounded,
 // then added in CSR order), each by the thread that gathered the row (its
-// own copies are complete, no barrier needed); then the levels bottom-up and,
-// for the game's root unit, its top-down pass into V.
+// own copies are complete, no barrier needed); then the levels bottom-up.
 __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
-                           const ChildEv *cev, bool internal, bool root) {
+                           const ChildEv *cev, bool internal) {
     cp_async_wait_all();
     for_rows(nl, lv, [&](int k, int q) {
         const int n0 = lv[k].n0;
@@ -691,13 +645,12 @@ __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, con
     case VAR_PCFR: up_levels<VAR_PCFR>(ip, nl, lv, tab, cev, internal); break;
     default: up_levels<VAR_CFR>(ip, nl, lv, tab, cev, internal); break;
     }
-    if (root) root_topdown(nl, lv, tab);
 }
 
-// Part 3: write-back (coalesced): r, b, the top level's ev, and the root
-// unit's next x (xn).
+// Part 3: write-back (coalesced): r, b and the top level's ev (every level's
+// with `all_ev`).
 __device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab,
-                                              bool root) {
+                                              bool all_ev) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
@@ -706,21 +659,20 @@ __device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const 
         for (int q = tid; q < ns; q += nt) {
             P.r[L.s0 + q] = t.r[q];
             P.b[L.s0 + q] = t.b[q];
-            if (root) P.xn[L.s0 + q] = t.V[q];
         }
     }
-    if (nl > 0) {
-        const int ni = lv[0].j1 - lv[0].j0;
-        const float *ev = sh<const float>(tab[0].ev);
-        for (int i = tid; i < ni; i += nt) P.ev[lv[0].j0 + i] = ev[i];
+    for (int k = 0; k < (all_ev ? nl : min(nl, 1)); k++) {
+        const int ni = lv[k].j1 - lv[k].j0;
+        const float *ev = sh<const float>(tab[k].ev);
+        for (int i = tid; i < ni; i += nt) P.ev[lv[k].j0 + i] = ev[i];
     }
 }
 
-// Down pass of a staged unit: x[(j,a)] = x[p_j] b_j[a] top-down, and
-// xbar += w x for the strategy being replaced.  The top level's parents
-// belong to the root or to internal units, whose next x the bottom-up pass
-// published in xn; the roots' parent is the empty sequence (x = 1).
-__device__ void compute_down(const DevPlayer &P, int nl, const SLvl *lv, const DownTab *tab) {
+// Down pass of a staged unit: x[(j,a)] = x[p_j] b_j[a] top-down over its
+// levels, the first n_anc of which are its ancestor chain (down to the parents
+// of its top level); level 0 of the chain holds the game's root, whose parent
+// is the empty sequence (x = 1).  Only the unit's own levels are written back.
+__device__ void compute_down(const DevPlayer &P, int nl, int n_anc, const SLvl *lv, const DownTab *tab) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
@@ -729,10 +681,8 @@ __device__ void compute_down(const DevPlayer &P, int nl, const SLvl *lv, const D
         float *x = sh<float>(t.x);
         const int32_t *ipar = sh<const int32_t>(t.ipar), *iseq = sh<const int32_t>(t.iseq);
         const int ni = L.j1 - L.j0;
-        // parents' x: the level above, or (the first level) the staged next
-        // x of the parent sequences
-        const int ps0 = (k > 0) ? lv[k - 1].s0 : t.ps0;
-        const float *xpar = sh<const float>((k > 0) ? tab[k - 1].x : t.xp);
+        const int ps0 = (k > 0) ? lv[k - 1].s0 : 0;
+        const float *xpar = sh<const float>((k > 0) ? tab[k - 1].x : t.x);
         for (int i = tid; i < ni; i += nt) {
             const int par = ipar[i];
             const float xp = par < 0 ? 1.f : xpar[par - ps0];
@@ -749,7 +699,7 @@ __device__ void compute_down(const DevPlayer &P, int nl, const SLvl *lv, const D
         }
         consumer_sync();
     }
-    for (int k = 0; k < nl; k++) {
+    for (int k = n_anc; k < nl; k++) {
         const SLvl L = lv[k];
         const float *x = sh<const float>(tab[k].x);
         const int ns = L.s1 - L.s0;

@@ -280,13 +280,21 @@ def large_random_game(seed: int = 3) -> Tree:
 def batch_games(n_games: int = 4096, seed0: int = 1000, lo: float = 1e2, hi: float = 1e5):
     """Seeded games with node counts log-uniform in [lo, hi], depth 4-10, 2-4
     actions, U[-1,1] payoffs."""
-    out = []
-    for s in range(seed0, seed0 + n_games):
-        rng = np.random.default_rng(s)
-        target = math.exp(rng.uniform(math.log(lo), math.log(hi)))
-        out.append(sized_random_game(s, target, depth_range=(4, 10), actions=(2, 4),
-                                     payoff="uniform", name=f"batch_s{s}"))
-    return out
+    return [batch_game(s, lo, hi) for s in range(seed0, seed0 + n_games)]
+
+
+def batch_game(seed: int, lo: float = 1e2, hi: float = 1e5) -> Tree:
+    """Game `seed` of the batched workload (see batch_games)."""
+    rng = np.random.default_rng(seed)
+    target = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+    return sized_random_game(seed, target, depth_range=(4, 10), actions=(2, 4),
+                             payoff="uniform", name=f"batch_s{seed}")
+
+
+def batch_sample_seeds(n_sample: int = 64, n_games: int = 4096, seed0: int = 1000):
+    """Seeds of an evenly spaced sample of the batched workload's games."""
+    step = max(1, n_games // n_sample)
+    return [seed0 + k * step for k in range(n_sample)]
 
 
 def serving_request(seed: int, lo: float = 1e3, hi: float = 1e6) -> Tree:

@@ -57,7 +57,7 @@ class Layout:
             d = {}
             for name in ("inf_seq", "seq_child", "inf_par", "seq_game", "m_ptr", "m_col", "ranges", "rwin", "win", "lcol",
                          "up_queue", "down_queue", "game_root", "game_tiers", "ext_inf", "ext_seq0", "units", "dunits",
-                         "itd"):
+                         "danc_off"):
                 m = L.probe_i32(h, p, name.encode(), None)
                 a = np.zeros(m, np.int32)
                 L.probe_i32(h, p, name.encode(), a.ctypes.data)
@@ -66,7 +66,7 @@ class Layout:
             a = np.zeros(m)
             L.probe_f64(h, p, b"m_val64", a.ctypes.data)
             d["m_val64"] = a
-            for name in ("game_jbase", "game_sbase", "itd_off"):
+            for name in ("game_jbase", "game_sbase"):
                 m = L.probe_i64(h, p, name.encode(), None)
                 a = np.zeros(m, np.int64)
                 L.probe_i64(h, p, name.encode(), a.ctypes.data)

@@ -59,7 +59,7 @@ int64_t probe_i32(void *h, int p, const char *name, void *out) {
     if (s == "down_queue") return copy_out(P.down_queue, out);
     if (s == "game_root") return copy_out(P.game_root, out);
     if (s == "game_tiers") return copy_out(P.game_tiers, out);
-    if (s == "itd") return copy_out(P.itd, out);
+    if (s == "danc_off") return copy_out(P.danc_off, out);
     if (s == "ext_inf") return copy_out(P.ext_inf, out);
     if (s == "ext_seq0") return copy_out(P.ext_seq0, out);
     if (s == "units" || s == "dunits") {
@@ -87,7 +87,6 @@ int64_t probe_i64(void *h, int p, const char *name, void *out) {
     std::string s(name);
     if (s == "game_jbase") return copy_out(P.game_jbase, out);
     if (s == "game_sbase") return copy_out(P.game_sbase, out);
-    if (s == "itd_off") return copy_out(P.itd_off, out);
     return -1;
 }
 

@@ -88,62 +88,47 @@ def check_invariants(lay, G_):
         for ui in range(len(units)):
             if units[ui][5] >= 0:
                 assert upos[units[ui][5]] > upos[ui]
-        # the internal ranges below each root: exactly the infosets of the
-        # game's internal non-root units, level by level top down, each level
-        # closed by a sync mark
-        itd, off = d["itd"].reshape(-1, 3), d["itd_off"]
-        assert off[0] == 0 and off[-1] == itd.shape[0] and len(off) == G_ + 1
-        level_of = np.zeros(J, np.int64)
-        for (g, lvl0, nlvl, r0, flags, par, nch, depth) in units:
-            for k in range(nlvl):
-                level_of[rng[r0 + 6 * k]: rng[r0 + 6 * k + 1]] = lvl0 + k
-        for g in range(G_):
-            want = set()
-            for (gg, lvl0, nlvl, r0, flags, par, nch, depth) in units:
-                if gg == g and par >= 0 and nch > 0:
-                    for k in range(nlvl):
-                        want.update(range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]))
-            got, last_level = [], -1
-            ents = itd[off[g]:off[g + 1]]
-            for k, (j0, j1, last) in enumerate(ents):
-                assert j1 > j0
-                lvls = set(level_of[j0:j1].tolist())
-                assert len(lvls) == 1
-                lvl = lvls.pop()
-                assert lvl >= last_level
-                if lvl > last_level and k > 0:
-                    assert ents[k - 1][2] == 1
-                last_level = lvl
-                got.extend(range(j0, j1))
-            assert len(got) == len(set(got)) and set(got) == want
-            if len(ents):
-                assert ents[-1][2] == 1
         # top-down units: merged runs of siblings; they cover every infoset
         # once, hang below their parent's deepest level, and come after it
+        # each starts with its ancestor chain (flags >> 16 records, the game's
+        # root level first): every chain level holds exactly the infosets
+        # that own the parents of the level below it
         du = d["dunits"]
         cover = np.zeros(J, np.int64)
         dunit_of = {}
+
+        def owner(seq):
+            return np.searchsorted(inf_seq, seq, side="right") - 1
+
         for di, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(du):
-            prev = None
-            for k in range(nlvl):
-                lo, hi, s0, s1 = rng[r0 + 6 * k: r0 + 6 * k + 4]
+            n_anc = flags >> 16
+            assert n_anc == lvl0 and nlvl > n_anc
+            recs = [rng[r0 + 6 * k: r0 + 6 * k + 4] for k in range(nlvl)]
+            for k, (lo, hi, s0, s1) in enumerate(recs):
                 assert hi > lo and s0 == inf_seq[lo] and s1 == inf_seq[hi]
-                cover[lo:hi] += 1
-                for j in range(lo, hi):
-                    dunit_of[j] = (di, k)
-                if prev is not None:
-                    assert lo == seq_child[inf_seq[prev[0]]] and hi == seq_child[inf_seq[prev[1]]]
-                prev = (lo, hi)
+                if k == 0:
+                    assert (inf_par[lo:hi] < 0).all() and hi - lo == 1 and d["seq_game"][s0] == g
+                else:
+                    plo, phi = recs[k - 1][0], recs[k - 1][1]
+                    if k <= n_anc:   # a chain level, or the unit's top level: parents in the level above
+                        assert plo == owner(inf_par[lo]) and phi == owner(inf_par[hi - 1]) + 1
+                    if k > n_anc:    # own levels: the children of the level above
+                        assert lo == seq_child[inf_seq[plo]] and hi == seq_child[inf_seq[phi]]
+                if k >= n_anc:
+                    cover[lo:hi] += 1
+                    for j in range(lo, hi):
+                        dunit_of[j] = (di, k)
         assert (cover == 1).all()
         nchild_d = np.zeros(len(du), np.int64)
         for di, (g, lvl0, nlvl, r0, flags, par, nch, depth) in enumerate(du):
-            lo, hi = rng[r0], rng[r0 + 1]
+            n_anc = flags >> 16
+            lo, hi = rng[r0 + 6 * n_anc], rng[r0 + 6 * n_anc + 1]
             if par < 0:
                 assert lvl0 == 0 and hi - lo == 1
                 continue
             nchild_d[par] += 1
             for j in range(lo, hi):
-                pinf = np.searchsorted(inf_seq, inf_par[j], side="right") - 1
+                pinf = owner(inf_par[j])
                 assert dunit_of[pinf] == (par, du[par][2] - 1)
             assert bool(flags & 4) == (du[par][5] < 0)
         assert nchild_d.tolist() == du[:, 6].tolist()
@@ -174,17 +159,9 @@ def test_staged_units_fit_their_buffer():
             d = lay.pl[p]
             n_staged = 0
             for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["dunits"]:
+                # own levels and the ancestor chain staged with them
                 rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
                 fd = sum(down_bytes(s1 - s0, j1 - j0) for j0, j1, s0, s1, n0, n1 in rng)
-                # the top level's parent sequences, staged with the unit
-                ps0, ps1 = d["rwin"][4 * (r0 // 6): 4 * (r0 // 6) + 2]
-                j0, j1 = rng[0, :2]
-                parents = d["inf_par"][j0:j1]
-                if parents[0] < 0:
-                    assert (parents < 0).all() and ps0 == ps1 == 0
-                else:
-                    assert ps0 == parents.min() and ps1 == parents.max() + 1
-                    fd += span16(ps1 - ps0, 4)
                 if flags & 1:
                     assert fd <= item_bytes and nlvl <= 24
             for (g, lvl0, nlvl, r0, flags, par, nch, depth) in d["units"]:
@@ -297,17 +274,20 @@ class Sim:
         inf_seq, rng, inf_par = d["inf_seq"], d["ranges"], d["inf_par"]
         x, xbar, b = st[p]["x"], st[p]["xbar"], st[p]["b"]
         units = d["dunits"]
-        finished = np.zeros(len(units), bool)
+        # every unit works from its own values only: the next x of its
+        # ancestor chain (recomputed, not written) and of its own levels
         for ui in d["down_queue"]:
             g, lvl0, nlvl, r0, flags, par = units[ui][:6]
-            assert par < 0 or finished[par]
+            n_anc = flags >> 16
+            local = {}
             for k in range(nlvl):
                 for j in range(rng[r0 + 6 * k], rng[r0 + 6 * k + 1]):
-                    xp = 1.0 if inf_par[j] < 0 else x[inf_par[j]]
+                    xp = 1.0 if inf_par[j] < 0 else local[inf_par[j]]
                     for s in range(inf_seq[j], inf_seq[j + 1]):
-                        xbar[s] += w[g] * x[s]
-                        x[s] = xp * b[s]
-            finished[ui] = True
+                        local[s] = xp * b[s]
+                        if k >= n_anc:
+                            xbar[s] += w[g] * x[s]
+                            x[s] = local[s]
 
     def iteration(self, st, variant, alpha, beta, gamma, alternating, t_done):
         t = t_done + 1.0
