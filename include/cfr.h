@@ -111,6 +111,13 @@ int cfr_load_batch(const cfr_tree_desc *games, int64_t n_games, void *cuda_strea
  *          GPU for the units it depends on before giving up (the wait is
  *          bounded so that a fault elsewhere cannot hang the device; the
  *          context then reports CFR_ERR_TIMEOUT); 0 = the default, 1 s.
+ *   precision: 0 or 32 = the passes in FP32 with float-float (Kahan)
+ *          regret and average sums (default, the fast path); 64 = every
+ *          pass in FP64 from global memory (payoffs, values, regrets,
+ *          strategies and averages), for games whose iterates are sensitive
+ *          to FP32 rounding or range (exact regret ties, reach below 1e-38);
+ *          several times slower.  Calls that return state convert it to FP64
+ *          either way.
  *   reserved: must be zero.
  * Every choice computes the same iteration; they differ only in speed (see
  * the autotuner in the Python package). */
@@ -120,12 +127,14 @@ typedef struct {
     int32_t passes;
     int32_t values;
     int32_t wait_us;
-    int32_t reserved[3];
+    int32_t precision;
+    int32_t reserved[2];
 } cfr_load_options;
 
 /* cfr_load_batch with load options (NULL = defaults).  CFR_ERR_ARG on an
  * unknown shape, a flat or values field other than 0/1, passes outside 0..2,
- * a negative wait_us or a nonzero reserved field. */
+ * a negative wait_us, a precision other than 0, 32 or 64, or a nonzero
+ * reserved field. */
 int cfr_load_batch_opts(const cfr_tree_desc *games, int64_t n_games, void *cuda_stream,
                         const cfr_load_options *options, cfr_ctx **out);
 

@@ -30,7 +30,8 @@ class CFRError(RuntimeError):
 
 class LoadOptions(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("flat", ctypes.c_int32), ("passes", ctypes.c_int32),
-                ("values", ctypes.c_int32), ("wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("values", ctypes.c_int32), ("wait_us", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class TreeDesc(ctypes.Structure):
@@ -153,17 +154,18 @@ class Solver:
     launches per player and half-iteration; 0 / False = the library's
     choice); every choice computes the same iterations.  ``values`` keeps every
     infoset's counterfactual value for ``get_values``; ``wait_us`` bounds a
-    unit's wait for the units it depends on (0 = the library's 1 s)."""
+    unit's wait for the units it depends on (0 = the library's 1 s);
+    ``precision`` 64 runs every pass in FP64 (default 32: FP32 passes)."""
 
     def __init__(self, trees, stream=None, shape: int = 0, flat: bool = False, passes: int = 0,
-                 values: bool = False, wait_us: int = 0):
+                 values: bool = False, wait_us: int = 0, precision: int = 32):
         L = lib()
         batch = isinstance(trees, (list, tuple))
         trees = list(trees) if batch else [trees]
         keep = []
         descs = (TreeDesc * len(trees))(*[_desc(t, keep) for t in trees])
         h = ctypes.c_void_p()
-        opts = LoadOptions(int(shape), int(bool(flat)), int(passes), int(bool(values)), int(wait_us))
+        opts = LoadOptions(int(shape), int(bool(flat)), int(passes), int(bool(values)), int(wait_us), int(precision))
         _check(L.cfr_load_batch_opts(descs, len(trees), _stream_handle(stream), ctypes.byref(opts), ctypes.byref(h)),
                "cfr_load_batch_opts")
         self.shape, self.flat, self.passes = int(shape), bool(flat), int(passes)

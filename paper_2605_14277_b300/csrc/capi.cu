@@ -88,7 +88,7 @@ __global__ void k_params(DevGames gm, IterArgs ia, int G) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int g = (int)(e / (kParamSpan + 1)), k = (int)(e % (kParamSpan + 1));
         const int32_t t0 = gm.t_done[g];
-        params_of_t(gm, ia, g, t0 + k, &gm.par[e]);
+        params_of_t(gm, ia, g, t0 + k, &gm.par[e], gm.par64 ? &gm.par64[e] : nullptr);
         if (k == 0) {
             gm.pbase[g] = t0;
             if (t0 != gm.t_done[0] || gm.active[g] != gm.active[0]) *gm.mixed = 1;
@@ -96,20 +96,25 @@ __global__ void k_params(DevGames gm, IterArgs ia, int G) {
     }
 }
 
-// Best-response pass (MODE_BR, FP64) over every unit from global memory, in
-// bottom-up queue order: an internal unit waits (bounded) until its children
-// are done; the root's ev is the game's best-response value.
+__device__ void average_pass64(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, int64_t S);
+
+// Passes over every unit from global memory, in bottom-up queue order: an
+// internal unit waits (bounded) until its children are done.  MODE_BR: the
+// FP64 best response (the root's ev is the game's best-response value);
+// MODE_CFR64: the bottom-up pass of an FP64 iteration (precision 64), with
+// the average update once the queue is empty, as in the staged pass.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const void *xo, IterArgs ia) {
     extern __shared__ __align__(128) unsigned char smem[];
     void *stage = smem;
     __shared__ int s_item, s_err;
     __shared__ ItemParams s_ip;
+    __shared__ ItemParams64 s_ip64;
+    if (threadIdx.x == 0) s_err = MODE == MODE_CFR64 && __ldcg(P.err) != 0;   // a timed-out context does no work
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = atomicAdd(&P.qup[0], 1);
-            s_err = 0;
-        }
+        if (s_err) break;
+        if (threadIdx.x == 0) s_item = atomicAdd(&P.qup[0], 1);
         __syncthreads();
         const int it = s_item;
         if (it >= P.n_up) break;
@@ -118,7 +123,13 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         const int u = q.x;
         const int2 tr = make_int2(q.y, q.z);
         if (threadIdx.x == 0) {
-            item_params(gm, ia, d.x, &s_ip);
+            if (MODE == MODE_CFR64) {
+                s_ip64 = gm.par64[(int64_t)d.x * (kParamSpan + 1) + ia.pslot];
+                s_ip.active = s_ip64.active;
+                s_ip.t = s_ip64.t;
+            } else {
+                item_params(gm, ia, d.x, &s_ip);
+            }
             if (s_ip.active && tr.y > 0) {
                 if (!flag_wait(&P.unit_cnt[u], tr.y, P.err, P.wait_ns)) s_err = 1;
                 P.unit_cnt[u] = 0;
@@ -129,11 +140,18 @@ __global__ void __launch_bounds__(kThreads) k_up(DevPlayer P, DevGames gm, const
         const ItemParams ip = s_ip;
         if (s_err) break;
         if (!ip.active) continue;
-        run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage);
+        run_up<MODE>(P, xo, ia, ip, d.y, P.ranges + d.z, stage, &s_ip64);
         unit_done(P, u);
         if (threadIdx.x == 0 && tr.x < 0 && MODE == MODE_BR) gm.br[d.x] = __ldcg(&P.ev64[d.x]);
+        if (threadIdx.x == 0 && tr.x < 0 && MODE == MODE_CFR64 && ia.first_of_iter) gm.t_done[d.x] = ip.t;
     }
-    launch_exit(P.qup);
+    if (MODE == MODE_CFR64) {
+        if (ia.average && !s_err) average_pass64(P, gm, ia, P.S);
+        __syncthreads();
+        launch_exit2(P.qup, P.qavg);
+    } else {
+        launch_exit(P.qup);
+    }
 }
 
 // The average strategy's update xbar += t^gamma x for the strategy x about to
@@ -201,6 +219,25 @@ __device__ void average_pass(const DevPlayer &P, const DevGames &gm, const IterA
         else
             average_chunk<false>(P, gm, ia, ip0, q0, q1);
         if (threadIdx.x == 0) s_chunk = next;
+    }
+}
+
+// The same in FP64 (precision 64): xbar += t^gamma x on the FP64 state, one
+// sequence per thread of each chunk.
+__device__ void average_pass64(const DevPlayer &P, const DevGames &gm, const IterArgs &ia, int64_t S) {
+    __shared__ int s_chunk64;
+    const int64_t nch = (S + kAvgChunk - 1) / kAvgChunk;
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk64 = atomicAdd(&P.qavg[0], 1);
+        __syncthreads();
+        const int64_t c = s_chunk64;
+        __syncthreads();
+        if (c >= nch) break;
+        const int64_t q1 = min((int64_t)S, (c + 1) * kAvgChunk);
+        for (int64_t s = c * kAvgChunk + threadIdx.x; s < q1; s += blockDim.x) {
+            const ItemParams64 pp = gm.par64[(int64_t)P.seq_game[s] * (kParamSpan + 1) + ia.pslot];
+            if (pp.active) P.xbar64[s] += pp.w * P.x64[s];
+        }
     }
 }
 
@@ -480,6 +517,52 @@ __device__ void run_down(const DevPlayer &P, int nlvl, int n_anc, const int32_t 
 }
 
 
+// the same in FP64 (precision 64); every unit keeps its ancestors' x in its
+// own scratch area
+__device__ void run_down64(const DevPlayer &P, int nlvl, int n_anc, const int32_t *rng, double *xa) {
+    int aoff = 0, poff = 0;
+    for (int k = 0; k < nlvl; k++) {
+        const int s0 = rng[kLvl * k + 2];
+        const int ps0 = k > 0 ? rng[kLvl * (k - 1) + 2] : 0;
+        const bool par_anc = k > 0 && k - 1 < n_anc, anc = k < n_anc;
+        for (int j = rng[kLvl * k] + (int)threadIdx.x; j < rng[kLvl * k + 1]; j += blockDim.x) {
+            const int par = P.inf_par[j];
+            const double xp = par < 0 ? 1.0 : par_anc ? __ldcg(&xa[poff + (par - ps0)]) : __ldcg(&P.x64[par]);
+            for (int s = P.inf_seq[j]; s < P.inf_seq[j + 1]; s++) {
+                const double v = xp * P.b64[s];
+                if (anc) xa[aoff + (s - s0)] = v;
+                else P.x64[s] = v;
+            }
+        }
+        __syncthreads();
+        if (anc) {
+            poff = aoff;
+            aoff += rng[kLvl * k + 3] - s0;
+        }
+    }
+}
+
+// Top-down pass of an FP64 iteration: every top-down unit from the queue,
+// worked from global memory.
+__global__ void __launch_bounds__(kThreads) k_down64(DevPlayer P, DevGames gm, IterArgs ia) {
+    __shared__ int s_item, s_err;
+    if (threadIdx.x == 0) s_err = __ldcg(P.err) != 0;
+    __syncthreads();
+    for (;;) {
+        if (s_err) break;
+        if (threadIdx.x == 0) s_item = atomicAdd(&P.qdn[0], 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= P.n_units) break;
+        const int4 h = P.downq[2 * it];
+        const int4 q = P.downq[2 * it + 1];
+        if (!gm.par64[(int64_t)h.x * (kParamSpan + 1) + ia.pslot].active) continue;
+        run_down64(P, h.y, h.w >> kAncShift, P.ranges + h.z, P.xanc64 + q.w);
+    }
+    launch_exit(P.qdn);
+}
+
 // Down pass (Alg. 2 NextStrategy: y += L^T y, x = A^T y; the average
 // xbar += t^gamma x was done by the bottom-up pass's CTAs before).  Every
 // unit recomputes the next x of its ancestor chain (the infosets above its
@@ -644,18 +727,32 @@ __global__ void k_uniform(DevPlayer P, int64_t J) {
         const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
         const float v = __frcp_rn((float)(s1 - s0));
         for (int s = s0; s < s1; s++) P.b[s] = v;
+        if (P.fp64)
+            for (int s = s0; s < s1; s++) P.b64[s] = 1.0 / (double)(s1 - s0);
     }
 }
+
+// the state of sequence s as FP64, from whichever precision the context keeps
+__device__ __forceinline__ double st_xbar(const DevPlayer &P, int64_t s) {
+    if (P.fp64) return P.xbar64[s];
+    const float2 v = P.xbar[s];
+    return (double)v.x + (double)v.y;
+}
+__device__ __forceinline__ double st_r(const DevPlayer &P, int64_t s) {
+    if (P.fp64) return P.r64[s];
+    const float2 v = P.r[s];
+    return (double)v.x + (double)v.y;
+}
+__device__ __forceinline__ double st_b(const DevPlayer &P, int64_t s) { return P.fp64 ? P.b64[s] : (double)P.b[s]; }
+__device__ __forceinline__ double st_x(const DevPlayer &P, int64_t s) { return P.fp64 ? P.x64[s] : (double)P.x[s]; }
 
 // normalised average (FP64) for the best-response pass; current x where no
 // iteration has been averaged yet
 __global__ void k_normalize(DevPlayer P, int64_t S) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
         const int g = P.seq_game[s];
-        const float2 dn = P.xbar[g];
-        const double den = (double)dn.x + (double)dn.y;
-        const float2 v = P.xbar[s];
-        P.xnorm[s] = den > 0.0 ? ((double)v.x + (double)v.y) / den : (double)P.x[s];
+        const double den = st_xbar(P, g);
+        P.xnorm[s] = den > 0.0 ? st_xbar(P, s) / den : st_x(P, s);
     }
 }
 
@@ -663,37 +760,41 @@ __global__ void k_normalize(DevPlayer P, int64_t S) {
 __global__ void k_get_state(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
                             double *out_r, double *out_b, double *out_xbar) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) {
-        const float2 v = P.xbar[g];
-        out_xbar[0] = (double)v.x + (double)v.y;
-    }
+    if (k == 0) out_xbar[0] = st_xbar(P, g);
     if (k >= Jg) return;
     const int j = ext_inf[k];
     const int base = ext_seq0[k];
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     for (int s = s0; s < s1; s++) {
         const int o = base + (s - s0);
-        const float2 r = P.r[s];
-        out_r[o] = (double)r.x + (double)r.y;
-        out_b[o] = (double)P.b[s];
-        const float2 xb = P.xbar[s];
-        out_xbar[1 + o] = (double)xb.x + (double)xb.y;
+        out_r[o] = st_r(P, s);
+        out_b[o] = st_b(P, s);
+        out_xbar[1 + o] = st_xbar(P, s);
     }
 }
 
 __global__ void k_set_state(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
                             const double *in_r, const double *in_b, const double *in_xbar) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) P.xbar[g] = ff_from_double(in_xbar[0]);
+    if (k == 0) {
+        if (P.fp64) P.xbar64[g] = in_xbar[0];
+        else P.xbar[g] = ff_from_double(in_xbar[0]);
+    }
     if (k >= Jg) return;
     const int j = ext_inf[k];
     const int base = ext_seq0[k];
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     for (int s = s0; s < s1; s++) {
         const int o = base + (s - s0);
-        P.r[s] = ff_from_double(in_r[o]);
-        P.b[s] = (float)in_b[o];
-        P.xbar[s] = ff_from_double(in_xbar[1 + o]);
+        if (P.fp64) {
+            P.r64[s] = in_r[o];
+            P.b64[s] = in_b[o];
+            P.xbar64[s] = in_xbar[1 + o];
+        } else {
+            P.r[s] = ff_from_double(in_r[o]);
+            P.b[s] = (float)in_b[o];
+            P.xbar[s] = ff_from_double(in_xbar[1 + o]);
+        }
     }
 }
 
@@ -704,12 +805,8 @@ __global__ void k_average(DevPlayer P, const int32_t *ext_inf, const int32_t *ex
     const int j = ext_inf[k];
     const int base = ext_seq0[k];
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
-    const float2 dp = P.xbar[P.inf_par[j]];
-    const double den = (double)dp.x + (double)dp.y;
-    for (int s = s0; s < s1; s++) {
-        const float2 v = P.xbar[s];
-        out[base + (s - s0)] = den > 0.0 ? ((double)v.x + (double)v.y) / den : 1.0 / (double)(s1 - s0);
-    }
+    const double den = st_xbar(P, P.inf_par[j]);
+    for (int s = s0; s < s1; s++) out[base + (s - s0)] = den > 0.0 ? st_xbar(P, s) / den : 1.0 / (double)(s1 - s0);
 }
 
 __global__ void k_set_t(int32_t *t_done, int g, int32_t t) { t_done[g] = t; }
@@ -719,13 +816,13 @@ __global__ void k_set_t(int32_t *t_done, int g, int32_t t) { t_done[g] = t; }
 __global__ void k_get_values(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
                              double *out_x, double *out_ev) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) out_x[0] = (double)P.x[g];
+    if (k == 0) out_x[0] = st_x(P, g);
     if (k >= Jg) return;
     const int j = ext_inf[k];
     const int base = ext_seq0[k];
-    out_ev[k] = (double)P.ev[j];
+    out_ev[k] = P.fp64 ? P.evc64[j] : (double)P.ev[j];
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
-    for (int s = s0; s < s1; s++) out_x[1 + base + (s - s0)] = (double)P.x[s];
+    for (int s = s0; s < s1; s++) out_x[1 + base + (s - s0)] = st_x(P, s);
 }
 
 }  // namespace cfrb
@@ -787,7 +884,7 @@ struct PlayerBuf {
     int32_t *ext_inf = nullptr, *ext_seq0 = nullptr;
     int64_t S = 0, J = 0, n_units = 0, n_up = 0;
     int n_levels = 0;
-    int grid_up = 1, grid_up_br = 1, grid_down = 1, grid_half = 1;
+    int grid_up = 1, grid_up_br = 1, grid_down = 1, grid_half = 1, grid_up64 = 1, grid_down64 = 1;
     size_t smem_br = 0;
     std::vector<int32_t> game_J, game_S;
     std::vector<int64_t> game_jbase;
@@ -814,6 +911,8 @@ struct cfr_ctx {
     uint8_t *active_keep = nullptr; // device copy of the caller's mask, restored after a
                                     // best-response pass (which runs every game)
     ItemParams *par = nullptr;      // per-game parameter table (kParamSpan + 1 entries)
+    ItemParams64 *par64 = nullptr;  // the same in FP64 (precision 64 only)
+    bool fp64 = false;              // precision 64: the iteration runs in FP64 from global memory
     int32_t *pbase = nullptr;
     int32_t *mixed = nullptr;   // set by k_params when the games' parameters differ
     double *br[2] = {nullptr, nullptr};
@@ -893,7 +992,9 @@ int upload(cfr_ctx *c, T **p, const std::vector<T> &v) {
     return CFR_OK;
 }
 
-DevGames dev_games(const cfr_ctx *c) { return DevGames{c->t_done, c->active, nullptr, c->par, c->pbase, c->mixed}; }
+DevGames dev_games(const cfr_ctx *c) {
+    return DevGames{c->t_done, c->active, nullptr, c->par, c->pbase, c->mixed, c->par64};
+}
 
 // the parameter table for the next kParamSpan iterations of every game
 int launch_params(cfr_ctx *c, int variant, double alpha, double beta, double gamma) {
@@ -912,8 +1013,11 @@ int launch_rebuild_x(cfr_ctx *c, int p) {
     TRY(launch_params(c, 0, 0.0, 0.0, 0.0));
     IterArgs ia{};
     ia.average = 0;
-    kConfigs[c->cfg].down<<<B.grid_down, c->threads, c->smem_staged, c->stream>>>(B.d, dev_games(c), ia,
-                                                                                   c->item_bytes);
+    if (c->fp64)
+        k_down64<<<B.grid_down64, kThreads, 0, c->stream>>>(B.d, dev_games(c), ia);
+    else
+        kConfigs[c->cfg].down<<<B.grid_down, c->threads, c->smem_staged, c->stream>>>(B.d, dev_games(c), ia,
+                                                                                       c->item_bytes);
     CU(cudaGetLastError());
     return CFR_OK;
 }
@@ -965,6 +1069,35 @@ int launch_iteration(cfr_ctx *c, int variant, double alpha, double beta, double 
     const bool pdl0 = pdl && !params;
     const float *x1 = A.d.x, *x2 = B.d.x;
     mark(0);
+    if (c->fp64) {
+        // precision 64: the same schedule with the FP64 passes, from global memory
+        const double *y1 = A.d.x64, *y2 = B.d.x64;
+        auto up64 = [&](PlayerBuf &P, const double *xo, const IterArgs &ia) {
+            k_up<MODE_CFR64><<<P.grid_up64, kThreads, P.smem_br, c->stream>>>(P.d, gm, (const void *)xo, ia);
+        };
+        auto down64 = [&](PlayerBuf &P) { k_down64<<<P.grid_down64, kThreads, 0, c->stream>>>(P.d, gm, dn); };
+        if (alternating) {
+            up64(A, y2, up1);
+            mark(1);
+            down64(A);
+            mark(2);
+            up64(B, y1, up2);
+            mark(3);
+            down64(B);
+        } else {
+            up64(A, y2, up1);
+            mark(1);
+            up64(B, y1, up2);
+            mark(2);
+            down64(A);
+            mark(3);
+            down64(B);
+        }
+        *nlaunch += 4;
+        mark(4);
+        CU(cudaGetLastError());
+        return CFR_OK;
+    }
     if (alternating && !c->split && !ev) {
         const HalfFn half = kConfigs[c->cfg].half;
         CU(launch_pass(half, A.grid_half, nt, sm, c->stream, pdl0, A.d, gm, x2, up1, dn, ib));
@@ -1091,6 +1224,18 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     TRY(dalloc(c, &d.b, H.S));
     TRY(dalloc(c, &d.x, H.S));
     TRY(dalloc(c, &d.xanc, H.xanc_size));
+    d.fp64 = c->fp64 ? 1 : 0;
+    d.r64 = d.b64 = d.x64 = d.xbar64 = d.evc64 = d.xanc64 = nullptr;
+    if (c->fp64) {
+        TRY(dalloc(c, &d.r64, H.S));
+        TRY(dalloc(c, &d.b64, H.S));
+        TRY(dalloc(c, &d.x64, H.S));
+        TRY(dalloc(c, &d.xbar64, H.S));
+        TRY(dalloc(c, &d.evc64, H.J));
+        TRY(dalloc(c, &d.xanc64, H.xanc_size));
+        for (double *a : {d.r64, d.x64, d.xbar64}) CU(cudaMemsetAsync(a, 0, H.S * sizeof(double), c->stream));
+        CU(cudaMemsetAsync(d.evc64, 0, H.J * sizeof(double), c->stream));
+    }
     TRY(dalloc(c, &d.xbar, H.S));
     TRY(dalloc(c, &d.u, H.S));
     TRY(dalloc(c, &d.ev, H.J));
@@ -1126,6 +1271,10 @@ int build_player(cfr_ctx *c, const Layout &L, int p) {
     }
     TRY(occupancy_grid((const void *)cf.up, c->threads, c->smem_staged, B.n_up, &B.grid_up));
     TRY(occupancy_grid((const void *)k_up<MODE_BR>, kThreads, B.smem_br, B.n_up, &B.grid_up_br));
+    // the FP64 iteration's bottom-up CTAs also run the average update: as
+    // many as fit, whatever the unit count
+    TRY(occupancy_grid((const void *)k_up<MODE_CFR64>, kThreads, B.smem_br, INT32_MAX, &B.grid_up64));
+    TRY(occupancy_grid((const void *)k_down64, kThreads, 0, B.n_units, &B.grid_down64));
     TRY(occupancy_grid((const void *)cf.down, c->threads, c->smem_staged, B.n_units, &B.grid_down));
     TRY(occupancy_grid((const void *)cf.half, c->threads, c->smem_staged, std::max(B.n_up, B.n_units),
                        &B.grid_half));
@@ -1143,19 +1292,23 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     int passes = 0;
     bool values = false;
     uint64_t wait_ns = kFlagWaitNs;
+    bool fp64 = false;
     if (lo) {
         if (lo->shape < 0 || lo->shape > kNumConfigs) return set_err(CFR_ERR_ARG, "unknown launch shape");
         if (lo->flat != 0 && lo->flat != 1) return set_err(CFR_ERR_ARG, "flat must be 0 or 1");
         if (lo->passes < 0 || lo->passes > 2) return set_err(CFR_ERR_ARG, "passes must be 0, 1 or 2");
         if (lo->values != 0 && lo->values != 1) return set_err(CFR_ERR_ARG, "values must be 0 or 1");
         if (lo->wait_us < 0) return set_err(CFR_ERR_ARG, "wait_us must not be negative");
-        for (int k = 0; k < 3; k++)
+        if (lo->precision != 0 && lo->precision != 32 && lo->precision != 64)
+            return set_err(CFR_ERR_ARG, "precision must be 0, 32 or 64");
+        for (int k = 0; k < 2; k++)
             if (lo->reserved[k] != 0) return set_err(CFR_ERR_ARG, "reserved load options must be zero");
         if (lo->shape > 0) shape = lo->shape - 1;
         flat = lo->flat != 0;
         passes = lo->passes;
         values = lo->values != 0;
         if (lo->wait_us > 0) wait_ns = 1000ull * (uint64_t)lo->wait_us;
+        fp64 = lo->precision == 64;
     }
     if (!games || n < 1) return set_err(CFR_ERR_ARG, "no games");
     std::vector<TreeView> tv(n);
@@ -1213,6 +1366,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     c->split = passes != 1;
     c->values = values;
     c->wait_ns = wait_ns;
+    c->fp64 = fp64;
     c->threads = kConfigs[c->cfg].threads;
     c->item_bytes = (int)opt.item_bytes;
     // two unit buffers; a unit too large to stage uses its buffer as the
@@ -1229,6 +1383,7 @@ int load(const cfr_tree_desc *games, int64_t n, void *stream, const cfr_load_opt
     if ((rc = dalloc(c, &c->active, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->active_keep, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->par, L.G * (kParamSpan + 1)))) return bail(rc);
+    if (c->fp64 && (rc = dalloc(c, &c->par64, L.G * (kParamSpan + 1)))) return bail(rc);
     if ((rc = dalloc(c, &c->pbase, L.G))) return bail(rc);
     if ((rc = dalloc(c, &c->mixed, 1))) return bail(rc);
     if ((rc = dalloc(c, &c->br[0], L.G))) return bail(rc);

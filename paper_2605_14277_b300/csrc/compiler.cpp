@@ -648,10 +648,10 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
                 }
                 if (d.nlvl < kMaxStagedLevels && fd <= opt.item_bytes) d.flags |= kStaged;
                 d.flags |= n_anc << kAncShift;
-                // a unit worked from global memory keeps its ancestors' x in
-                // a scratch area of its own
-                P.danc_off.push_back((d.flags & kStaged) ? 0 : (int32_t)P.xanc_size);
-                if (!(d.flags & kStaged)) P.xanc_size += anc_seqs;
+                // a unit worked from global memory (unstaged, or any unit in
+                // FP64) keeps its ancestors' x in a scratch area of its own
+                P.danc_off.push_back((int32_t)P.xanc_size);
+                P.xanc_size += anc_seqs;
                 const int32_t up_par = f.parent;
                 if (up_par >= 0) {
                     d.parent = down_of[up_par];

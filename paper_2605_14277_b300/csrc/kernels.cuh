@@ -39,7 +39,9 @@ enum { VAR_CFR = 0, VAR_PLUS = 1, VAR_DCFR = 2, VAR_PCFR_PLUS = 3, VAR_PCFR = 4 
 // predictive variants: the next strategy is regret matching of r + the
 // instantaneous regret just observed (Alg. 5 with m^(t+1) = u^t)
 __host__ __device__ constexpr bool predictive(int v) { return v == VAR_PCFR_PLUS || v == VAR_PCFR; }
-enum { MODE_CFR = 0, MODE_BR = 1 };
+// MODE_CFR: the FP32 iteration (units too large to stage); MODE_BR: the FP64
+// best response; MODE_CFR64: the iteration in FP64 throughout (precision 64)
+enum { MODE_CFR = 0, MODE_BR = 1, MODE_CFR64 = 2 };
 
 struct DevPlayer {
     // structure (read-only)
@@ -83,9 +85,15 @@ struct DevPlayer {
     // g's root unit has written b (the launch's top-down epoch + 1)
     int32_t *root_done;
     uint64_t wait_ns;               // longest wait of a unit for the units it depends on
+    // precision 64: the state in FP64 (the FP32 state above is then unused)
+    int fp64;
+    double *r64, *b64, *x64, *xbar64;
+    double *evc64;   // ev of every infoset from the last FP64 bottom-up pass
+    double *xanc64;  // top-down units: their ancestors' x
 };
 
 struct ItemParams;
+struct ItemParams64;
 struct DevGames {
     int32_t *t_done;        // completed iterations per game
     const uint8_t *active;  // 1 = advance this game
@@ -93,6 +101,7 @@ struct DevGames {
     ItemParams *par;        // [G][kParamSpan + 1] parameters of t = pbase[g] + k
     int32_t *pbase;         // [G]
     int32_t *mixed;         // 0: every game has game 0's parameters in every slot of the table
+    ItemParams64 *par64;    // the same table in FP64 (precision 64)
 };
 constexpr int kParamSpan = 64;   // iterations covered by one parameter table
 
@@ -155,20 +164,31 @@ struct ItemParams {
     int32_t active;
 };
 
+// the same in FP64
+struct ItemParams64 {
+    double w, fpos, fneg;
+    int32_t t, active;
+};
+
 __device__ __forceinline__ void params_of_t(const DevGames &gm, const IterArgs &ia, int g, int32_t t,
-                                            ItemParams *ip) {
+                                            ItemParams *ip, ItemParams64 *ip64 = nullptr) {
     const double td = (double)t;
     ip->t = t;
     ip->active = gm.active[g];
-    ip->w = ff_from_double(pow(td, ia.gamma));
+    const double w = pow(td, ia.gamma);
+    double fp = 1.0, fn = 1.0;
+    ip->w = ff_from_double(w);
     if (ia.variant == VAR_DCFR) {
         const double ta = pow(td, ia.alpha), tb = pow(td, ia.beta);
-        ip->fpos = ff_from_double(ta / (ta + 1.0));
-        ip->fneg = ff_from_double(tb / (tb + 1.0));
+        fp = ta / (ta + 1.0);
+        fn = tb / (tb + 1.0);
+        ip->fpos = ff_from_double(fp);
+        ip->fneg = ff_from_double(fn);
     } else {
         ip->fpos = make_float2(1.f, 0.f);
         ip->fneg = make_float2(1.f, 0.f);
     }
+    if (ip64) *ip64 = ItemParams64{w, fp, fn, t, ip->active};
 }
 __device__ __forceinline__ void item_params(const DevGames &gm, const IterArgs &ia, int g, ItemParams *ip) {
     params_of_t(gm, ia, g, gm.t_done[g] + (ia.first_of_iter ? 1 : 0), ip);
@@ -322,6 +342,37 @@ __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const Ite
     for (int s = s0; s < s1; s++) P.b[s] = pos > 0.f ? rm_prob(P.u[s], nrm) : uni;
 }
 
+// the bottom-up step in FP64 (precision 64): the same arithmetic as
+// up_infoset_cfr on the FP64 state, with regret matching's division exact
+// (IEEE) and the FP64 parameters
+__device__ void up_infoset_cfr64(const DevPlayer &P, int j, int variant, const ItemParams64 &ip) {
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    const bool pred = predictive(variant);
+    double ev = 0.0;
+    for (int s = s0; s < s1; s++) {
+        double v = P.u64[s];
+        const int c0 = P.seq_child[s], c1 = P.seq_child[s + 1];
+        for (int c = c0; c < c1; c++) v += __ldcg(&P.evc64[c]);
+        P.u64[s] = v;   // u is scratch: keep V for the next loops
+        ev += P.b64[s] * v;
+    }
+    P.evc64[j] = ev;
+    double pos = 0.0;
+    for (int s = s0; s < s1; s++) {
+        const double d = P.u64[s] - ev;
+        double r = P.r64[s] + d;
+        if (variant == VAR_PLUS || variant == VAR_PCFR_PLUS) r = r < 0.0 ? 0.0 : r;
+        else if (variant == VAR_DCFR) r = r > 0.0 ? r * ip.fpos : (r < 0.0 ? r * ip.fneg : r);
+        P.r64[s] = r;
+        const double rr = pred ? r + d : r;
+        const double q = rr > 0.0 ? rr : 0.0;
+        P.u64[s] = q;
+        pos += q;
+    }
+    const double uni = 1.0 / (double)(s1 - s0);
+    for (int s = s0; s < s1; s++) P.b64[s] = pos > 0.0 ? P.u64[s] / pos : uni;
+}
+
 // best-response step (MODE_BR, FP64): V = u + sum children, ev = max_a V
 __device__ void up_infoset_br(const DevPlayer &P, int j) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
@@ -340,7 +391,7 @@ __device__ void up_infoset_br(const DevPlayer &P, int j) {
 // best-response pass).  rng: kLvl ints per level.
 template <int MODE>
 __device__ void run_up(const DevPlayer &P, const void *xo, const IterArgs &ia, const ItemParams &ip, int nlvl,
-                       const int32_t *rng, void *stage) {
+                       const int32_t *rng, void *stage, const ItemParams64 *ip64 = nullptr) {
     if (MODE == MODE_CFR)
         spmv_ranges<float, float>(P.m_ptr, P.m_col, P.m_val, (const float *)xo, P.u, rng, nlvl, ia.sign,
                                   (float *)stage);
@@ -352,6 +403,7 @@ __device__ void run_up(const DevPlayer &P, const void *xo, const IterArgs &ia, c
         const int jlo = rng[kLvl * k], jhi = rng[kLvl * k + 1];
         for (int j = jlo + (int)threadIdx.x; j < jhi; j += blockDim.x) {
             if (MODE == MODE_CFR) up_infoset_cfr(P, j, ia.variant, ip);
+            else if (MODE == MODE_CFR64) up_infoset_cfr64(P, j, ia.variant, *ip64);
             else up_infoset_br(P, j);
         }
         __syncthreads();

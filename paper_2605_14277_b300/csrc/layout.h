@@ -118,8 +118,8 @@ struct PlayerLayout {
                                         // sequence); parent / nchild / depth in this tree.  Their
                                         // range records start with the ancestor chain (flags >>
                                         // kAncShift levels, from level 0 down), then their own levels
-    std::vector<int32_t> danc_off;      // [dunits] a unit worked from global memory: offset of its
-                                        // ancestors' x in the scratch area (xanc_size floats)
+    std::vector<int32_t> danc_off;      // [dunits] offset of the unit's ancestors' x in the scratch
+                                        // area that units worked from global memory use (xanc_size)
     int64_t xanc_size = 0;
     std::vector<int32_t> down_queue;    // all top-down units by tree depth, then largest first
     std::vector<int32_t> game_root;     // [G] root unit of each game
