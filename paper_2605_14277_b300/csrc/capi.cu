@@ -253,6 +253,7 @@ struct UpSmem {
     int nwin0, win0_at; // their number and first record
     BulkCmd cmd[kUpArrays * kMaxStagedLevels];   // the producer's staged copies
     int unit[2];        // queue position of the unit in each buffer (n: none)
+    int4 hq[2][2];      // its queue entry (header, tree record), for the consumers
     int armed[2];       // times each buffer's barrier was armed (bulk copies issued)
     int err;
 };
@@ -347,7 +348,11 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             S.nwin0 = (p0 < n && (h0.w & kStaged)) ? unit_nwin(h0) : 0;
             S.win0_at = q0.w;
         }
-        if (tid == 0) S.unit[0] = p0 < n ? p0 : n;
+        if (tid == 0) {
+            S.unit[0] = p0 < n ? p0 : n;
+            S.hq[0][0] = h0;
+            S.hq[0][1] = q0;
+        }
         if (tid == 0 && p0 < n) p1 = fetch();
         p1 = __shfl_sync(0xffffffffu, p1, 0);
         if (tid == 0) pend = p1 < n ? fetch() : n;
@@ -374,8 +379,9 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
     int cur = S.unit[0];
     bool early = false;
     while (cur < n) {
-        const int4 h = P.upq[2 * cur];
-        const int4 q = P.upq[2 * cur + 1];
+        // the unit's queue entry, as the producer kept it
+        const int4 h = S.hq[buf][0];
+        const int4 q = S.hq[buf][1];
         const int u = q.x;
         const int2 tr = make_int2(q.y, q.z);
         const bool staged = (h.w & kStaged) != 0, internal = tr.y > 0, root = tr.x < 0;
@@ -420,7 +426,11 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
                     if (tid == 0) S.armed[buf ^ 1]++;
                 }
             }
-            if (tid == 0) S.unit[buf ^ 1] = nx;
+            if (tid == 0) {
+                S.unit[buf ^ 1] = nx;
+                S.hq[buf ^ 1][0] = S.pre.h;
+                S.hq[buf ^ 1][1] = S.pre.q;
+            }
             __syncwarp();   // S.pre is read: the next one may overwrite it
             if (tid == 0) pend = p < n ? fetch() : n;
             if (p < n) up_prefetch(P, gm, ia, p, hp, qp, S.pre);

@@ -672,8 +672,11 @@ __device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const 
 // levels, the first n_anc of which are its ancestor chain (down to the parents
 // of its top level); level 0 of the chain holds the game's root, whose parent
 // is the empty sequence (x = 1).  Only the unit's own levels are written back.
+constexpr int kSoloInfosets = 64;   // ancestor levels this small are worked by one warp
+
 __device__ void compute_down(const DevPlayer &P, int nl, int n_anc, const SLvl *lv, const DownTab *tab) {
-    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
+    const int tid0 = threadIdx.x - kProducerThreads, nt0 = blockDim.x - kProducerThreads;
+    bool pending = false;   // levels worked by the first consumer warp alone since the last barrier
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
         const DownTab t = tab[k];
@@ -683,6 +686,18 @@ __device__ void compute_down(const DevPlayer &P, int nl, int n_anc, const SLvl *
         const int ni = L.j1 - L.j0;
         const int ps0 = (k > 0) ? lv[k - 1].s0 : 0;
         const float *xpar = sh<const float>((k > 0) ? tab[k - 1].x : t.x);
+        // the ancestor chain is usually a few infosets per level: one warp
+        // works those levels, synchronising only its lanes
+        const bool solo = k < n_anc && ni <= kSoloInfosets;
+        if (!solo && pending) {
+            consumer_sync();
+            pending = false;
+        }
+        if (solo && tid0 >= 32) {
+            pending = true;
+            continue;
+        }
+        const int tid = tid0, nt = solo ? 32 : nt0;
         for (int i = tid; i < ni; i += nt) {
             const int par = ipar[i];
             const float xp = par < 0 ? 1.f : xpar[par - ps0];
@@ -697,8 +712,15 @@ __device__ void compute_down(const DevPlayer &P, int nl, int n_anc, const SLvl *
                     if (q + a < q1) x[q + a] = xp * bb[a];
             }
         }
-        consumer_sync();
+        if (solo) {
+            __syncwarp();
+            pending = true;
+        } else {
+            consumer_sync();
+        }
     }
+    if (pending) consumer_sync();
+    const int tid = tid0, nt = nt0;
     for (int k = n_anc; k < nl; k++) {
         const SLvl L = lv[k];
         const float *x = sh<const float>(tab[k].x);
