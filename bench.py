@@ -101,12 +101,11 @@ def profiled_traffic(kernel_slot):
     return None
 
 
-def graph_length(steps, warmup, cap=64):
+def graph_length(steps, cap=64):
     """Iterations per CUDA graph for the timed run: the largest k <= cap that
-    divides both step counts."""
-    import math
-    g = math.gcd(max(1, steps), max(1, warmup))
-    return max(d for d in range(1, min(cap, g) + 1) if g % d == 0)
+    divides the step count (the timed region is whole replays)."""
+    steps = max(1, steps)
+    return max(d for d in range(1, min(cap, steps) + 1) if steps % d == 0)
 
 
 def alg_bytes(sz):
@@ -184,21 +183,60 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(tree, variant, budget_s=15.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded number of
-    iterations of the same game."""
+def cpu_info():
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return model, n
+
+
+def _oracle_timed(job):
+    """One oracle process: build the game of `job`, run `warm` untimed
+    iterations, then as many timed iterations as fit the budget (at most
+    `cap`).  Returns (node-updates, seconds, iterations)."""
+    name, variant, budget_s, cap, warm = (tuple(job) + (1,))[:5]
     from oracle.oracle import Oracle
+    tree, _ = workload(name)
     o = Oracle(tree)
     t0 = time.perf_counter()
-    o.iterate(1, variant)
-    one = time.perf_counter() - t0
-    n = int(max(1, min(200, budget_s / max(one, 1e-6))))
+    o.iterate(max(1, warm), variant)
+    one = (time.perf_counter() - t0) / max(1, warm)
+    n = int(max(1, min(cap, budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
     o.iterate(n, variant)
     el = time.perf_counter() - t0
-    return {"value": tree.n_nodes * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} {variant} iterations of the full {tree.n_nodes}-node game (after 1 untimed)",
-            "sec_per_iteration": el / n}
+    return tree.n_nodes * n, el, n
+
+
+def cpu_baseline(tree, variant, budget_s=15.0, name="large", cores=None):
+    """The FP64 oracle as it stands on the host's cores: one process per core
+    (spawned), each iterating its own copy of the same game for a bounded
+    time; the aggregate node-updates/s over all of them, and the
+    single-process figure beside it.  The oracle is sequential, so more cores
+    means more independent copies, not a faster single game."""
+    import multiprocessing as mp
+    model, nproc = cpu_info()
+    cores = int(cores or min(nproc, 16))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_timed, [(name, variant, budget_s, 200, 1)] * cores)
+    work = sum(r[0] for r in res)
+    span = max(r[1] for r in res)
+    one = res[0]
+    return {"value": work / span, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, each {min(r[2] for r in res)}-{max(r[2] for r in res)} {variant} "
+                      f"iterations of its own copy of the full {tree.n_nodes}-node game (after 1 untimed)",
+            "single_core": {"value": one[0] / one[1], "unit": UNIT, "sec_per_iteration": one[1] / one[2]},
+            "cpu_model": model, "nproc": nproc}
 
 
 def max_over_ranks(x, dist):
@@ -307,22 +345,27 @@ def run_reference(args):
     if args.workload == "serve":
         return run_reference_serve(args)
     tree, variant = workload(args.workload, args.variant)
-    from oracle.oracle import Oracle
-    o = Oracle(tree)
-    t0 = time.perf_counter()
-    o.iterate(max(1, args.warmup), variant)
-    per = (time.perf_counter() - t0) / max(1, args.warmup)
-    k = int(min(args.steps, max(3, 150.0 / max(per, 1e-9))))
-    t0 = time.perf_counter()
-    o.iterate(k, variant)
-    el = time.perf_counter() - t0
-    value = tree.n_nodes * k / el
-    sample = f"{k} of {args.steps} requested {variant} iterations of the full {tree.n_nodes}-node game"
+    # the oracle is sequential: the host's cores each run their own copy of
+    # the game (spawned processes), and the job's rate is their sum
+    import multiprocessing as mp
+    model, nproc = cpu_info()
+    cores = min(nproc, 16)
+    warm = min(args.warmup, 3)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_timed, [(args.workload, variant, 60.0, args.steps, warm)] * cores)
+    work = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    k = min(r[2] for r in res)
+    value = work / el
+    sample = (f"{cores} processes, each {k}-{max(r[2] for r in res)} of {args.steps} requested {variant} "
+              f"iterations of its own copy of the full {tree.n_nodes}-node game (after {max(1, warm)} untimed)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": workload_config(tree, variant),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "single_core": {"value": res[0][0] / res[0][1], "unit": UNIT},
+                             "cpu_model": model, "nproc": nproc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -345,12 +388,13 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     s = C.Solver(tree, stream=stream)
     sz = s.sizes()
-    # the product path: CUDA graphs of k iterations, k dividing both the
-    # warm-up and the timed step counts (so the warm-up captures the graph the
-    # timed region replays; every k computes the same iterations)
-    k_graph = graph_length(args.steps, args.warmup)
+    # the product path: the timed steps replay CUDA graphs of k iterations,
+    # k = the step count up to 64 (or the largest divisor of it up to 64),
+    # captured before the timed region; every k computes the same iterations
+    k_graph = graph_length(args.steps)
     s.set_graph_iterations(k_graph)
-    s.iterate(args.warmup, variant)   # untimed: graph captured, caches warm
+    s.prepare_graph(variant)
+    s.iterate(args.warmup, variant)   # untimed warm-up (caches, the first replays' set-up)
     s.sync()
     props = torch.cuda.get_device_properties(local)
     gpu_id = local
@@ -414,7 +458,8 @@ def run_ours(args):
                "h2d_bytes_per_step": sz2["h2d_bytes"] / e2e_iters, "d2h_bytes_per_step": d2h / e2e_iters,
                "iterations": e2e_iters, "seconds": el, "exploitability": expl[0],
                "what": "Solver(host tree) + iterate + exploitability + average strategies, wall clock"}
-        cpu = cpu_baseline(tree, variant, budget_s=args.cpu_budget) if (world == 1 and not args.no_cpu) else None
+        cpu = (cpu_baseline(tree, variant, budget_s=args.cpu_budget, name=args.workload)
+               if (world == 1 and not args.no_cpu) else None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -440,11 +485,141 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if not args.no_sub and world == 1:
+            # the batched and served workloads, bounded, in the same run
+            line["batch"] = batch_summary(args, stream)
+            line["serve"] = serve_summary(args, local)
         print(json.dumps(line))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def solve_batch(s, trees, variant, target_rel=1e-3, cap=8192):
+    """Rounds of 64 iterations with solved games masked off, until every game
+    is at or below target_rel of its payoff range (or `cap` iterations).
+    Returns (seconds, iterations per game, final exploitabilities)."""
+    import torch
+    from paper_2605_14277_b300 import serving as SV
+    G_ = len(trees)
+    rng = np.array([SV.payoff_range(t) for t in trees])
+    active = np.ones(G_, np.uint8)
+    its = np.zeros(G_, np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while active.any() and its.max() < cap:
+        s.iterate(64, variant, active=active)
+        its[active.astype(bool)] += 64
+        e = s.exploitability_batch()[0]
+        active &= (e > target_rel * rng).astype(np.uint8)
+    return time.perf_counter() - t0, its, e
+
+
+def batch_summary(args, stream):
+    """The 4096-game batch (CFR+, 64-iteration graphs, the library's launch
+    shape): iteration time and node-updates/s against one launch sequence
+    per game, and solves/s to exploitability <= 1e-3 of the payoff range
+    against solving the games one at a time (on a sample)."""
+    import torch
+    from paper_2605_14277_b300 import cfr as C
+    variant = "cfr+"
+    trees = G.batch_games(args.batch_games)
+    nodes = sum(t.n_nodes for t in trees)
+    s = C.Solver(trees, stream=stream)
+    sizes = [s.sizes(g) for g in range(len(trees))]
+    s.iterate(64, variant)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n_it = 256
+    n0 = s.kernel_launches()
+    e0.record(stream)
+    s.iterate(n_it, variant)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n_it
+    launches = (s.kernel_launches() - n0) / n_it
+    s.close()
+    hbm, _ = peaks()
+    iter_bytes = batch_alg_bytes(sizes)
+    # one context per game, the same 64 iterations, on a sample
+    sample = trees[:: max(1, len(trees) // 64)][:64]
+    solos = [C.Solver(t, stream=stream) for t in sample]
+    for x in solos:
+        x.iterate(64, variant)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for x in solos:
+        x.iterate(64, variant)
+    e1.record(stream)
+    e1.synchronize()
+    solo_rate = sum(t.n_nodes for t in sample) * 64 / (e0.elapsed_time(e1) * 1e-3)
+    for x in solos:
+        x.close()
+    # solves: the whole batch in one context, against a sample one at a time
+    s = C.Solver(trees, stream=stream)
+    sec, its, e = solve_batch(s, trees, variant)
+    s.close()
+    one_sec = 0.0
+    one_its = []
+    for t in sample[:32]:
+        x = C.Solver(t, stream=stream)
+        sec1, it1, _ = solve_batch(x, [t], variant)
+        one_sec += sec1
+        one_its.append(int(it1[0]))
+        x.close()
+    return {"workload": f"{len(trees)} random games, nodes log-uniform in [1e2, 1e5], CFR+", "nodes": nodes,
+            "us_per_iteration": ms * 1e3, "node_updates_per_s": nodes / (ms * 1e-3),
+            "roofline_frac_of_measured_hbm": iter_bytes / (ms * 1e-3) / 1e9 / hbm,
+            "alg_bytes_per_iteration": iter_bytes, "gpu_launches_per_iteration": launches,
+            "per_game_launches_node_updates_per_s": solo_rate,
+            "batched_over_per_game": nodes / (ms * 1e-3) / solo_rate,
+            "solves_per_s": len(trees) / sec, "solve_seconds": sec, "solved": int((its < 8192).sum()),
+            "iterations_to_target": {"median": float(np.median(its)), "max": int(its.max())},
+            "one_at_a_time_solves_per_s": len(one_its) / one_sec,
+            "one_at_a_time_sample": f"{len(one_its)} of the games, each alone in rounds of 64",
+            "solves_batched_over_one_at_a_time": (len(trees) / sec) / (len(one_its) / one_sec),
+            "target": "exploitability <= 1e-3 of the payoff range"}
+
+
+def serve_workload(args, local, n, seed0=500000):
+    """Poisson arrivals of subgame-solve requests through the continuous
+    batching server; returns (server stats, one-at-a-time stats, nodes)."""
+    import torch
+    from paper_2605_14277_b300 import cfr as C
+    from paper_2605_14277_b300 import serving as SV
+    arrivals = G.poisson_arrivals(seed0, args.serve_rate, n)
+    trees = [G.serving_request(seed0 + 1 + k) for k in range(n)]
+    factory = lambda ts, st: C.Solver(ts, stream=st)   # noqa: E731
+    # warm-up: one small cohort through the whole path (library load, graphs)
+    warm = SV.make_requests(trees[:4], [0.0] * 4)
+    SV.Server(factory, stream_factory=torch.cuda.Stream, max_iterations=256).run(warm)
+    reqs = SV.make_requests(trees, arrivals)
+    # every loader thread started, with its device set, before the server runs
+    with SV.loader_pool(args.serve_loaders, initializer=torch.cuda.set_device, initargs=(local,)) as pool:
+        srv = SV.Server(factory, hbm_budget=args.serve_budget_gb * 1e9, round_iters=64, variant="dcfr",
+                        target_rel=1e-3, max_cohort_nodes=args.serve_cohort_nodes,
+                        stream_factory=torch.cuda.Stream, loader=pool.submit)
+        st = srv.run(reqs, time_limit=args.serve_time_limit)
+    base_n = min(n, args.serve_baseline)
+    base = SV.make_requests(trees[:base_n], arrivals[:base_n])
+    bst = SV.serve_one_at_a_time(factory, base, round_iters=64, variant="dcfr", target_rel=1e-3,
+                                 time_limit=args.serve_time_limit)
+    return st, bst, sum(t.n_nodes for t in trees)
+
+
+def serve_summary(args, local):
+    n = max(1, int(round(args.serve_rate * args.serve_sub_seconds)))
+    st, bst, nodes = serve_workload(args, local, n)
+    return {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s, nodes log-uniform in [1e3, 1e6], "
+                        f"DCFR to exploitability <= 1e-3 of the payoff range", "nodes": nodes,
+            "solves_per_s": st["solves_per_s"], "p50_latency_s": st["p50_latency_s"],
+            "p99_latency_s": st["p99_latency_s"], "completed": st["completed"], "cohorts": st["cohorts"],
+            "moved_games": st["moved_games"], "peak_bytes": st["peak_bytes"],
+            "one_at_a_time": {"requests": bst["requests"], "completed": bst["completed"],
+                              "solves_per_s": bst["solves_per_s"]},
+            "served_over_one_at_a_time": st["solves_per_s"] / max(bst["solves_per_s"], 1e-12)}
 
 
 def gpu_uuid(local):
@@ -567,9 +742,8 @@ def run_batch(args):
                        "launches_per_player": 1 if tuned["passes"] == 1 else 2,
                        "shape_info": C.shapes()[tuned["shape"]],
                        "l2": f"inputs larger than L2: {iter_bytes / 2**20:.0f} MiB streamed per iteration vs 126 MiB L2",
-                       "parallelism": f"replicas x{world}",
-                       "cuda_graph_iterations": k_graph},
-            "gpu_launches": (2 if tuned["passes"] == 1 else 4) * args.steps + (args.steps + 63) // 64,
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": n_launch,
             "roofline": {"bound": "hbm", "achieved": iter_bytes / (ms / args.steps * 1e-3) / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": iter_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm, "traffic": None,
                          "kernel": "whole iteration (every pass launch)", "alg_bytes_per_iteration": iter_bytes,
@@ -590,42 +764,20 @@ def run_batch(args):
 
 def run_serve(args):
     """Subgame-solve requests (nodes log-uniform in [1e3, 1e6], N(0,1)
-    payoffs) arriving as a Poisson process, admitted under a 120 GB budget in
-    cohorts and solved by DCFR to exploitability <= 1e-3 of the payoff range;
-    against the one-at-a-time loop on a sample."""
+    payoffs) arriving as a Poisson process, served with continuous batching
+    under a 120 GB budget and solved by DCFR to exploitability <= 1e-3 of the
+    payoff range; against the one-at-a-time loop on a sample."""
     import torch
     world, rank, local = dist_setup()
     if not torch.cuda.is_available():
         print(json.dumps({"error": "no CUDA device"}))
         return 1
     torch.cuda.set_device(local)
-    from paper_2605_14277_b300 import cfr as C
-    from paper_2605_14277_b300 import serving as SV
-
     n = max(1, int(round(args.serve_rate * args.serve_seconds)))
-    seed0 = 500000 + rank * 100000
-    arrivals = G.poisson_arrivals(seed0, args.serve_rate, n)
-    trees = [G.serving_request(seed0 + 1 + k) for k in range(n)]
-    factory = lambda ts, st: C.Solver(ts, stream=st)   # noqa: E731
-    # warm-up: one small cohort through the whole path (library load, graphs)
-    warm = SV.make_requests(trees[:4], [0.0] * 4)
-    SV.Server(factory, stream_factory=torch.cuda.Stream, max_iterations=256).run(warm)
-    reqs = SV.make_requests(trees, arrivals)
     sampler = ClockSampler(gpu_uuid(local))
     sampler.start()
-    # every loader thread started, with its device set, before the server runs
-    with SV.loader_pool(args.serve_loaders, initializer=torch.cuda.set_device, initargs=(local,)) as pool:
-        srv = SV.Server(factory, hbm_budget=args.serve_budget_gb * 1e9, round_iters=64, variant="dcfr",
-                        target_rel=1e-3, max_cohort_nodes=args.serve_cohort_nodes,
-                        stream_factory=torch.cuda.Stream, loader=pool.submit)
-        st = srv.run(reqs, time_limit=args.serve_time_limit)
+    st, bst, nodes = serve_workload(args, local, n, seed0=500000 + rank * 100000)
     clocks = sampler.stop()
-    # one request at a time, on the first requests (bounded)
-    base_n = min(n, args.serve_baseline)
-    base = SV.make_requests(trees[:base_n], arrivals[:base_n])
-    bst = SV.serve_one_at_a_time(factory, base, round_iters=64, variant="dcfr", target_rel=1e-3,
-                                 time_limit=args.serve_time_limit)
-    nodes = sum(t.n_nodes for t in trees)
     if rank == 0:
         line = {
             "metric": "solves/s at exploitability <= 1e-3 of the payoff range (serving, Poisson arrivals)",
@@ -640,7 +792,7 @@ def run_serve(args):
             "latency": {"p50_s": st["p50_latency_s"], "p99_s": st["p99_latency_s"]},
             "serving": st,
             "node_updates_per_s": st["node_iterations"] / max(st["elapsed_s"], 1e-9),
-            "one_at_a_time": {"requests": base_n, "solves_per_s": bst["solves_per_s"],
+            "one_at_a_time": {"requests": bst["requests"], "solves_per_s": bst["solves_per_s"],
                               "p50_s": bst["p50_latency_s"], "p99_s": bst["p99_latency_s"],
                               "completed": bst["completed"]},
             "clocks": clocks,
@@ -681,7 +833,11 @@ def main():
     ap.add_argument("--variant", default=None, choices=["cfr", "cfr+", "dcfr", "pcfr+", "pcfr"],
                     help="regret minimiser for the single-game workloads (default: the workload's own)")
     ap.add_argument("--serve-rate", type=float, default=1000.0)
-    ap.add_argument("--serve-seconds", type=float, default=0.25)
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-sub-seconds", type=float, default=1.0,
+                    help="arrival window of the serving summary in the default line (rate x seconds requests)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="leave the batched and served summaries out of the default line")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-time-limit", type=float, default=120.0)
     ap.add_argument("--serve-baseline", type=int, default=16)

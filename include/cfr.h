@@ -172,6 +172,13 @@ int cfr_set_update_mode(cfr_ctx *ctx, int mode);
 /* Number of iterations captured per CUDA graph replay (1..4096, default 64). */
 int cfr_set_graph_iterations(cfr_ctx *ctx, int k);
 
+/* Capture and instantiate now the CUDA graph that cfr_iterate replays for
+ * this variant and these parameters at the context's graph length (and
+ * update schedule), without running it, so that the first cfr_iterate of at
+ * least that many iterations only replays it.  Nothing is computed and no
+ * state changes. */
+int cfr_prepare_graph(cfr_ctx *ctx, cfr_variant v, double alpha, double beta, double gamma);
+
 /* Sizes of game g: out[0..9] = S1, S2 (non-empty sequences), J1, J2
  * (infosets), nnz of the payoff matrix, game-tree nodes, completed
  * iterations, number of games in the context, device bytes the context holds,
@@ -218,6 +225,30 @@ int cfr_exploitability_batch(cfr_ctx *ctx, double *host_expl, double *host_br1, 
  *     array, so calls whose work overlaps on the GPU (different streams or
  *     contexts) race; calls on one stream are ordered. */
 int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl);
+
+/* Exploitability of every game, as cfr_exploitability_batch, written to a
+ * caller-owned DEVICE buffer of n_games doubles and left asynchronous on the
+ * context's stream (valid once the stream has reached this point: record an
+ * event, or call cfr_sync).  The scratch is the context's own, so calls on
+ * different contexts and streams may overlap.  A game whose best-response
+ * pass gave up on a bounded wait reads as NaN; the status comes with the
+ * next synchronising call.  For serving loops that keep many contexts busy
+ * without waiting on any one of them. */
+int cfr_exploitability_async(cfr_ctx *ctx, double *dev_expl);
+
+/* Copy the state of n games (cumulative regrets, next strategy, average sums
+ * and iteration counter; either precision, bit for bit) from context src into
+ * context dst, game host_src_games[k] of src into game host_dst_games[k] of
+ * dst; the two must be the same game (checked through its sequence,
+ * infoset, node and payoff counts).  dst's sequence-form strategies are
+ * rebuilt from the copied behavioural ones.  The copy follows the work
+ * already issued on src's stream; the call returns once it is complete, so
+ * src may be freed right after.  Both contexts must be on one device and
+ * have the same precision.  For serving: the unfinished games of a batch are
+ * moved, with new requests, into a new context, and the old one's memory is
+ * released (the iteration continues exactly as it would have). */
+int cfr_copy_game_states(cfr_ctx *dst, int64_t n, const int64_t *host_dst_games, cfr_ctx *src,
+                         const int64_t *host_src_games);
 
 /* Checkpoint / resume of game g, player p: cumulative regrets r (S_p), the
  * behavioural strategy to be played next b (S_p), the average sums xbar

@@ -62,6 +62,7 @@ def lib():
         L.cfr_iterate_batch.argtypes = [P, i64, i, d, d, d, P]
         L.cfr_set_update_mode.argtypes = [P, i]
         L.cfr_set_graph_iterations.argtypes = [P, i]
+        L.cfr_prepare_graph.argtypes = [P, i, d, d, d]
         L.cfr_sizes.argtypes = [P, i64, P]
         L.cfr_get_average_strategy.argtypes = [P, i64, i, P, i64]
         L.cfr_exploitability.argtypes = [P, P, P, P]
@@ -71,6 +72,8 @@ def lib():
         L.cfr_get_values.argtypes = [P, i64, i, P, P]
         L.cfr_profile_iterations.argtypes = [P, i64, i, d, d, d, P]
         L.cfr_exploitability_batch_noalloc.argtypes = [P, P]
+        L.cfr_exploitability_async.argtypes = [P, P]
+        L.cfr_copy_game_states.argtypes = [P, i64, P, P, P]
         L.cfr_sync.argtypes = [P]
         L.cfr_kernel_launches.argtypes = [P, P]
         L.cfr_free.argtypes = [P]
@@ -145,6 +148,21 @@ def _resolve(variant, alpha, beta, gamma):
     return v, (a0 if alpha is None else alpha), (b0 if beta is None else beta), (g0 if gamma is None else gamma)
 
 
+class _Round:
+    """A round queued by Solver.start_round."""
+
+    def __init__(self, solver, event):
+        self._s, self._ev = solver, event
+
+    def done(self) -> bool:
+        return bool(self._ev.query())
+
+    def result(self):
+        self._ev.synchronize()
+        self._s.sync()   # a bounded device wait that gave up is reported here
+        return self._s._host_expl.numpy().copy()
+
+
 class Solver:
     """CFR state of one game or of a batch of games resident on the GPU.
 
@@ -169,6 +187,8 @@ class Solver:
         _check(L.cfr_load_batch_opts(descs, len(trees), _stream_handle(stream), ctypes.byref(opts), ctypes.byref(h)),
                "cfr_load_batch_opts")
         self.shape, self.flat, self.passes = int(shape), bool(flat), int(passes)
+        self._torch_stream = stream if (stream is not None and not isinstance(stream, int)) else None
+        self._dev_expl = self._host_expl = None
         self._h = h
         self.n_games = len(trees)
         self.batch = batch
@@ -198,6 +218,11 @@ class Solver:
 
     def set_graph_iterations(self, k: int):
         _check(lib().cfr_set_graph_iterations(self._h, int(k)), "cfr_set_graph_iterations")
+
+    def prepare_graph(self, variant="cfr", alpha=None, beta=None, gamma=None):
+        """Capture now the CUDA graph iterate() will replay (nothing runs)."""
+        v, a, b, g = _resolve(variant, alpha, beta, gamma)
+        _check(lib().cfr_prepare_graph(self._h, v, a, b, g), "cfr_prepare_graph")
 
     def iterate(self, n: int, variant="cfr", alpha=None, beta=None, gamma=None, active=None):
         v, a, b, g = _resolve(variant, alpha, beta, gamma)
@@ -242,6 +267,40 @@ class Solver:
         without any allocation; asynchronous on the solver's stream."""
         _check(lib().cfr_exploitability_batch_noalloc(self._h, ctypes.c_void_p(int(dev_ptr))),
                "cfr_exploitability_batch_noalloc")
+
+    def exploitability_async(self, dev_ptr: int):
+        """Exploitability of every game into a caller-owned device buffer of
+        n_games doubles (a device address), asynchronous on the solver's
+        stream; the solver's own scratch, so solvers may overlap."""
+        _check(lib().cfr_exploitability_async(self._h, ctypes.c_void_p(int(dev_ptr))), "cfr_exploitability_async")
+
+    def start_round(self, n: int, variant="cfr", active=None, alpha=None, beta=None, gamma=None):
+        """n iterations, then the exploitability of every game, all queued on
+        the solver's stream without waiting; returns a handle whose done()
+        polls and whose result() returns the exploitabilities (and reports a
+        device timeout).  Needs a torch stream at construction."""
+        import torch
+        if self._torch_stream is None:
+            raise ValueError("start_round needs Solver(..., stream=torch.cuda.Stream())")
+        if self._dev_expl is None:
+            self._dev_expl = torch.empty(self.n_games, dtype=torch.float64, device=self._torch_stream.device)
+            self._host_expl = torch.empty(self.n_games, dtype=torch.float64, pin_memory=True)
+        self.iterate(n, variant, alpha=alpha, beta=beta, gamma=gamma, active=active)
+        self.exploitability_async(self._dev_expl.data_ptr())
+        with torch.cuda.stream(self._torch_stream):
+            self._host_expl.copy_(self._dev_expl, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self._torch_stream)
+        return _Round(self, ev)
+
+    def copy_states_from(self, src: "Solver", dst_games, src_games):
+        """Take the state of games src_games of `src` (same games) into games
+        dst_games of this solver, exactly; returns once the copy is done."""
+        d = np.ascontiguousarray(dst_games, dtype=np.int64)
+        s_ = np.ascontiguousarray(src_games, dtype=np.int64)
+        if d.shape != s_.shape:
+            raise ValueError("game lists must have the same length")
+        _check(lib().cfr_copy_game_states(self._h, d.shape[0], _ptr(d), src._h, _ptr(s_)), "cfr_copy_game_states")
 
     def average_strategy(self, player: int, game: int = 0):
         S = self._game_sizes(game)["S1" if player == 1 else "S2"]

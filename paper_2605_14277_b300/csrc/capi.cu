@@ -821,6 +821,32 @@ __global__ void k_average(DevPlayer P, const int32_t *ext_inf, const int32_t *ex
 
 __global__ void k_set_t(int32_t *t_done, int g, int32_t t) { t_done[g] = t; }
 
+// One game's state (r, b, xbar, in either precision) from another context
+// holding the same game, infoset by infoset in caller order; x is rebuilt
+// afterwards.
+__global__ void k_copy_game(DevPlayer D, const int32_t *dext, int gd, DevPlayer S, const int32_t *sext, int gs, int Jg) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        if (D.fp64) D.xbar64[gd] = S.xbar64[gs];
+        else D.xbar[gd] = S.xbar[gs];
+    }
+    if (k >= Jg) return;
+    const int jd = dext[k], js = sext[k];
+    const int d0 = D.inf_seq[jd], s0 = S.inf_seq[js], na = S.inf_seq[js + 1] - s0;
+    for (int a = 0; a < na; a++) {
+        if (D.fp64) {
+            D.r64[d0 + a] = S.r64[s0 + a];
+            D.b64[d0 + a] = S.b64[s0 + a];
+            D.xbar64[d0 + a] = S.xbar64[s0 + a];
+        } else {
+            D.r[d0 + a] = S.r[s0 + a];
+            D.b[d0 + a] = S.b[s0 + a];
+            D.xbar[d0 + a] = S.xbar[s0 + a];
+        }
+    }
+}
+__global__ void k_copy_t(int32_t *dt, int gd, const int32_t *st, int gs) { dt[gd] = st[gs]; }
+
 // current sequence-form strategy (empty sequence first) and per-infoset ev of
 // one game in caller order (FP64)
 __global__ void k_get_values(DevPlayer P, const int32_t *ext_inf, const int32_t *ext_seq0, int g, int Jg,
@@ -1017,9 +1043,12 @@ int launch_params(cfr_ctx *c, int variant, double alpha, double beta, double gam
     return CFR_OK;
 }
 
-// x of player p from the current b (top-down, no averaging)
+// x of player p from the current b (top-down, no averaging), for every game
+// whatever the active mask
 int launch_rebuild_x(cfr_ctx *c, int p) {
     PlayerBuf &B = c->pl[p];
+    const bool masked = std::find(c->active_host.begin(), c->active_host.end(), 0) != c->active_host.end();
+    if (masked) CU(cudaMemsetAsync(c->active, 1, c->G, c->stream));
     TRY(launch_params(c, 0, 0.0, 0.0, 0.0));
     IterArgs ia{};
     ia.average = 0;
@@ -1029,6 +1058,7 @@ int launch_rebuild_x(cfr_ctx *c, int p) {
         kConfigs[c->cfg].down<<<B.grid_down, c->threads, c->smem_staged, c->stream>>>(B.d, dev_games(c), ia,
                                                                                        c->item_bytes);
     CU(cudaGetLastError());
+    if (masked) CU(cudaMemcpyAsync(c->active, c->active_keep, c->G, cudaMemcpyDeviceToDevice, c->stream));
     return CFR_OK;
 }
 
@@ -1432,6 +1462,39 @@ int check_err(cfr_ctx *c) {
     return CFR_OK;
 }
 
+// The CUDA graph of K = key.k iterations for key's variant and parameters:
+// captured and instantiated on first use, then kept by the context.
+int graph_for(cfr_ctx *c, const GraphKey &key, bool alt, cudaGraphExec_t *out) {
+    auto f = c->graphs.find(key);
+    if (f != c->graphs.end()) {
+        *out = f->second;
+        return CFR_OK;
+    }
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = CFR_OK;
+    int64_t nk = 0;
+    for (int k = 0; k < key.k && rc == CFR_OK; k++)
+        rc = launch_iteration(c, key.variant, key.a, key.b, key.g, alt, k, &nk);
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ee != cudaSuccess) return set_err(CFR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+    ee = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ee != cudaSuccess) return set_err(CFR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
+    c->graphs[key] = exec;
+    c->graph_kernels[key] = nk;
+    *out = exec;
+    return CFR_OK;
+}
+
+bool default_alternating(int variant);
+
 int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, double gamma) {
     if (!c) return set_err(CFR_ERR_ARG, "ctx is NULL");
     if (c->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
@@ -1445,31 +1508,8 @@ int iterate(cfr_ctx *c, int64_t n, int variant, double alpha, double beta, doubl
     int64_t done = 0;
     if (n >= K) {
         GraphKey key{variant, alt ? 2 : 1, K, alpha, beta, gamma};
-        auto f = c->graphs.find(key);
         cudaGraphExec_t exec = nullptr;
-        if (f == c->graphs.end()) {
-            std::lock_guard<std::recursive_mutex> setup(setup_mutex());
-            cudaGraph_t graph = nullptr;
-            CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            int rc = CFR_OK;
-            int64_t nk = 0;
-            for (int k = 0; k < K && rc == CFR_OK; k++)
-                rc = launch_iteration(c, variant, alpha, beta, gamma, alt, k, &nk);
-            cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
-            if (rc) {
-                if (graph) cudaGraphDestroy(graph);
-                return rc;
-            }
-            if (ee != cudaSuccess) return set_err(CFR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
-            ee = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ee != cudaSuccess)
-                return set_err(CFR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
-            c->graphs[key] = exec;
-            c->graph_kernels[key] = nk;
-        } else {
-            exec = f->second;
-        }
+        TRY(graph_for(c, key, alt, &exec));
         const int64_t nk = c->graph_kernels[key];
         for (; done + K <= n; done += K) {
             CU(cudaGraphLaunch(exec, c->stream));
@@ -1576,6 +1616,84 @@ int cfr_exploitability_batch_noalloc(cfr_ctx *ctx, double *dev_expl) {
     return CFR_OK;
 }
 
+int cfr_exploitability_async(cfr_ctx *ctx, double *dev_expl) {
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (!dev_expl) return set_err(CFR_ERR_ARG, "dev_expl is NULL");
+    if (ctx->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != ctx->device) return set_err(CFR_ERR_ARG, "the context's device must be current");
+    double *br1 = ctx->br[0], *br2 = ctx->br[1];
+    // a game whose best-response pass did not finish reads as NaN
+    CU(cudaMemsetAsync(br1, 0xFF, ctx->G * sizeof(double), ctx->stream));
+    CU(cudaMemsetAsync(br2, 0xFF, ctx->G * sizeof(double), ctx->stream));
+    const bool masked = std::find(ctx->active_host.begin(), ctx->active_host.end(), 0) != ctx->active_host.end();
+    if (masked) CU(cudaMemsetAsync(ctx->active, 1, ctx->G, ctx->stream));
+    DevGames gm{ctx->t_done, ctx->active, nullptr};
+    IterArgs ia{};
+    for (int p = 0; p < 2; p++) {
+        PlayerBuf &B = ctx->pl[p];
+        k_normalize<<<(unsigned)std::min<int64_t>((B.S + kThreads - 1) / kThreads, 65535), kThreads, 0,
+                      ctx->stream>>>(B.d, B.S);
+    }
+    for (int p = 0; p < 2; p++) {
+        PlayerBuf &B = ctx->pl[p];
+        gm.br = p == 0 ? br1 : br2;
+        ia.sign = p == 0 ? 1.f : -1.f;
+        k_up<MODE_BR><<<B.grid_up_br, kThreads, B.smem_br, ctx->stream>>>(B.d, gm, ctx->pl[1 - p].d.xnorm, ia);
+    }
+    k_expl_combine<<<(unsigned)std::min<int64_t>((ctx->G + 255) / 256, 65535), 256, 0, ctx->stream>>>(br1, br2,
+                                                                                                    ctx->G, dev_expl);
+    CU(cudaGetLastError());
+    if (masked) CU(cudaMemcpyAsync(ctx->active, ctx->active_keep, ctx->G, cudaMemcpyDeviceToDevice, ctx->stream));
+    return CFR_OK;
+}
+
+int cfr_copy_game_states(cfr_ctx *dst, int64_t n, const int64_t *host_dst_games, cfr_ctx *src,
+                         const int64_t *host_src_games) {
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
+    if (!dst || !src || (n > 0 && (!host_dst_games || !host_src_games)))
+        return set_err(CFR_ERR_ARG, "NULL context or game list");
+    if (n < 0) return set_err(CFR_ERR_ARG, "negative game count");
+    if (dst->poisoned || src->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    if (dst == src) return set_err(CFR_ERR_ARG, "source and destination must differ");
+    if (dst->device != src->device) return set_err(CFR_ERR_ARG, "both contexts must be on one device");
+    if (dst->fp64 != src->fp64) return set_err(CFR_ERR_ARG, "both contexts must have the same precision");
+    for (int64_t k = 0; k < n; k++) {
+        const int64_t gd = host_dst_games[k], gs = host_src_games[k];
+        if (gd < 0 || gd >= dst->G || gs < 0 || gs >= src->G) return set_err(CFR_ERR_ARG, "game index out of range");
+        for (int p = 0; p < 2; p++)
+            if (dst->pl[p].game_S[gd] != src->pl[p].game_S[gs] || dst->pl[p].game_J[gd] != src->pl[p].game_J[gs])
+                return set_err(CFR_ERR_ARG, "games differ in their sequence or infoset counts");
+        if (dst->game_nodes[gd] != src->game_nodes[gs] || dst->game_nnz[gd] != src->game_nnz[gs])
+            return set_err(CFR_ERR_ARG, "games differ in their node or payoff counts");
+    }
+    if (n == 0) return CFR_OK;
+    // the source's work so far comes first
+    cudaEvent_t ev = nullptr;
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, src->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
+    cudaEventDestroy(ev);
+    CU(e);
+    for (int64_t k = 0; k < n; k++) {
+        const int64_t gd = host_dst_games[k], gs = host_src_games[k];
+        for (int p = 0; p < 2; p++) {
+            PlayerBuf &D = dst->pl[p], &S = src->pl[p];
+            const int Jg = D.game_J[gd];
+            k_copy_game<<<(Jg + kThreads) / kThreads, kThreads, 0, dst->stream>>>(
+                D.d, D.ext_inf + D.game_jbase[gd], (int)gd, S.d, S.ext_inf + S.game_jbase[gs], (int)gs, Jg);
+        }
+        k_copy_t<<<1, 1, 0, dst->stream>>>(dst->t_done, (int)gd, src->t_done, (int)gs);
+    }
+    CU(cudaGetLastError());
+    for (int p = 0; p < 2; p++) TRY(launch_rebuild_x(dst, p));
+    // the source may be freed once this returns
+    CU(cudaStreamSynchronize(dst->stream));
+    return check_err(dst);
+}
+
 int cfr_load_tree(const cfr_tree_desc *tree, void *cuda_stream, cfr_ctx **out) {
     return load(tree, 1, cuda_stream, nullptr, out);
 }
@@ -1632,6 +1750,20 @@ int cfr_iterate_batch(cfr_ctx *ctx, int64_t n, cfr_variant v, double alpha, doub
         CU(cudaMemcpyAsync(ctx->active_keep, ctx->active, ctx->G, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     return iterate(ctx, n, (int)v, alpha, beta, gamma);
+}
+
+int cfr_prepare_graph(cfr_ctx *ctx, cfr_variant v, double alpha, double beta, double gamma) {
+    std::lock_guard<std::recursive_mutex> setup(setup_mutex());
+    if (!ctx) return set_err(CFR_ERR_ARG, "ctx is NULL");
+    if (ctx->poisoned) return set_err(CFR_ERR_STATE, "context unusable after an earlier device timeout");
+    if ((int)v < 0 || (int)v > 4) return set_err(CFR_ERR_ARG, "unknown variant");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(gamma))
+        return set_err(CFR_ERR_ARG, "alpha, beta, gamma must be finite");
+    const bool alt = ctx->update_mode == CFR_UPDATES_DEFAULT ? default_alternating((int)v)
+                                                             : ctx->update_mode == CFR_UPDATES_ALTERNATING;
+    GraphKey key{(int)v, alt ? 2 : 1, ctx->graph_k, alpha, beta, gamma};
+    cudaGraphExec_t exec = nullptr;
+    return graph_for(ctx, key, alt, &exec);
 }
 
 int cfr_set_update_mode(cfr_ctx *ctx, int mode) {

@@ -1,18 +1,23 @@
-"""Serving loop: subgame-solve requests admitted under an HBM budget and
-iterated until each meets its exploitability target.
+"""Serving loop with continuous batching: subgame-solve requests admitted
+as memory frees up and iterated until each meets its exploitability target.
 
 Requests arrive over time (each a game tree).  The loop:
 
-* admits the requests that have arrived, as one *cohort* (one batched
-  context on its own CUDA stream), while the cohort's estimated device bytes
-  fit the remaining budget;
-* advances every live cohort by a round of K iterations, with the games that
-  are already solved masked off;
-* after each round reads the FP64 exploitability of every game of the cohort
-  and completes the games at or below ``target_rel`` x (max payoff - min
-  payoff), recording completion time - arrival time as the request's latency;
-* frees a cohort once all its games are done, returning its bytes to the
-  budget.
+* admits the requests that have arrived into a new *cohort* (one batched
+  context on its own CUDA stream) while their estimated device bytes fit the
+  budget, compiling and uploading it on a loader thread;
+* runs every live cohort in rounds of K iterations with its solved games
+  masked off; a round queues the iterations and the FP64 exploitability of
+  every game on the cohort's stream, and the loop polls each round's event,
+  so cohorts never wait for one another;
+* completes a game at or below ``target_rel`` x (max payoff - min payoff),
+  recording completion - arrival as the request's latency;
+* returns memory as games finish, not as cohorts finish: the unfinished
+  games of a cohort that is mostly solved join the next new cohort, their
+  state moved exactly between contexts (``copy_states_from``) at a round
+  boundary, and the old context is freed.  A game's iterations are the same
+  alone, in a cohort or moved between cohorts (every launch computes each
+  game as it would alone).
 
 Every CFR step runs in the library (through ``cfr.Solver``); this module is
 host-side scheduling only.  ``solver_factory`` lets the tests drive the loop
@@ -37,6 +42,8 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     iterations: int = 0
+    exploitability: float = float("nan")   # at completion
+    moves: int = 0                          # times moved to a new cohort
 
     @property
     def latency(self) -> float:
@@ -56,28 +63,35 @@ def make_requests(trees, arrivals) -> List[Request]:
 
 
 class Cohort:
-    def __init__(self, reqs: List[Request], solver, est_bytes: int):
+    def __init__(self, reqs: List[Request], est_bytes: float):
         self.reqs = reqs
-        self.solver = solver
+        self.solver = None
         self.active = np.ones(len(reqs), dtype=np.uint8)
         self.bytes = est_bytes
-        self.iterations = 0
+        self.round = None          # the round in flight (start_round's handle)
+        self.moving_to = None      # the cohort its unfinished games move into
+        self.sources = []          # cohorts whose unfinished games move into this one: (cohort, [(dst, src)])
+        self.started = False
 
     @property
     def finished(self) -> bool:
         return not self.active.any()
 
+    def live_nodes(self) -> int:
+        return sum(r.nodes for r, a in zip(self.reqs, self.active) if a)
+
 
 class Server:
     """`solver_factory(trees, stream)` returns an object with the Solver
-    methods iterate(n, variant, active=mask), exploitability_batch(), sizes()
-    and close().  `stream_factory()` returns a stream per cohort (or None)."""
+    methods start_round(n, variant, active=mask) (a handle with done() and
+    result()), copy_states_from(src, dst_games, src_games), sizes() and
+    close().  `stream_factory()` returns a stream per cohort."""
 
     def __init__(self, solver_factory: Callable, hbm_budget: float = 120e9, round_iters: int = 64,
                  variant: str = "dcfr", target_rel: float = 1e-3, bytes_per_node: float = 90.0,
                  max_cohort: int = 4096, max_cohort_nodes: float = 4e6, stream_factory: Optional[Callable] = None,
                  clock: Callable[[], float] = time.perf_counter, max_iterations: int = 100000,
-                 loader: Optional[Callable] = None):
+                 loader: Optional[Callable] = None, repack_live: float = 0.5, on_complete: Optional[Callable] = None):
         self.factory = solver_factory
         self.budget = float(hbm_budget)
         self.round_iters = int(round_iters)
@@ -95,29 +109,26 @@ class Server:
         self.loader = loader
         self.clock = clock
         self.max_iterations = int(max_iterations)
+        # a cohort whose unfinished games hold less than this fraction of its
+        # nodes moves them into the next new cohort
+        self.repack_live = float(repack_live)
+        # on_complete(request, solver, game index): called as a game completes
+        self.on_complete = on_complete
         self.cohorts: List[Cohort] = []
         self.in_use = 0.0
         self.peak_in_use = 0.0
         self.n_cohorts = 0
+        self.n_moves = 0
         self.rejected: List[Request] = []
-
-    def _wait_until(self, t0: float, t: float):
-        while True:
-            left = t - (self.clock() - t0)
-            if left <= 0:
-                return
-            if self.clock is time.perf_counter:
-                time.sleep(min(left, 1e-3))
 
     def estimate(self, req: Request) -> float:
         return req.nodes * self.bytes_per_node
 
-    def _admit(self, pending: List[Request], now: float) -> List[Request]:
-        """Take arrived requests, in arrival order, while they fit the budget.
-        A request larger than the whole budget can never be admitted: it is
+    def _admit(self, pending: List[Request], now: float, room: float) -> List[Request]:
+        """Take arrived requests, in arrival order, while they fit `room`.  A
+        request larger than the whole budget can never be admitted: it is
         rejected (done stays negative, counted in the stats)."""
         take = []
-        room = self.budget - self.in_use
         nodes = 0
         while pending and pending[0].arrival <= now and len(take) < self.max_cohort:
             need = self.estimate(pending[0])
@@ -131,17 +142,51 @@ class Server:
             take.append(pending.pop(0))
         return take
 
-    def _complete(self, c: Cohort, expl: np.ndarray, now: float):
-        for k, r in enumerate(c.reqs):
-            if not c.active[k]:
+    def _sparse(self) -> List[Cohort]:
+        """Running cohorts whose unfinished games are worth moving."""
+        out = []
+        for c in self.cohorts:
+            if c.moving_to is not None or not c.started or c.finished:
                 continue
-            r.iterations = c.iterations
-            if expl[k] <= self.target_rel * r.payoff_range or c.iterations >= self.max_iterations:
-                c.active[k] = 0
-                r.done = now
+            total = sum(r.nodes for r in c.reqs)
+            if c.live_nodes() < self.repack_live * total:
+                out.append(c)
+        return out
 
-    def _start(self, c: Cohort, t0: float):
-        """A loaded cohort joins the rounds; its bytes are re-counted from what
+    def _form(self, pending: List[Request], now: float, t0: float, loading: list) -> bool:
+        """Form one new cohort from arrived requests and the unfinished games
+        of sparse cohorts; returns False when there is nothing to form."""
+        sparse = self._sparse()
+        movers = [(c, k) for c in sparse for k in range(len(c.reqs)) if c.active[k]]
+        room = self.budget - self.in_use - sum(self.estimate(c.reqs[k]) for c, k in movers)
+        take = self._admit(pending, now, room)
+        waiting = bool(pending) and pending[0].arrival <= now
+        if not take and not (movers and waiting):
+            # nothing arrived that fits; unfinished games move on their own
+            # only when that frees memory for a request that is waiting
+            return False
+        reqs = take + [c.reqs[k] for c, k in movers]
+        if not reqs:
+            return False
+        c = Cohort(reqs, sum(self.estimate(r) for r in reqs))
+        self.in_use += c.bytes
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
+        self.n_cohorts += 1
+        for src in sparse:
+            pairs = [(len(take) + i, k) for i, (s_, k) in enumerate(movers) if s_ is src]
+            if pairs:
+                src.moving_to = c
+                c.sources.append((src, pairs))
+        trees, stream = [r.tree for r in reqs], self.stream_factory()
+        if self.loader is None:
+            c.solver = self.factory(trees, stream)
+            self._ready(c, t0)
+        else:
+            loading.append((self.loader(lambda ts=trees, st=stream: self.factory(ts, st)), c))
+        return True
+
+    def _ready(self, c: Cohort, t0: float):
+        """A loaded cohort joins the loop; its bytes are re-counted from what
         the library really holds."""
         real = float(c.solver.sizes()["device_bytes"])
         self.bytes_per_node = max(self.bytes_per_node, real / max(1, sum(r.nodes for r in c.reqs)))
@@ -150,8 +195,47 @@ class Server:
         self.peak_in_use = max(self.peak_in_use, self.in_use)
         now = self.clock() - t0
         for r in c.reqs:
-            r.admitted = now
+            if r.admitted < 0:
+                r.admitted = now
         self.cohorts.append(c)
+
+    def _move_in(self, c: Cohort) -> bool:
+        """Take the unfinished games of c's source cohorts once each is between
+        rounds; frees a source once its games are in.  True when c may run."""
+        for src, pairs in list(c.sources):
+            if src.round is not None:
+                continue
+            live = [(d, k) for d, k in pairs if src.active[k]]
+            for d, k in pairs:
+                if not src.active[k]:
+                    c.active[d] = 0     # solved in the meantime (its slot idles)
+            if live:
+                c.solver.copy_states_from(src.solver, [d for d, _ in live], [k for _, k in live])
+                for d, k in live:
+                    src.active[k] = 0
+                    c.reqs[d].moves += 1
+                self.n_moves += len(live)
+            c.sources.remove((src, pairs))
+            if src.finished:
+                self._free(src)
+        return not c.sources
+
+    def _free(self, c: Cohort):
+        c.solver.close()
+        self.in_use -= c.bytes
+        self.cohorts.remove(c)
+
+    def _complete(self, c: Cohort, expl: np.ndarray, now: float):
+        for k, r in enumerate(c.reqs):
+            if not c.active[k]:
+                continue
+            r.iterations += self.round_iters
+            r.exploitability = float(expl[k])
+            if expl[k] <= self.target_rel * r.payoff_range or r.iterations >= self.max_iterations:
+                c.active[k] = 0
+                r.done = now
+                if self.on_complete is not None:
+                    self.on_complete(r, c.solver, k)
 
     def run(self, requests: List[Request], time_limit: float = float("inf")) -> dict:
         pending = sorted(requests, key=lambda r: r.arrival)
@@ -161,45 +245,52 @@ class Server:
             now = self.clock() - t0
             if now > time_limit:
                 break
-            # admit what has arrived, as cohorts under the budget (bytes are
-            # counted from admission on)
-            while True:
-                take = self._admit(pending, now)
-                if not take:
-                    break
-                c = Cohort(take, None, sum(self.estimate(r) for r in take))
-                self.in_use += c.bytes
-                self.peak_in_use = max(self.peak_in_use, self.in_use)
-                self.n_cohorts += 1
-                trees, stream = [r.tree for r in take], self.stream_factory()
-                if self.loader is None:
-                    c.solver = self.factory(trees, stream)
-                    self._start(c, t0)
-                else:
-                    loading.append((self.loader(lambda ts=trees, st=stream: self.factory(ts, st)), c))
+            progress = False
+            while self._form(pending, now, t0, loading):
+                progress = True
             for item in [x for x in loading if x[0].done()]:
                 loading.remove(item)
                 item[1].solver = item[0].result()
-                self._start(item[1], t0)
-            if not self.cohorts:
-                if loading:
-                    time.sleep(2e-4) if self.clock is time.perf_counter else None
-                elif pending:   # nothing resident: wait for the next arrival
+                self._ready(item[1], t0)
+                progress = True
+            for c in list(self.cohorts):
+                if c not in self.cohorts:   # freed as a source earlier in this pass
+                    continue
+                if not c.started:
+                    if not self._move_in(c):
+                        continue
+                    c.started = True
+                    if c.finished:      # every game was solved before it moved
+                        self._free(c)
+                        continue
+                if c.round is not None and c.round.done():
+                    expl = c.round.result()
+                    c.round = None
+                    self._complete(c, expl, self.clock() - t0)
+                    progress = True
+                if c.round is None:
+                    if c.finished:
+                        if c.moving_to is None or c.moving_to.started:
+                            self._free(c)
+                        continue
+                    if c.moving_to is not None and c.moving_to.solver is not None:
+                        continue        # its unfinished games are about to move
+                    c.round = c.solver.start_round(self.round_iters, self.variant, active=c.active)
+                    progress = True
+            if not progress:
+                if not self.cohorts and not loading and pending:
                     self._wait_until(t0, pending[0].arrival)
-                continue
-            # one round for every live cohort (asynchronous on their streams),
-            # then the exploitability of each cohort's games
-            for c in self.cohorts:
-                c.solver.iterate(self.round_iters, self.variant, active=c.active)
-                c.iterations += self.round_iters
-            for c in self.cohorts:
-                expl, _, _ = c.solver.exploitability_batch()
-                self._complete(c, expl, self.clock() - t0)
-            for c in [c for c in self.cohorts if c.finished]:
-                c.solver.close()
-                self.in_use -= c.bytes
-                self.cohorts.remove(c)
+                elif self.clock is time.perf_counter:
+                    time.sleep(5e-5)
         return self.stats(requests, self.clock() - t0)
+
+    def _wait_until(self, t0: float, t: float):
+        while True:
+            left = t - (self.clock() - t0)
+            if left <= 0:
+                return
+            if self.clock is time.perf_counter:
+                time.sleep(min(left, 1e-3))
 
     def stats(self, requests: List[Request], elapsed: float) -> dict:
         done = [r for r in requests if r.done >= 0]
@@ -214,8 +305,8 @@ class Server:
             "p99_latency_s": float(np.percentile(lat, 99)) if done else None,
             "mean_iterations": float(np.mean([r.iterations for r in done])) if done else None,
             "node_iterations": float(sum(r.nodes * r.iterations for r in done)),
-            "cohorts": self.n_cohorts, "peak_bytes": self.peak_in_use, "budget_bytes": self.budget,
-            "rejected": len(self.rejected),
+            "cohorts": self.n_cohorts, "moved_games": self.n_moves, "peak_bytes": self.peak_in_use,
+            "budget_bytes": self.budget, "rejected": len(self.rejected),
         }
 
 
@@ -265,6 +356,7 @@ def serve_one_at_a_time(solver_factory: Callable, requests: List[Request], round
             if e[0] <= target_rel * r.payoff_range or it >= max_iterations:
                 break
         r.iterations = it
+        r.exploitability = float(e[0])
         r.done = clock() - t0
         s.close()
     srv = Server(solver_factory)

@@ -569,6 +569,26 @@ def test_graph_length_does_not_change_results(cfr):
         assert np.array_equal(a.get_state(p)["r"], b.get_state(p)["r"])
 
 
+def test_prepared_graph_replays_the_same_iterations(cfr):
+    """prepare_graph captures without running: the state stays put, and the
+    iterations replayed from the prepared graph equal eager ones."""
+    tree = G.poker_game()
+    a = cfr.Solver(tree)
+    b = cfr.Solver(tree)
+    a.set_graph_iterations(1)
+    b.set_graph_iterations(20)
+    before = b.get_state(1)["r"].copy()
+    b.prepare_graph("dcfr")
+    b.prepare_graph("pcfr+")
+    b.sync()
+    assert np.array_equal(b.get_state(1)["r"], before)
+    assert b.sizes(0)["t"] == 0
+    a.iterate(40, "dcfr")
+    b.iterate(40, "dcfr")
+    for p in (1, 2):
+        assert np.array_equal(a.get_state(p)["r"], b.get_state(p)["r"])
+
+
 def test_checkpoint_resume(cfr):
     tree = G.poker_game()
     a = cfr.Solver(tree)

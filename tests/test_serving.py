@@ -16,15 +16,32 @@ class FakeClock:
         return self.t
 
 
+class FakeRound:
+    """A round whose result is ready after a few polls."""
+
+    def __init__(self, e, polls=2):
+        self.e, self.left = e, polls
+
+    def done(self):
+        self.left -= 1
+        return self.left < 0
+
+    def result(self):
+        return self.e
+
+
 class FakeSolver:
-    """exploitability of game k after n iterations: range_k * 0.5 / n, so a
-    1e-3 target is met after 512 iterations; holds 100 bytes per node."""
+    """exploitability of game k after n iterations: range_k * c_k / n, with
+    c_k = 0.5 unless `spread` varies it by game; a 1e-3 target is then met
+    after 512 iterations; holds 100 bytes per node."""
     log = []
+    spread = False
 
     def __init__(self, trees, stream=None):
         self.trees = trees
         self.n = np.zeros(len(trees))
         self.ranges = np.array([S.payoff_range(t) for t in trees])
+        self.c = np.array([0.05 + 0.2 * (t.n_nodes % 7) if FakeSolver.spread else 0.5 for t in trees])
         self.closed = False
         FakeSolver.log.append(self)
         self.masks = []
@@ -35,8 +52,19 @@ class FakeSolver:
         self.n[a] += n
 
     def exploitability_batch(self):
-        e = self.ranges * 0.5 / np.maximum(self.n, 1)
+        e = self.ranges * self.c / np.maximum(self.n, 1)
         return e, e, e
+
+    def start_round(self, n, variant="dcfr", active=None):
+        assert not self.closed
+        self.iterate(n, variant, active)
+        return FakeRound(self.exploitability_batch()[0].copy())
+
+    def copy_states_from(self, src, dst_games, src_games):
+        assert not src.closed and not self.closed
+        for d, k in zip(dst_games, src_games):
+            assert src.trees[k] is self.trees[d]
+            self.n[d] = src.n[k]
 
     def sizes(self, g=0):
         return {"device_bytes": 100 * sum(t.n_nodes for t in self.trees)}
@@ -62,7 +90,7 @@ def test_all_requests_complete_at_their_target():
     assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
     assert st["solves_per_s"] > 0
     assert all(s.closed for s in FakeSolver.log)
-    assert srv.in_use == 0
+    assert abs(srv.in_use) < 1.0
 
 
 def test_budget_limits_what_is_resident():
@@ -110,6 +138,36 @@ def test_mixed_sizes_finish_in_a_shared_cohort():
     assert st["completed"] == 3 and st["cohorts"] == 1
 
 
+def alone_iterations(r, c_of):
+    c = c_of(r.tree)
+    need = c / 1e-3                     # range * c / n <= 1e-3 * range
+    return int(np.ceil(need / 64.0) * 64)
+
+
+def test_unfinished_games_move_to_new_cohorts_and_memory_returns():
+    """Games of one cohort finish at different times; once most of a cohort
+    is solved, its unfinished games move into the next cohort formed from new
+    arrivals, with their state, and the old cohort's memory is returned.
+    Every request still takes exactly the iterations it takes alone."""
+    FakeSolver.log = []
+    FakeSolver.spread = True
+    try:
+        trees = [G.sized_random_game(7000 + k, 200 + 37 * k) for k in range(40)]
+        rq = S.make_requests(trees, np.repeat(np.arange(5) * 0.008, 8))   # five bursts of eight
+        srv = S.Server(FakeSolver, hbm_budget=1e12, round_iters=64, max_cohort=8, clock=FakeClock(2e-4),
+                       repack_live=0.6)
+        st = srv.run(rq)
+        assert st["completed"] == len(rq)
+        assert st["moved_games"] > 0
+        assert all(s.closed for s in FakeSolver.log) and srv.in_use == 0
+        c_of = lambda t: 0.05 + 0.2 * (t.n_nodes % 7)
+        for r in rq:
+            assert r.iterations == alone_iterations(r, c_of), (r.rid, r.iterations, r.moves)
+        assert any(r.moves > 0 for r in rq)
+    finally:
+        FakeSolver.spread = False
+
+
 def test_one_at_a_time_baseline():
     rq = reqs(5)
     st = S.serve_one_at_a_time(FakeSolver, rq, clock=FakeClock())
@@ -127,7 +185,7 @@ def test_background_loader():
         st = srv.run(rq)
     assert st["completed"] == len(rq)
     assert st["cohorts"] >= 2          # the node cap splits the arrivals
-    assert srv.in_use == 0
+    assert abs(srv.in_use) < 1.0
 
 
 def test_loader_pool_starts_every_thread_first():
