@@ -239,6 +239,41 @@ def cpu_baseline(tree, variant, budget_s=15.0, name="large", cores=None):
             "cpu_model": model, "nproc": nproc}
 
 
+def oracle_parity(s, tree, variant):
+    """The timed run's parity against the FP64 oracle, taken in the CPU leg:
+    the oracle picks up the GPU's final state.  Both sides evaluate the FP64
+    exploitability of the GPU's average strategies, then each runs one more
+    iteration from that state.  Reported: the relative difference of the two
+    exploitabilities, and the largest element-wise one-step errors of the
+    regrets (against the regret update's own magnitude) and of the average
+    sums (against the vector's RMS), beside the tests' one-step bound."""
+    from oracle.oracle import Oracle
+    from tests.parity_util import ONE_STEP_RTOL, elementwise, oracle_values, regret_scale
+    t0 = time.perf_counter()
+    o = Oracle(tree)
+    for p in (1, 2):
+        st = s.get_state(p)
+        o.set_state(p, st["r"], st["b"], st["xbar"], st["t"])
+    e_o = o.exploitability()[0]
+    e_g = s.exploitability()[0]
+    init = {p: (o.get_state(p)["r"], o.get_state(p)["b"]) for p in (1, 2)}
+    o.iterate(1, variant)
+    s.iterate(1, variant)
+    vals = oracle_values(o, init, s.get_state(1)["b"], alternating=(variant != "cfr"))
+    err_r = err_x = 0.0
+    for p in (1, 2):
+        g_, o_ = s.get_state(p), o.get_state(p)
+        sc = regret_scale(o, p, init[p][0], o_["r"], vals[p][0], vals[p][1])
+        err_r = max(err_r, float(np.max(np.abs(g_["r"] - o_["r"]) / np.maximum(sc, 1e-300))))
+        err_x = max(err_x, elementwise(g_["xbar"], o_["xbar"]))
+    return {"t": s.sizes()["t"] - 1, "exploitability": e_g, "oracle_exploitability": e_o,
+            "exploitability_rel_diff": abs(e_g - e_o) / max(abs(e_o), 1e-300),
+            "one_step_r_err": err_r, "one_step_xbar_err": err_x, "one_step_tol": ONE_STEP_RTOL,
+            "seconds": time.perf_counter() - t0,
+            "what": "FP64 exploitability of the GPU's averages on both sides; then one iteration each from "
+                    "the GPU's state, element-wise errors"}
+
+
 def max_over_ranks(x, dist):
     """The largest value over all ranks (the slowest rank's time), on every rank."""
     if not dist:
@@ -460,6 +495,7 @@ def run_ours(args):
                "what": "Solver(host tree) + iterate + exploitability + average strategies, wall clock"}
         cpu = (cpu_baseline(tree, variant, budget_s=args.cpu_budget, name=args.workload)
                if (world == 1 and not args.no_cpu) else None)
+        parity = oracle_parity(s, tree, variant) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -484,6 +520,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "parity": parity,
         }
         if not args.no_sub and world == 1:
             # the batched and served workloads, bounded, in the same run
@@ -517,16 +554,23 @@ def solve_batch(s, trees, variant, target_rel=1e-3, cap=8192):
 
 
 def batch_summary(args, stream):
-    """The 4096-game batch (CFR+, 64-iteration graphs, the library's launch
-    shape): iteration time and node-updates/s against one launch sequence
-    per game, and solves/s to exploitability <= 1e-3 of the payoff range
-    against solving the games one at a time (on a sample)."""
+    """The 4096-game batch (CFR+, 64-iteration graphs, the launch shape and
+    layout the autotuner picks on every 8th game within a few seconds):
+    iteration time and node-updates/s against one launch sequence per game,
+    and solves/s to exploitability <= 1e-3 of the payoff range against
+    solving the games one at a time (on a sample)."""
     import torch
+    from paper_2605_14277_b300 import autotune
     from paper_2605_14277_b300 import cfr as C
     variant = "cfr+"
     trees = G.batch_games(args.batch_games)
     nodes = sum(t.n_nodes for t in trees)
-    s = C.Solver(trees, stream=stream)
+    t0 = time.perf_counter()
+    tuned = autotune.tune(trees[::8], variant=variant, iterations=64, repeats=2, stream=stream,
+                          budget_s=args.batch_tune_seconds)
+    tune_s = time.perf_counter() - t0
+    layout = {"shape": tuned["shape"], "flat": tuned["flat"], "passes": tuned["passes"]}
+    s = C.Solver(trees, stream=stream, **layout)
     sizes = [s.sizes(g) for g in range(len(trees))]
     s.iterate(64, variant)
     s.sync()
@@ -558,7 +602,7 @@ def batch_summary(args, stream):
     for x in solos:
         x.close()
     # solves: the whole batch in one context, against a sample one at a time
-    s = C.Solver(trees, stream=stream)
+    s = C.Solver(trees, stream=stream, **layout)
     sec, its, e = solve_batch(s, trees, variant)
     s.close()
     one_sec = 0.0
@@ -570,6 +614,9 @@ def batch_summary(args, stream):
         one_its.append(int(it1[0]))
         x.close()
     return {"workload": f"{len(trees)} random games, nodes log-uniform in [1e2, 1e5], CFR+", "nodes": nodes,
+            "layout": {**layout, "shape_info": C.shapes()[layout["shape"]], "tune_seconds": tune_s,
+                       "candidates_timed": len(tuned["table"]),
+                       "default_shape": C.pick_shape(len(trees), nodes)},
             "us_per_iteration": ms * 1e3, "node_updates_per_s": nodes / (ms * 1e-3),
             "roofline_frac_of_measured_hbm": iter_bytes / (ms * 1e-3) / 1e9 / hbm,
             "alg_bytes_per_iteration": iter_bytes, "gpu_launches_per_iteration": launches,
@@ -664,7 +711,7 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     # autotune on a sample of the batch (every 8th game)
     tuned = autotune.tune(trees[::8], variant=variant, iterations=64, repeats=2, stream=stream,
-                          budget_s=args.tune_budget)
+                          cache=args.tune_cache, budget_s=args.tune_budget)
     s = C.Solver(trees, stream=stream, shape=tuned["shape"], flat=tuned["flat"], passes=tuned["passes"])
     s.set_graph_iterations(64)
     sizes = [s.sizes(g) for g in range(n_games)]
@@ -848,6 +895,10 @@ def main():
     ap.add_argument("--batch-games", type=int, default=4096)
     ap.add_argument("--per-game-sample", type=int, default=128)
     ap.add_argument("--tune-budget", type=float, default=60.0)
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file keeping the autotuner's choice per layout signature (--workload batch)")
+    ap.add_argument("--batch-tune-seconds", type=float, default=8.0,
+                    help="autotuning budget of the batch summary in the default line")
     ap.add_argument("--e2e-iters", type=int, default=10000)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")

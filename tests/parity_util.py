@@ -79,6 +79,31 @@ def check_final_expl(e_g, runs, what, rtol=EXPL_RTOL):
     return "oracle range", err, spread
 
 
+def oracle_values(o, init, b1_next, alternating):
+    """The oracle's counterfactual values V (per sequence) and ev (per
+    infoset) of each player's bottom-up pass in the iteration just run, from
+    the state before it (init[p] = (r, b)) and, for player 2 under alternating
+    updates, player 1's next strategy as the GPU computed it (so a
+    regret-matching tie in player 1 cannot leak into player 2's check)."""
+    (r1, b1), (r2, b2) = init[1], init[2]
+    u1 = o.utility(1, o.sequence_form(2, b2))
+    _, V1, ev1 = o.observe_utility(1, u1, b1, r1)
+    x1 = o.sequence_form(1, b1_next if alternating else b1)
+    _, V2, ev2 = o.observe_utility(2, o.utility(2, x1), b2, r2)
+    return {1: (V1[1:], ev1), 2: (V2[1:], ev2)}
+
+
+def regret_scale(o, p, r_old, r_new, V, ev):
+    """Per-sequence magnitude of the regret update r + (V - ev) followed by
+    the post-op (a clip or a factor <= 1): an FP32 evaluation of it is off by
+    a few ulp of |r_old| + |V| + |ev|, so that (or the vector's RMS, if
+    larger) is the scale of the element-wise check."""
+    _, na = o.infosets(p)
+    ev_seq = np.repeat(ev, na)
+    s = np.abs(r_old) + np.abs(V) + np.abs(ev_seq)
+    return np.maximum(s, np.sqrt(np.mean(r_new * r_new)))
+
+
 def random_state(o, p, rng, scale=1.0, t=5):
     """Seeded state for player p of an oracle game: regrets, a behavioural
     strategy on each infoset's simplex, positive average sums."""

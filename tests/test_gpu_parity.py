@@ -26,7 +26,7 @@ import json
 import os
 
 from tests.parity_util import (EXPL_RTOL, ONE_STEP_RTOL, assert_elementwise, check_ensembles, check_final_expl,
-                               random_state, rel, reorder,
+                               oracle_values, random_state, regret_scale, rel, reorder,
                                strategy_mismatch_ok)
 
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -58,31 +58,6 @@ def parity_games():
         "rps": G.rps(),
         "mixed3": G.matrix_game(G.random_fully_mixed(3, 3)[0]),
     }
-
-
-def oracle_values(o, init, b1_next, alternating):
-    """The oracle's counterfactual values V (per sequence) and ev (per
-    infoset) of each player's bottom-up pass in the iteration just run, from
-    the state before it (init[p] = (r, b)) and, for player 2 under alternating
-    updates, player 1's next strategy as the GPU computed it (so a
-    regret-matching tie in player 1 cannot leak into player 2's check)."""
-    (r1, b1), (r2, b2) = init[1], init[2]
-    u1 = o.utility(1, o.sequence_form(2, b2))
-    _, V1, ev1 = o.observe_utility(1, u1, b1, r1)
-    x1 = o.sequence_form(1, b1_next if alternating else b1)
-    _, V2, ev2 = o.observe_utility(2, o.utility(2, x1), b2, r2)
-    return {1: (V1[1:], ev1), 2: (V2[1:], ev2)}
-
-
-def regret_scale(o, p, r_old, r_new, V, ev):
-    """Per-sequence magnitude of the regret update r + (V - ev) followed by
-    the post-op (a clip or a factor <= 1): an FP32 evaluation of it is off by
-    a few ulp of |r_old| + |V| + |ev|, so that (or the vector's RMS, if
-    larger) is the scale of the element-wise check."""
-    _, na = o.infosets(p)
-    ev_seq = np.repeat(ev, na)
-    s = np.abs(r_old) + np.abs(V) + np.abs(ev_seq)
-    return np.maximum(s, np.sqrt(np.mean(r_new * r_new)))
 
 
 def assert_regrets(g_r, o_r, r_old, V, ev, o, p, what):
