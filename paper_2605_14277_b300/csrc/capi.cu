@@ -1487,6 +1487,12 @@ int graph_for(cfr_ctx *c, const GraphKey &key, bool alt, cudaGraphExec_t *out) {
     ee = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ee != cudaSuccess) return set_err(CFR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
+    // the graph's device-side set-up now, not on its first replay
+    ee = cudaGraphUpload(exec, c->stream);
+    if (ee != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return set_err(CFR_ERR_CUDA, std::string("graph upload: ") + cudaGetErrorString(ee));
+    }
     c->graphs[key] = exec;
     c->graph_kernels[key] = nk;
     *out = exec;
