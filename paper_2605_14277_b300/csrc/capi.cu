@@ -451,9 +451,19 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
                 consumer_sync();
             }
             if (staged && !S.err) {
-                up_gather(xo, h.y, S.lv[buf], S.tab[buf]);
+                up_gather(xo, h.y, S.lv[buf], S.tab[buf], internal);
                 compute_up(ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal);
-                up_write_back(P, h.y, S.lv[buf], S.tab[buf], ia.keep_values != 0);
+                up_write_ev(P, h.y, S.lv[buf], S.tab[buf], ia.keep_values != 0);
+                if (internal && !root) {
+                    // the parent reads only this unit's top-level ev: count
+                    // the unit there now, before r and b are written back
+                    consumer_sync();
+                    if (tid == 32) {
+                        __threadfence();
+                        atomicAdd(&P.unit_cnt[tr.x], 1);
+                    }
+                }
+                up_write_rb(P, h.y, S.lv[buf], S.tab[buf]);
             }
         }
         __syncthreads();
@@ -468,7 +478,9 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             __threadfence();
             st_release(&P.root_done[h.x], root_flag);
         }
-        done_par = ip.active ? tr.x : -1;
+        // the producer counts the unit at its parent at the start of the next
+        // round (a staged internal unit has counted itself already)
+        done_par = (ip.active && !(staged && internal)) ? tr.x : -1;
         cur = S.unit[buf ^ 1];
         buf ^= 1;
     }

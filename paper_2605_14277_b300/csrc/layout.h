@@ -82,8 +82,8 @@ __host__ __device__ inline int64_t up_level_bytes(int64_t ns, int64_t ni, int64_
     return up_level_bytes_x(ns, ni, nz, work16(nz, 4));
 }
 __host__ __device__ inline int64_t down_level_bytes(int64_t ns, int64_t ni) {
-    // b, infoset parents, infoset segments; work: the next x
-    return span16(ns, 4) + span16(ni, 4) + span16(ni + 1, 4) + work16(ns, 4);
+    // b (the next x is computed in place over it), infoset parents, infoset segments
+    return span16(ns, 4) + span16(ni, 4) + span16(ni + 1, 4);
 }
 
 struct PlayerLayout {

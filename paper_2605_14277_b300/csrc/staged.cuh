@@ -147,7 +147,8 @@ struct UpTab {
 };
 struct DownTab {
     uint32_t b;     // float, copied in
-    uint32_t x;     // float, the next x (work area)
+    uint32_t x;     // float, the next x: computed in place over b (each sequence's b is read
+                    // once, by the thread that then writes its x)
     uint32_t ipar, iseq;
 };
 constexpr int kDownArrays = 3;   // commands staged per top-down level: b, infoset parents, infoset segments
@@ -434,8 +435,7 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
         CFR_STAGE(ipar, P.inf_par, L.j0, L.j1, 4, 1)
         CFR_STAGE(iseq, P.inf_seq, L.j0, L.j1 + 1, 4, 2)
 #undef CFR_STAGE
-        t.x = sh_off(cur);
-        cur += work16(L.s1 - L.s0, 4);
+        t.x = t.b;
     }
     __syncwarp();
     uint32_t mine = carried;
@@ -554,7 +554,7 @@ __device__ __forceinline__ float ordered_sum(float acc, int i0, int i1, T &&term
 
 // the levels of a staged unit, bottom-up, for one variant (the rows are done)
 template <int VAR>
-__device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
+__device__ __forceinline__ void up_levels(const ItemParams &ip, float sign, int nl, const SLvl *lv, const UpTab *tab,
                                           const ChildEv *cev, bool internal) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     const float2 fpos = ip.fpos, fneg = ip.fneg;
@@ -568,8 +568,12 @@ __device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SL
             const float *evc = sh<const float>(deepest ? cev->ev : tab[k + 1].ev);
             const int cj0 = deepest ? cev->c0 : lv[k + 1].j0;
             const int ns = L.s1 - L.s0;
+            // a level without payoff entries had no row pass: its rows are
+            // sign * 0, the value the row pass gives an empty row
+            const bool rows = L.n1 > L.n0;
             for (int q = tid; q < ns; q += nt)
-                t.V[q] = ordered_sum(t.V[q], t.sch[q] - cj0, t.sch[q + 1] - cj0, [&](int c) { return evc[c]; });
+                t.V[q] = ordered_sum(rows ? t.V[q] : sign * 0.f, t.sch[q] - cj0, t.sch[q + 1] - cj0,
+                                     [&](int c) { return evc[c]; });
             consumer_sync();
         }
         const int ni = L.j1 - L.j0;
@@ -585,12 +589,18 @@ __device__ __forceinline__ void up_levels(const ItemParams &ip, int nl, const SL
 // The payoff rows of a staged unit are worked by one consumer thread per
 // sequence, every level of the unit in one numbering (the thread index runs on
 // across levels, so a short level does not idle a round).  f(k, q) is called
-// for level k, sequence q of the level, by the thread that owns it.
+// for level k, sequence q of the level, by the thread that owns it.  A level
+// without payoff entries is skipped, except a leaf's deepest level (no child
+// phase follows it there): its values start at sign * 0 in the child phase.
+__device__ __forceinline__ bool level_has_rows(const SLvl *lv, int k, int nl, bool internal) {
+    return lv[k].n1 > lv[k].n0 || (k + 1 == nl && !internal);
+}
 template <class F>
-__device__ __forceinline__ void for_rows(int nl, const SLvl *lv, F &&f) {
+__device__ __forceinline__ void for_rows(int nl, const SLvl *lv, bool internal, F &&f) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     int off = 0;
     for (int k = 0; k < nl; k++) {
+        if (!level_has_rows(lv, k, nl, internal)) continue;
         const int ns = lv[k].s1 - lv[k].s0;
         int q = tid - off;
         if (q < 0) q += nt;
@@ -604,8 +614,9 @@ __device__ __forceinline__ void for_rows(int nl, const SLvl *lv, F &&f) {
 // row's by the thread that will sum it.  Issued as soon as the unit's arrays
 // are in, which is normally while the previous unit is still being written
 // back, so the gathers' latency is hidden.
-__device__ __forceinline__ void up_gather(const float *__restrict__ xo, int nl, const SLvl *lv, const UpTab *tab) {
-    for_rows(nl, lv, [&](int k, int q) {
+__device__ __forceinline__ void up_gather(const float *__restrict__ xo, int nl, const SLvl *lv, const UpTab *tab,
+                                          bool internal) {
+    for_rows(nl, lv, internal, [&](int k, int q) {
         if (tab[k].nwin) return;   // copied in as windows
         const int n0 = lv[k].n0;
         const int32_t *mptr = sh<const int32_t>(tab[k].mptr);
@@ -622,7 +633,7 @@ __device__ __forceinline__ void up_gather(const float *__restrict__ xo, int nl, 
 __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
                            const ChildEv *cev, bool internal) {
     cp_async_wait_all();
-    for_rows(nl, lv, [&](int k, int q) {
+    for_rows(nl, lv, internal, [&](int k, int q) {
         const int n0 = lv[k].n0;
         const int32_t *mptr = sh<const int32_t>(tab[k].mptr);
         const float *val = sh<const float>(tab[k].val);
@@ -639,18 +650,26 @@ __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, con
     });
     consumer_sync();
     switch (ia.variant) {
-    case VAR_PLUS: up_levels<VAR_PLUS>(ip, nl, lv, tab, cev, internal); break;
-    case VAR_DCFR: up_levels<VAR_DCFR>(ip, nl, lv, tab, cev, internal); break;
-    case VAR_PCFR_PLUS: up_levels<VAR_PCFR_PLUS>(ip, nl, lv, tab, cev, internal); break;
-    case VAR_PCFR: up_levels<VAR_PCFR>(ip, nl, lv, tab, cev, internal); break;
-    default: up_levels<VAR_CFR>(ip, nl, lv, tab, cev, internal); break;
+    case VAR_PLUS: up_levels<VAR_PLUS>(ip, ia.sign, nl, lv, tab, cev, internal); break;
+    case VAR_DCFR: up_levels<VAR_DCFR>(ip, ia.sign, nl, lv, tab, cev, internal); break;
+    case VAR_PCFR_PLUS: up_levels<VAR_PCFR_PLUS>(ip, ia.sign, nl, lv, tab, cev, internal); break;
+    case VAR_PCFR: up_levels<VAR_PCFR>(ip, ia.sign, nl, lv, tab, cev, internal); break;
+    default: up_levels<VAR_CFR>(ip, ia.sign, nl, lv, tab, cev, internal); break;
     }
 }
 
-// Part 3: write-back (coalesced): r, b and the top level's ev (every level's
-// with `all_ev`).
-__device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab,
-                                              bool all_ev) {
+// Part 3: write-back (coalesced): the top level's ev (every level's with
+// `all_ev`), which is all a parent unit reads, and r and b.
+__device__ __forceinline__ void up_write_ev(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab,
+                                            bool all_ev) {
+    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
+    for (int k = 0; k < (all_ev ? nl : min(nl, 1)); k++) {
+        const int ni = lv[k].j1 - lv[k].j0;
+        const float *ev = sh<const float>(tab[k].ev);
+        for (int i = tid; i < ni; i += nt) P.ev[lv[k].j0 + i] = ev[i];
+    }
+}
+__device__ __forceinline__ void up_write_rb(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     for (int k = 0; k < nl; k++) {
         const SLvl L = lv[k];
@@ -660,11 +679,6 @@ __device__ __forceinline__ void up_write_back(const DevPlayer &P, int nl, const 
             P.r[L.s0 + q] = t.r[q];
             P.b[L.s0 + q] = t.b[q];
         }
-    }
-    for (int k = 0; k < (all_ev ? nl : min(nl, 1)); k++) {
-        const int ni = lv[k].j1 - lv[k].j0;
-        const float *ev = sh<const float>(tab[k].ev);
-        for (int i = tid; i < ni; i += nt) P.ev[lv[k].j0 + i] = ev[i];
     }
 }
 

@@ -110,5 +110,6 @@ def up_bytes(ns, ni, nz):
 
 
 def down_bytes(ns, ni):
-    """shared-memory bytes of one staged level of the down pass (layout.h)"""
-    return span16(ns, 4) + span16(ni, 4) + span16(ni + 1, 4) + work16(ns, 4)
+    """shared-memory bytes of one staged level of the down pass (layout.h): b,
+    over which the next x is computed in place, infoset parents and segments"""
+    return span16(ns, 4) + span16(ni, 4) + span16(ni + 1, 4)
