@@ -397,15 +397,11 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
         }
         const ItemParams ip = S.ip[buf];
         if (warp == 0) {
-            // producer: count the previous unit at its parent (its results
-            // were written before the barrier above); issue the prefetched
-            // unit into the other buffer; then prefetch the unit after it,
-            // whose queue position came last round, and start fetching the
-            // next position
-            if (tid == 0 && done_par >= 0) {
-                __threadfence();
-                atomicAdd(&P.unit_cnt[done_par], 1);
-            }
+            // producer: issue the prefetched unit into the other buffer;
+            // count the previous unit at its parent (its results were
+            // written before the barrier above); then prefetch the unit after
+            // the next one, whose queue position came last round, and start
+            // fetching the next position
             // the queue entry of the unit after next (its position came
             // last round): loaded now, used after the issue below
             const int p = __shfl_sync(0xffffffffu, pend, 0);
@@ -431,6 +427,10 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
                 S.hq[buf ^ 1][0] = S.pre.h;
                 S.hq[buf ^ 1][1] = S.pre.q;
             }
+            if (tid == 0 && done_par >= 0) {
+                __threadfence();
+                atomicAdd(&P.unit_cnt[done_par], 1);
+            }
             __syncwarp();   // S.pre is read: the next one may overwrite it
             if (tid == 0) pend = p < n ? fetch() : n;
             if (p < n) up_prefetch(P, gm, ia, p, hp, qp, S.pre);
@@ -452,18 +452,14 @@ __device__ bool up_loop(const DevPlayer &P, const DevGames &gm, const float *__r
             }
             if (staged && !S.err) {
                 up_gather(xo, h.y, S.lv[buf], S.tab[buf], internal);
-                compute_up(ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal);
-                up_write_ev(P, h.y, S.lv[buf], S.tab[buf], ia.keep_values != 0);
-                if (internal && !root) {
-                    // the parent reads only this unit's top-level ev: count
-                    // the unit there now, before r and b are written back
-                    consumer_sync();
-                    if (tid == 32) {
-                        __threadfence();
-                        atomicAdd(&P.unit_cnt[tr.x], 1);
-                    }
+                compute_up(P, ia, ip, h.y, S.lv[buf], S.tab[buf], &S.cev[buf], internal);
+                if (internal && !root && tid == 32) {
+                    // the parent reads only this unit's top-level ev, stored
+                    // (with r and b) by the steps before the last consumer
+                    // barrier: count the unit there now
+                    __threadfence();
+                    atomicAdd(&P.unit_cnt[tr.x], 1);
                 }
-                up_write_rb(P, h.y, S.lv[buf], S.tab[buf]);
             }
         }
         __syncthreads();

@@ -479,9 +479,13 @@ __device__ __forceinline__ UpView view(const UpTab &t) {
 //   step:  one thread per infoset: ev = sum_a b[a] V[a], the regret update and
 //          post-op, regret matching (straight-line code for <= kRegA actions).
 // Every sum runs in the same order as in the global-memory path, so results
-// do not depend on how a game is cut into units.
+// do not depend on how a game is cut into units.  The step stores the new r
+// and b straight to global memory (gr, gb: the level's first sequence) and,
+// when gev is given, ev too (the level's first infoset); the staged ev stays
+// in shared memory for the level above.
 template <int VAR>
-__device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int na, float2 fpos, float2 fneg) {
+__device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int na, float2 fpos, float2 fneg,
+                                            float2 *gr, float *gb, float *gev) {
     float V[kRegA], bb[kRegA];
     float2 rr[kRegA];
 #pragma unroll
@@ -496,12 +500,13 @@ __device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int 
     for (int a = 0; a < kRegA; a++)
         if (a < na) ev = fmaf(bb[a], V[a], ev);
     t.ev[i] = ev;
+    if (gev) gev[i] = ev;
     float pos = 0.f, qv[kRegA];
 #pragma unroll
     for (int a = 0; a < kRegA; a++) {
         const float d = V[a] - ev;
         const float2 r = post_op_v<VAR>(ff_add_f(rr[a], d), fpos, fneg);
-        if (a < na) t.r[q0 + a] = r;
+        if (a < na) gr[q0 + a] = r;
         const float x = predictive(VAR) ? r.x + d : r.x;
         qv[a] = (a < na && x > 0.f) ? x : 0.f;
         pos += qv[a];
@@ -510,21 +515,23 @@ __device__ __forceinline__ void up_step_reg(const UpView &t, int i, int q0, int 
     const float uni = uniform_prob(na);
 #pragma unroll
     for (int a = 0; a < kRegA; a++)
-        if (a < na) t.b[q0 + a] = pos > 0.f ? rm_prob(qv[a], nrm) : uni;
+        if (a < na) gb[q0 + a] = pos > 0.f ? rm_prob(qv[a], nrm) : uni;
 }
 
 // the same for infosets with more actions, through shared memory
 template <int VAR>
-__device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float2 fpos, float2 fneg) {
+__device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float2 fpos, float2 fneg, float2 *gr,
+                                          float *gb, float *gev) {
     const UpView t = view(tt);
     float ev = 0.f;
     for (int q = q0; q < q1; q++) ev = fmaf(t.b[q], t.V[q], ev);
     t.ev[i] = ev;
+    if (gev) gev[i] = ev;
     float pos = 0.f;
     for (int q = q0; q < q1; q++) {
         const float d = t.V[q] - ev;
         const float2 r = post_op_v<VAR>(ff_add_f(t.r[q], d), fpos, fneg);
-        t.r[q] = r;
+        gr[q] = r;
         const float rr = predictive(VAR) ? r.x + d : r.x;
         const float qq = rr > 0.f ? rr : 0.f;
         t.V[q] = qq;   // V is no longer needed: keep the clipped regret
@@ -532,7 +539,7 @@ __device__ __noinline__ void up_step_wide(UpTab tt, int i, int q0, int q1, float
     }
     const RmNorm nrm = rm_norm(pos);
     const float uni = uniform_prob(q1 - q0);
-    for (int q = q0; q < q1; q++) t.b[q] = pos > 0.f ? rm_prob(t.V[q], nrm) : uni;
+    for (int q = q0; q < q1; q++) gb[q] = pos > 0.f ? rm_prob(t.V[q], nrm) : uni;
 }
 
 // Ordered sums over a short index range, four terms per step: the four
@@ -554,8 +561,9 @@ __device__ __forceinline__ float ordered_sum(float acc, int i0, int i1, T &&term
 
 // the levels of a staged unit, bottom-up, for one variant (the rows are done)
 template <int VAR>
-__device__ __forceinline__ void up_levels(const ItemParams &ip, float sign, int nl, const SLvl *lv, const UpTab *tab,
-                                          const ChildEv *cev, bool internal) {
+__device__ __forceinline__ void up_levels(const DevPlayer &P, const ItemParams &ip, float sign, int nl,
+                                          const SLvl *lv, const UpTab *tab, const ChildEv *cev, bool internal,
+                                          bool all_ev) {
     const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
     const float2 fpos = ip.fpos, fneg = ip.fneg;
     for (int k = nl - 1; k >= 0; k--) {
@@ -577,10 +585,13 @@ __device__ __forceinline__ void up_levels(const ItemParams &ip, float sign, int 
             consumer_sync();
         }
         const int ni = L.j1 - L.j0;
+        float2 *gr = P.r + L.s0;
+        float *gb = P.b + L.s0;
+        float *gev = (k == 0 || all_ev) ? P.ev + L.j0 : nullptr;   // the parent reads the top level's
         for (int i = tid; i < ni; i += nt) {
             const int q0 = t.iseq[i] - L.s0, q1 = t.iseq[i + 1] - L.s0;
-            if (q1 - q0 <= kRegA) up_step_reg<VAR>(t, i, q0, q1 - q0, fpos, fneg);
-            else up_step_wide<VAR>(tab[k], i, q0, q1, fpos, fneg);
+            if (q1 - q0 <= kRegA) up_step_reg<VAR>(t, i, q0, q1 - q0, fpos, fneg, gr, gb, gev);
+            else up_step_wide<VAR>(tab[k], i, q0, q1, fpos, fneg, gr, gb, gev);
         }
         consumer_sync();
     }
@@ -629,9 +640,10 @@ __device__ __forceinline__ void up_gather(const float *__restrict__ xo, int nl, 
 
 // Part 2: the row sums V[s] = sign * sum_e val[e] x[col[e]] (products rounded,
 // then added in CSR order), each by the thread that gathered the row (its
-// own copies are complete, no barrier needed); then the levels bottom-up.
-__device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv, const UpTab *tab,
-                           const ChildEv *cev, bool internal) {
+// own copies are complete, no barrier needed); then the levels bottom-up,
+// whose steps store r, b and ev to global memory.
+__device__ void compute_up(const DevPlayer &P, const IterArgs &ia, const ItemParams &ip, int nl, const SLvl *lv,
+                           const UpTab *tab, const ChildEv *cev, bool internal) {
     cp_async_wait_all();
     for_rows(nl, lv, internal, [&](int k, int q) {
         const int n0 = lv[k].n0;
@@ -650,35 +662,11 @@ __device__ void compute_up(const IterArgs &ia, const ItemParams &ip, int nl, con
     });
     consumer_sync();
     switch (ia.variant) {
-    case VAR_PLUS: up_levels<VAR_PLUS>(ip, ia.sign, nl, lv, tab, cev, internal); break;
-    case VAR_DCFR: up_levels<VAR_DCFR>(ip, ia.sign, nl, lv, tab, cev, internal); break;
-    case VAR_PCFR_PLUS: up_levels<VAR_PCFR_PLUS>(ip, ia.sign, nl, lv, tab, cev, internal); break;
-    case VAR_PCFR: up_levels<VAR_PCFR>(ip, ia.sign, nl, lv, tab, cev, internal); break;
-    default: up_levels<VAR_CFR>(ip, ia.sign, nl, lv, tab, cev, internal); break;
-    }
-}
-
-// Part 3: write-back (coalesced): the top level's ev (every level's with
-// `all_ev`), which is all a parent unit reads, and r and b.
-__device__ __forceinline__ void up_write_ev(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab,
-                                            bool all_ev) {
-    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
-    for (int k = 0; k < (all_ev ? nl : min(nl, 1)); k++) {
-        const int ni = lv[k].j1 - lv[k].j0;
-        const float *ev = sh<const float>(tab[k].ev);
-        for (int i = tid; i < ni; i += nt) P.ev[lv[k].j0 + i] = ev[i];
-    }
-}
-__device__ __forceinline__ void up_write_rb(const DevPlayer &P, int nl, const SLvl *lv, const UpTab *tab) {
-    const int tid = threadIdx.x - kProducerThreads, nt = blockDim.x - kProducerThreads;
-    for (int k = 0; k < nl; k++) {
-        const SLvl L = lv[k];
-        const UpView t = view(tab[k]);
-        const int ns = L.s1 - L.s0;
-        for (int q = tid; q < ns; q += nt) {
-            P.r[L.s0 + q] = t.r[q];
-            P.b[L.s0 + q] = t.b[q];
-        }
+    case VAR_PLUS: up_levels<VAR_PLUS>(P, ip, ia.sign, nl, lv, tab, cev, internal, ia.keep_values != 0); break;
+    case VAR_DCFR: up_levels<VAR_DCFR>(P, ip, ia.sign, nl, lv, tab, cev, internal, ia.keep_values != 0); break;
+    case VAR_PCFR_PLUS: up_levels<VAR_PCFR_PLUS>(P, ip, ia.sign, nl, lv, tab, cev, internal, ia.keep_values != 0); break;
+    case VAR_PCFR: up_levels<VAR_PCFR>(P, ip, ia.sign, nl, lv, tab, cev, internal, ia.keep_values != 0); break;
+    default: up_levels<VAR_CFR>(P, ip, ia.sign, nl, lv, tab, cev, internal, ia.keep_values != 0); break;
     }
 }
 
