@@ -674,20 +674,41 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             auto chain_bytes = [&](int64_t a, int64_t k) -> int64_t {
                 return ancestors(P.ranges[P.units[a].rng], P.ranges[P.units[k].rng + 1]);
             };
-            int64_t a = 0, acc = 0;
-            for (int64_t k = 0; k < nu0; k++) {
-                const Unit &u = P.units[k];
-                const int64_t fk = fdown(u);
-                const bool same = k > a && u.game == P.units[a].game && u.parent == P.units[a].parent &&
-                                  u.parent >= 0 && u.lvl0 == P.units[a].lvl0;
-                if (!same || acc + fk + chain_bytes(a, k) > opt.item_bytes) {
-                    if (k > a) build(a, k);
-                    a = k;
-                    acc = 0;
+            // runs of siblings merged while their footprint stays within cap;
+            // emit(a, b) takes each run
+            std::vector<int64_t> fdu(nu0);
+            for (int64_t k = 0; k < nu0; k++) fdu[k] = fdown(P.units[k]);
+            auto merge = [&](int64_t cap, auto &&emit_run) {
+                int64_t a = 0, acc = 0;
+                for (int64_t k = 0; k < nu0; k++) {
+                    const Unit &u = P.units[k];
+                    const bool same = k > a && u.game == P.units[a].game && u.parent == P.units[a].parent &&
+                                      u.parent >= 0 && u.lvl0 == P.units[a].lvl0;
+                    if (!same || acc + fdu[k] + chain_bytes(a, k) > cap) {
+                        if (k > a) emit_run(a, k);
+                        a = k;
+                        acc = 0;
+                    }
+                    acc += fdu[k];
                 }
-                acc += fk;
+                if (nu0 > a) emit_run(a, nu0);
+            };
+            // the smallest cap (within the buffer) that still gives no more
+            // units than resident CTAs: top-down units are independent, so
+            // the pass is then one round of CTAs with the most parallelism
+            auto count = [&](int64_t cap) {
+                int64_t n = 0;
+                merge(cap, [&](int64_t, int64_t) { n++; });
+                return n;
+            };
+            int64_t lo_cap = opt.min_item_bytes, hi_cap = opt.item_bytes;
+            if (count(hi_cap) <= opt.slots) {
+                while (hi_cap - lo_cap > 4096) {
+                    const int64_t mid = (lo_cap + hi_cap) / 2;
+                    (count(mid) <= opt.slots ? hi_cap : lo_cap) = mid;
+                }
             }
-            if (nu0 > a) build(a, nu0);
+            merge(hi_cap, build);
         }
         // queues: leaves largest first for the bottom-up passes (a dynamic
         // queue then finishes with small units); every unit by tree depth for
