@@ -695,17 +695,30 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             };
             // the smallest cap (within the buffer) that still gives no more
             // units than resident CTAs: top-down units are independent, so
-            // the pass is then one round of CTAs with the most parallelism
-            auto count = [&](int64_t cap) {
-                int64_t n = 0;
-                merge(cap, [&](int64_t, int64_t) { n++; });
+            // the pass is then one round of CTAs with the most parallelism.
+            // The count is estimated without the ancestor chains (cheap: one
+            // pass over the units per probe), aiming a little under the CTAs.
+            auto estimate = [&](int64_t cap) {
+                int64_t n = 0, acc = 0, a = 0;
+                for (int64_t k = 0; k < nu0; k++) {
+                    const Unit &u = P.units[k];
+                    const bool same = k > a && u.game == P.units[a].game && u.parent == P.units[a].parent &&
+                                      u.parent >= 0 && u.lvl0 == P.units[a].lvl0;
+                    if (!same || acc + fdu[k] > cap) {
+                        n++;
+                        a = k;
+                        acc = 0;
+                    }
+                    acc += fdu[k];
+                }
                 return n;
             };
+            const int64_t want = std::max<int64_t>(1, opt.slots * 7 / 8);
             int64_t lo_cap = opt.min_item_bytes, hi_cap = opt.item_bytes;
-            if (count(hi_cap) <= opt.slots) {
-                while (hi_cap - lo_cap > 4096) {
+            if (estimate(hi_cap) <= want) {
+                while (hi_cap - lo_cap > 1024) {
                     const int64_t mid = (lo_cap + hi_cap) / 2;
-                    (count(mid) <= opt.slots ? hi_cap : lo_cap) = mid;
+                    (estimate(mid) <= want ? hi_cap : lo_cap) = mid;
                 }
             }
             merge(hi_cap, build);

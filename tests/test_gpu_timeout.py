@@ -48,16 +48,15 @@ def test_wait_that_runs_out_reports_timeout_and_poisons_the_context(cfr):
 
 
 def test_kernel_launch_count(cfr):
-    """One eager iteration is a parameter-table launch and L pass launches
-    (per player: the leaf kernel when the game has leaf chunks, the staged
-    bottom-up pass, the top-down pass).  130 iterations = two replays of a
-    64-iteration graph (one table launch and 64 L passes each) and two eager
-    iterations (one table launch for both)."""
+    """One eager iteration is a parameter-table launch and L = 4 pass launches
+    (per player: the staged bottom-up pass and the top-down pass).  130
+    iterations = two replays of a 64-iteration graph (one table launch and
+    64 L passes each) and two eager iterations (one table launch for both)."""
     from paper_2605_14277_b300 import games as G
     one = cfr.Solver(G.poker_game(), passes=2)
     one.iterate(1, "dcfr")
     L = one.kernel_launches() - 1
-    assert L in (4, 5, 6)
+    assert L == 4
     s = cfr.Solver(G.poker_game(), passes=2)
     assert s.kernel_launches() == 0
     s.iterate(130, "dcfr")
