@@ -101,18 +101,15 @@ def profiled_traffic(kernel_slot):
     return None
 
 
-def graph_length(steps, warmup=None, cap=64):
+def graph_length(steps, cap=64):
     """Iterations per CUDA graph for the timed run: the largest k <= cap that
-    divides the step count (the timed region is whole replays) and, when it
-    can, the warm-up count too, so that the warm-up replays the same graph the
-    timed region replays."""
+    divides the step count (the timed region is whole replays).  Each replay
+    starts with a parameter-table refill and cannot overlap the previous
+    replay's last pass (~16 us per replay on the large game), so longer graphs
+    win even when the warm-up cannot replay the same graph (it is captured and
+    uploaded to the device before the warm-up)."""
     steps = max(1, steps)
-    ks = [d for d in range(1, min(cap, steps) + 1) if steps % d == 0]
-    if warmup:
-        both = [d for d in ks if warmup % d == 0]
-        if both and max(both) >= 4:
-            return max(both)
-    return max(ks)
+    return max(d for d in range(1, min(cap, steps) + 1) if steps % d == 0)
 
 
 def alg_bytes(sz):
@@ -433,11 +430,9 @@ def run_ours(args):
     # the product path: the timed steps replay CUDA graphs of k iterations,
     # k = the step count up to 64 (or the largest divisor of it up to 64),
     # captured before the timed region; every k computes the same iterations
-    k_graph = graph_length(args.steps, args.warmup)
+    k_graph = graph_length(args.steps)
     s.set_graph_iterations(k_graph)
     s.prepare_graph(variant)
-    s.iterate(args.warmup, variant)   # untimed warm-up (caches, the first replays' set-up)
-    s.sync()
     props = torch.cuda.get_device_properties(local)
     gpu_id = local
     try:
@@ -446,6 +441,10 @@ def run_ours(args):
         pass
     sampler = ClockSampler(gpu_id)
     sampler.start()
+    # untimed warm-up right before the timed region (caches, clocks up after
+    # the sampler's start-up pause)
+    s.iterate(args.warmup, variant)
+    s.sync()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
