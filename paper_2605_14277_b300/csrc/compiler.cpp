@@ -49,7 +49,9 @@ bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
     g->nodes = n;
     if (n < 1) return fail(err, "empty tree");
     if (t.parent[0] != -1) return fail(err, "node 0 must be the root (parent -1)");
+    // pass 1: node kinds, parents, child counts, infoset ids per player, terminals
     std::vector<int32_t> nch(n, 0);
+    int64_t Jp[2] = {0, 0}, nterm = 0;
     for (int64_t i = 0; i < n; i++) {
         const int k = t.kind[i];
         if (k < 0 || k > 3) return fail(err, "bad node kind at " + std::to_string(i));
@@ -59,56 +61,40 @@ bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
             if (t.kind[q] == K_TERM) return fail(err, "terminal with children at " + std::to_string(q));
             nch[q]++;
         }
-        if ((k == K_P1 || k == K_P2) && t.infoset[i] < 0)
-            return fail(err, "decision node without infoset at " + std::to_string(i));
-        if (k == K_TERM && !std::isfinite(t.payoff[i]))
-            return fail(err, "non-finite payoff at " + std::to_string(i));
-    }
-    for (int64_t i = 0; i < n; i++)
-        if (t.kind[i] != K_TERM && nch[i] == 0)
-            return fail(err, "non-terminal without children at " + std::to_string(i));
-    // action labels 0..nch-1 once each; chance probabilities valid
-    {
-        std::vector<int64_t> coff(n + 1, 0);
-        for (int64_t i = 0; i < n; i++) coff[i + 1] = coff[i] + nch[i];
-        std::vector<uint8_t> seen(n > 1 ? n - 1 : 1, 0);
-        std::vector<double> psum(n, 0.0);
-        for (int64_t i = 1; i < n; i++) {
-            const int64_t q = t.parent[i];
-            const int32_t a = t.action[i];
-            if (a < 0 || a >= nch[q]) return fail(err, "action label out of range at " + std::to_string(i));
-            if (seen[coff[q] + a]) return fail(err, "duplicate action label below " + std::to_string(q));
-            seen[coff[q] + a] = 1;
-            if (t.kind[q] == K_CHANCE) {
-                const double pr = t.chance_prob[i];
-                if (!(pr >= 0.0 && pr <= 1.0)) return fail(err, "bad chance probability at " + std::to_string(i));
-                psum[q] += pr;
-            }
+        if (k == K_P1 || k == K_P2) {
+            if (t.infoset[i] < 0) return fail(err, "decision node without infoset at " + std::to_string(i));
+            Jp[k - 1] = std::max<int64_t>(Jp[k - 1], (int64_t)t.infoset[i] + 1);
+        } else if (k == K_TERM) {
+            if (!std::isfinite(t.payoff[i])) return fail(err, "non-finite payoff at " + std::to_string(i));
+            nterm++;
         }
-        for (int64_t i = 0; i < n; i++)
-            if (t.kind[i] == K_CHANCE && std::fabs(psum[i] - 1.0) > 1e-9)
-                return fail(err, "chance probabilities do not sum to 1 at " + std::to_string(i));
     }
-    // per player infosets and caller sequence numbering
+    for (int p = 0; p < 2; p++) {
+        if (Jp[p] > INT32_MAX / 2) return fail(err, "too many infosets");
+        g->p[p].J = (int32_t)Jp[p];
+        g->p[p].nact.assign(Jp[p], 0);
+        g->p[p].par.assign(Jp[p], INT32_MIN);
+    }
+    // pass 2: every non-terminal has children; each infoset's action count;
+    // the start of each node's action-label slots
+    std::vector<int32_t> coff(n + 1, 0);
+    for (int64_t i = 0; i < n; i++) {
+        const int k = t.kind[i];
+        if (k != K_TERM && nch[i] == 0) return fail(err, "non-terminal without children at " + std::to_string(i));
+        if (k == K_P1 || k == K_P2) {
+            int32_t &na = g->p[k - 1].nact[t.infoset[i]];
+            if (na == 0) na = nch[i];
+            else if (na != nch[i]) return fail(err, "infoset action-count mismatch");
+        }
+        if (coff[i] > INT32_MAX - nch[i]) return fail(err, "too many nodes");
+        coff[i + 1] = coff[i] + nch[i];
+    }
+    // caller sequence numbering
     for (int p = 0; p < 2; p++) {
         PlayerSF &P = g->p[p];
-        const int kp = p + 1;
-        int64_t J = 0;
-        for (int64_t i = 0; i < n; i++)
-            if (t.kind[i] == kp) J = std::max<int64_t>(J, (int64_t)t.infoset[i] + 1);
-        if (J > INT32_MAX / 2) return fail(err, "too many infosets");
-        P.J = (int32_t)J;
-        P.nact.assign(J, 0);
-        P.par.assign(J, INT32_MIN);
-        for (int64_t i = 0; i < n; i++) {
-            if (t.kind[i] != kp) continue;
-            const int32_t j = t.infoset[i];
-            if (P.nact[j] == 0) P.nact[j] = nch[i];
-            else if (P.nact[j] != nch[i]) return fail(err, "infoset action-count mismatch");
-        }
-        P.off.assign(J, 0);
+        P.off.assign(P.J, 0);
         int64_t s = 0;
-        for (int64_t j = 0; j < J; j++) {
+        for (int64_t j = 0; j < P.J; j++) {
             if (P.nact[j] == 0) return fail(err, "infoset ids are not dense");
             P.off[j] = (int32_t)s;
             s += P.nact[j];
@@ -116,20 +102,34 @@ bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
         if (s > INT32_MAX / 2) return fail(err, "too many sequences");
         P.S = (int32_t)s;
     }
-    // own sequence per node (top-down; parents precede children), chance reach
+    // pass 3, top-down (parents precede children): action labels 0..nch-1 once
+    // each; chance probabilities valid (their sums checked once a node's last
+    // child is seen, in the running sum kept per chance node); each node's own
+    // sequence per player and chance reach; perfect recall (all nodes of an
+    // infoset share its parent sequence); terminals
+    std::vector<uint8_t> seen(n > 1 ? n - 1 : 1, 0);
     std::vector<int32_t> seq1(n, -1), seq2(n, -1);
-    std::vector<double> reach(n, 1.0);
-    for (int64_t i = 1; i < n; i++) {
-        const int64_t q = t.parent[i];
-        const int kq = t.kind[q];
-        seq1[i] = (kq == K_P1) ? g->p[0].off[t.infoset[q]] + t.action[i] : seq1[q];
-        seq2[i] = (kq == K_P2) ? g->p[1].off[t.infoset[q]] + t.action[i] : seq2[q];
-        reach[i] = reach[q] * (kq == K_CHANCE ? t.chance_prob[i] : 1.0);
+    std::vector<double> reach(n, 1.0);   // the chance reach, and for a chance node the running sum of its
+    std::vector<double> psum;            // children's probabilities (psum, indexed by chance node rank)
+    std::vector<int32_t> crank;
+    {
+        int64_t nc = 0;
+        for (int64_t i = 0; i < n; i++) nc += t.kind[i] == K_CHANCE;
+        if (nc > 0) {
+            crank.assign(n, -1);
+            psum.assign(nc, 0.0);
+            nc = 0;
+            for (int64_t i = 0; i < n; i++)
+                if (t.kind[i] == K_CHANCE) crank[i] = (int32_t)nc++;
+        }
     }
-    // parent sequence per infoset: all nodes of an infoset must agree (perfect recall)
-    for (int64_t i = 0; i < n; i++) {
+    g->ts1.reserve(nterm);
+    g->ts2.reserve(nterm);
+    g->tw.reserve(nterm);
+    double mn = INFINITY, mx = -INFINITY;
+    auto own_infoset = [&](int64_t i) {
         const int k = t.kind[i];
-        if (k != K_P1 && k != K_P2) continue;
+        if (k != K_P1 && k != K_P2) return true;
         PlayerSF &P = g->p[k - 1];
         const int32_t own = (k == K_P1) ? seq1[i] : seq2[i];
         int32_t &pj = P.par[t.infoset[i]];
@@ -137,7 +137,44 @@ bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
         else if (pj != own)
             return fail(err, "imperfect recall: infoset " + std::to_string(t.infoset[i]) + " of player " +
                                  std::to_string(k) + " has two parent sequences");
+        return true;
+    };
+    if (!own_infoset(0)) return false;
+    if (t.kind[0] == K_TERM) {
+        g->ts1.push_back(-1);
+        g->ts2.push_back(-1);
+        g->tw.push_back(t.payoff[0]);
+        mn = mx = t.payoff[0];
     }
+    for (int64_t i = 1; i < n; i++) {
+        const int64_t q = t.parent[i];
+        const int kq = t.kind[q];
+        const int32_t a = t.action[i];
+        if (a < 0 || a >= nch[q]) return fail(err, "action label out of range at " + std::to_string(i));
+        if (seen[coff[q] + a]) return fail(err, "duplicate action label below " + std::to_string(q));
+        seen[coff[q] + a] = 1;
+        double rq = reach[q];
+        if (kq == K_CHANCE) {
+            const double pr = t.chance_prob[i];
+            if (!(pr >= 0.0 && pr <= 1.0)) return fail(err, "bad chance probability at " + std::to_string(i));
+            psum[crank[q]] += pr;
+            rq *= pr;
+        }
+        reach[i] = rq;
+        seq1[i] = (kq == K_P1) ? g->p[0].off[t.infoset[q]] + a : seq1[q];
+        seq2[i] = (kq == K_P2) ? g->p[1].off[t.infoset[q]] + a : seq2[q];
+        if (!own_infoset(i)) return false;
+        if (t.kind[i] == K_TERM) {
+            g->ts1.push_back(seq1[i]);
+            g->ts2.push_back(seq2[i]);
+            g->tw.push_back(reach[i] * t.payoff[i]);
+            mn = std::min(mn, t.payoff[i]);
+            mx = std::max(mx, t.payoff[i]);
+        }
+    }
+    for (int64_t i = 0; i < n; i++)
+        if (t.kind[i] == K_CHANCE && std::fabs(psum[crank[i]] - 1.0) > 1e-9)
+            return fail(err, "chance probabilities do not sum to 1 at " + std::to_string(i));
     // children of each caller sequence (index 0 = empty sequence), sorted by
     // infoset id; a cycle leaves infosets unreachable, which the forest
     // numbering detects
@@ -149,23 +186,6 @@ bool compile_game(const TreeView &t, GameSF *g, std::string *err) {
         P.kid_inf.assign(P.J, 0);
         std::vector<int32_t> fill(P.kid_ptr.begin(), P.kid_ptr.end() - 1);
         for (int32_t j = 0; j < P.J; j++) P.kid_inf[fill[P.par[j] + 1]++] = j;
-    }
-    // terminals
-    double mn = INFINITY, mx = -INFINITY;
-    {
-        int64_t nt = 0;
-        for (int64_t i = 0; i < n; i++) nt += t.kind[i] == K_TERM;
-        g->ts1.reserve(nt);
-        g->ts2.reserve(nt);
-        g->tw.reserve(nt);
-    }
-    for (int64_t i = 0; i < n; i++) {
-        if (t.kind[i] != K_TERM) continue;
-        g->ts1.push_back(seq1[i]);
-        g->ts2.push_back(seq2[i]);
-        g->tw.push_back(reach[i] * t.payoff[i]);
-        mn = std::min(mn, t.payoff[i]);
-        mx = std::max(mx, t.payoff[i]);
     }
     g->range = g->ts1.empty() ? 0.0 : mx - mn;
     return true;
