@@ -456,15 +456,33 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
         // sorted distinct columns cut wherever two are more than kWinGap
         // apart.  Taken when at most kMaxWin windows together need no more
         // shared memory than per-entry gathers.
-        std::vector<int32_t> cols;
+        std::vector<int32_t> cols, wend;
+        std::vector<int64_t> wbase;
+        std::vector<uint8_t> mark;
         auto windows = [&](int64_t rec, int32_t k, int32_t n0, int32_t n1) {
             const int32_t here = (int32_t)(P.win.size() / 4);
             P.rwin[4 * rec] = P.rwin[4 * rec + 1] = here;
             P.rwin[4 * rec + 2] = (int32_t)work16(n1 - n0, 4);
             if (n1 <= n0) return;
-            cols.assign(P.m_col.begin() + n0, P.m_col.begin() + n1);
-            std::sort(cols.begin(), cols.end());
-            cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+            // the level's distinct columns in order: marked in a table over
+            // their span when that span is small (clustered columns), else sorted
+            int32_t clo = P.m_col[n0], chi = P.m_col[n0];
+            for (int32_t e = n0; e < n1; e++) {
+                clo = std::min(clo, P.m_col[e]);
+                chi = std::max(chi, P.m_col[e]);
+            }
+            const int64_t span = (int64_t)chi - clo + 1;
+            if (span <= 8 * (int64_t)(n1 - n0) + 4096) {
+                mark.assign(span, 0);
+                for (int32_t e = n0; e < n1; e++) mark[P.m_col[e] - clo] = 1;
+                cols.clear();
+                for (int64_t c = 0; c < span; c++)
+                    if (mark[c]) cols.push_back((int32_t)(clo + c));
+            } else {
+                cols.assign(P.m_col.begin() + n0, P.m_col.begin() + n1);
+                std::sort(cols.begin(), cols.end());
+                cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+            }
             std::vector<int32_t> w;
             int64_t bytes = 0;
             int32_t a = cols[0];
@@ -485,12 +503,19 @@ int compile_forest(const TreeView *games, int64_t G, const CompileOptions &opt, 
             }
             P.rwin[4 * rec + 1] = here + (int32_t)nw;
             P.rwin[4 * rec + 2] = (int32_t)bytes;
-            // each entry's float index into the level's x area
+            // each entry's float index into the level's x area: its window is
+            // the first whose end lies past its column (binary search)
+            wend.resize(nw);
+            wbase.resize(nw);
+            for (int64_t q = 0, base = 0; q < nw; q++) {
+                wend[q] = w[2 * q + 1];
+                wbase[q] = base + (w[2 * q] & 3) - w[2 * q];
+                base += span16(w[2 * q + 1] - w[2 * q], 4) / 4;
+            }
             for (int32_t e = n0; e < n1; e++) {
                 const int32_t c = P.m_col[e];
-                int64_t base = 0, q = 0;
-                while (w[2 * q + 1] <= c) base += span16(w[2 * q + 1] - w[2 * q], 4) / 4, q++;
-                P.lcol[e] = (int32_t)(base + (w[2 * q] & 3) + (c - w[2 * q]));
+                const int64_t q = std::upper_bound(wend.begin(), wend.end(), c) - wend.begin();
+                P.lcol[e] = (int32_t)(wbase[q] + c);
             }
         };
         // footprints of the levels [0, below) truncated at `below` (the
