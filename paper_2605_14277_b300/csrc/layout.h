@@ -44,9 +44,9 @@ struct TreeView {
 // the child infosets of its deepest level at the top levels of its child
 // units.  Bottom-up passes take every leaf, then the internal units deepest
 // first, from one queue; an internal unit stages its own arrays at once and
-// starts computing when all its children are done.  The root unit, last,
-// also runs the top-down pass over itself and the internal units, so the
-// top-down pass proper finds every unit's parents' next x ready.
+// starts computing when all its children are done.  The top-down pass works
+// units of its own (dunits below): runs of sibling units, each carrying its
+// ancestor chain, so that no top-down unit depends on another.
 constexpr int kLvl = 6;
 struct Unit {
     int32_t game, lvl0, nlvl, rng;

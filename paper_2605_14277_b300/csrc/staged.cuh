@@ -4,9 +4,11 @@
 // touches, so the producer warp can copy the whole unit into shared memory
 // with bulk asynchronous copies (cp.async.bulk, completion counted in bytes on
 // an mbarrier) before any index is read.  The consumer warps then run the
-// unit's levels out of shared memory and write the results back with
-// coalesced stores.  Two buffers per CTA: the next unit's copies are in
-// flight while the current one is computed, and several CTAs share an SM.
+// unit's levels out of shared memory: the bottom-up steps store their results
+// (r, b, ev) straight to global memory, the top-down pass writes its own
+// levels' x back with coalesced stores.  Two buffers per CTA: the next unit's
+// copies are in flight while the current one is computed, and several CTAs
+// share an SM.
 #pragma once
 #include <cstdint>
 
@@ -453,8 +455,9 @@ __device__ uint32_t issue_down(const DevPlayer &P, const int4 hdr, unsigned char
 
 // Up pass of a staged unit (consumer warps only): gathers of the other
 // player's x, payoff rows, bottom-up values, regret update, variant post-op
-// and next strategy, all in shared memory; then write-back.  An internal
-// unit's deepest level finds its children's ev in the staged child range.
+// and next strategy, all out of shared memory; each step stores its new r, b
+// (and the ev its parent reads) to global memory.  An internal unit's deepest
+// level finds its children's ev in the staged child range.
 constexpr int kRegA = 4;    // infosets with at most kRegA actions keep their values in registers
 
 // shared-memory views of one staged up level
