@@ -113,10 +113,10 @@ struct PlayerLayout {
     std::vector<int32_t> win;           // 4 ints per window
     std::vector<int32_t> lcol;          // [Z]
     std::vector<int32_t> up_queue;      // leaves largest first, then internal units deepest first
-    std::vector<Unit> dunits;           // top-down units: runs of sibling units merged while they
-                                        // fit the buffer and the forest still gets at least as many
-                                        // units as resident CTAs allow in one round (the smallest
-                                        // such cap); parent / nchild / depth in this tree.  Their
+    std::vector<Unit> dunits;           // top-down units: runs of sibling units merged up to the
+                                        // smallest footprint cap (within the buffer) that leaves no
+                                        // more units than CTAs resident at once, so the pass is one
+                                        // round; parent / nchild / depth in this tree.  Their
                                         // range records start with the ancestor chain (flags >>
                                         // kAncShift levels, from level 0 down), then their own levels
     std::vector<int32_t> danc_off;      // [dunits] offset of the unit's ancestors' x in the scratch
