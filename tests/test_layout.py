@@ -394,3 +394,22 @@ def test_x_windows():
     assert n_win >= 0.4 * n_all
     for trees in (small_set(), [G.poker_game()]):
         check_windows(Layout(trees, item_bytes=48 * 1024))
+
+
+def test_top_down_units_fit_one_round_of_ctas(monkeypatch):
+    """The top-down pass's units are independent, so the packer merges them to
+    the smallest footprint that leaves no more units than CTAs resident at
+    once: the large game's top-down pass is then one round (296 CTAs), while
+    each unit still fits its buffer."""
+    monkeypatch.setenv("LAYOUT_PROBE_SLOTS", "296")
+    lay = Layout([G.large_random_game(3)], item_bytes=48 * 1024)
+    for p in (0, 1):
+        d = lay.pl[p]
+        du = d["dunits"]
+        assert len(du) <= 296
+        # not merged further than needed: at least half the CTAs get a unit
+        assert len(du) >= 148
+        for (g, lvl0, nlvl, r0, flags, par, nch, depth) in du:
+            rng = d["ranges"][r0: r0 + 6 * nlvl].reshape(-1, 6)
+            fd = sum(down_bytes(s1 - s0, j1 - j0) for j0, j1, s0, s1, n0, n1 in rng)
+            assert (flags & 1) == 0 or fd <= 48 * 1024
