@@ -165,7 +165,10 @@ constexpr int kAvgU = 4;   // sequences per thread with loads in flight together
 // One chunk's sequences [q0, q1).  UNIFORM: every game has game 0's
 // parameters; otherwise each sequence looks up its game's weight (the
 // sequences of several games are interleaved level by level), all kAvgU
-// lookups of a thread in flight together.
+// lookups of a thread in flight together.  A sequence the player does not
+// reach (x = 0: regret matching gave one of its actions probability 0) adds
+// exactly nothing, so its sums are neither read nor written; most sequences
+// of a large game are such zeros once the regrets have settled.
 template <bool UNIFORM>
 __device__ __forceinline__ void average_chunk(const DevPlayer &P, const DevGames &gm, const IterArgs &ia,
                                               const ItemParams &ip0, int64_t q0, int64_t q1) {
@@ -177,8 +180,12 @@ __device__ __forceinline__ void average_chunk(const DevPlayer &P, const DevGames
         for (int u = 0; u < kAvgU; u++) {
             const int64_t s = min(q + u * (int64_t)blockDim.x, q1 - 1);
             xv[u] = P.x[s];
-            xb[u] = P.xbar[s];
             if (!UNIFORM) gq[u] = P.seq_game[s];
+        }
+#pragma unroll
+        for (int u = 0; u < kAvgU; u++) {
+            const int64_t s = min(q + u * (int64_t)blockDim.x, q1 - 1);
+            xb[u] = xv[u] != 0.f ? P.xbar[s] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kAvgU; u++) {
@@ -194,7 +201,7 @@ __device__ __forceinline__ void average_chunk(const DevPlayer &P, const DevGames
 #pragma unroll
         for (int u = 0; u < kAvgU; u++) {
             const int64_t s = q + u * (int64_t)blockDim.x;
-            if (s < q1 && act[u]) P.xbar[s] = ff_add(xb[u], ff_mul_f(w[u], xv[u]));
+            if (s < q1 && act[u] && xv[u] != 0.f) P.xbar[s] = ff_add(xb[u], ff_mul_f(w[u], xv[u]));
         }
     }
 }
@@ -236,7 +243,8 @@ __device__ void average_pass64(const DevPlayer &P, const DevGames &gm, const Ite
         const int64_t q1 = min((int64_t)S, (c + 1) * kAvgChunk);
         for (int64_t s = c * kAvgChunk + threadIdx.x; s < q1; s += blockDim.x) {
             const ItemParams64 pp = gm.par64[(int64_t)P.seq_game[s] * (kParamSpan + 1) + ia.pslot];
-            if (pp.active) P.xbar64[s] += pp.w * P.x64[s];
+            const double xv = P.x64[s];
+            if (pp.active && xv != 0.0) P.xbar64[s] += pp.w * xv;
         }
     }
 }
