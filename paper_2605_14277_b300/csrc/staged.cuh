@@ -99,12 +99,14 @@ __device__ __forceinline__ void st_release(int32_t *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 // bounded wait for *flag == want (one thread): false (and the error word set)
-// if it does not happen within limit_ns
+// if it does not happen within limit_ns.  The poll interval stays short: only
+// one thread of a waiting CTA polls, and a waiting unit is on the pass's
+// critical path (a longer sleep only delays its wake-up).
 __device__ __forceinline__ bool flag_wait(const int32_t *flag, int want, int32_t *err, uint64_t limit_ns) {
     if (ld_acquire(flag) == want) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t k = 0;; k++) {
-        __nanosleep(k < 16 ? 32 : 256);
+        __nanosleep(32);
         if (ld_acquire(flag) == want) return true;
         if ((k & 15) == 15 && globaltimer() - t0 > limit_ns) break;
     }
