@@ -639,12 +639,18 @@ __device__ bool down_loop(const DevPlayer &P, const DevGames &gm, const IterArgs
             issue_down(P, h0, bufs[0], &S.bar[0], S.lv[0], S.tab[0], S.cmd, kDownOwn | kDownArm, 0);
             if (tid == 0) S.armed[0]++;
         }
-        if (tid == 0) S.nxt = cur < n ? atomicAdd(&P.qdn[0], 1) : n;
+        // the parameter table is written ahead of the passes, never by the
+        // kernel this one may overlap
+        if (tid == 0 && cur < n) S.ip[0] = unit_params(gm, ia, h0.x);
         pdl_wait();
-        if (cur < n) {
-            if (!root_ready(h0.x) && tid == 0) S.err = 1;
-            if (tid == 0) S.ip[0] = unit_params(gm, ia, h0.x);
-        }
+        // With no more units than CTAs every unit is some CTA's first, and a
+        // second claim could only move units onto CTAs that already hold one
+        // (those that started first), leaving others idle: the pass is one
+        // round.  Otherwise the second position is claimed only now, once
+        // every CTA that was resident while the previous kernel ran holds
+        // its first.
+        if (tid == 0) S.nxt = (cur < n && n > (int)gridDim.x) ? atomicAdd(&P.qdn[0], 1) : n;
+        if (cur < n && !root_ready(h0.x) && tid == 0) S.err = 1;
     }
     __syncthreads();
     pdl_trigger();
