@@ -484,3 +484,287 @@ def random_fully_mixed(seed: int, n: int):
     A = B - np.outer(B @ qv - v * ones, qv) / (qv @ qv)
     C = A - np.outer(p, p @ A - v * ones) / (p @ p)
     return C, p, qv, v
+
+
+# ----------------------------------------------------------------------------
+# n-player games (payoff tensors)
+# ----------------------------------------------------------------------------
+#
+# Tree format of ``cfrn_tree_desc`` in include/cfr_nplayer.h (nodes in an order
+# where every parent precedes its children, node 0 is the root):
+#
+# * ``parent``      int32   parent node, -1 for the root
+# * ``kind``        int8    0 chance, 1 decision, 2 terminal
+# * ``actor``       int8    decision nodes: the acting player 0..n-1; -1 otherwise
+# * ``infoset``     int32   decision nodes: infoset id, dense 0..J_i-1 per player; -1 otherwise
+# * ``action``      int32   index of the edge from the parent (0..|A|-1); -1 for the root
+# * ``chance_prob`` float64 probability of the edge from a chance parent, 1.0 otherwise
+# * ``payoff``      float64 [n_nodes, n_players] terminal utilities (0 elsewhere)
+
+N_CHANCE, N_DECISION, N_TERMINAL = 0, 1, 2
+
+
+@dataclass
+class NTree:
+    n_players: int
+    parent: np.ndarray
+    kind: np.ndarray
+    actor: np.ndarray
+    infoset: np.ndarray
+    action: np.ndarray
+    chance_prob: np.ndarray
+    payoff: np.ndarray
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    def __post_init__(self):
+        self.parent = np.ascontiguousarray(self.parent, dtype=np.int32)
+        self.kind = np.ascontiguousarray(self.kind, dtype=np.int8)
+        self.actor = np.ascontiguousarray(self.actor, dtype=np.int8)
+        self.infoset = np.ascontiguousarray(self.infoset, dtype=np.int32)
+        self.action = np.ascontiguousarray(self.action, dtype=np.int32)
+        self.chance_prob = np.ascontiguousarray(self.chance_prob, dtype=np.float64)
+        self.payoff = np.ascontiguousarray(self.payoff, dtype=np.float64).reshape(-1, self.n_players)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.parent.shape[0])
+
+    def n_infosets(self, player: int) -> int:
+        m = (self.kind == N_DECISION) & (self.actor == player)
+        return int(self.infoset[m].max()) + 1 if m.any() else 0
+
+    def payoff_range(self) -> float:
+        t = self.payoff[self.kind == N_TERMINAL]
+        return float(t.max() - t.min()) if t.size else 0.0
+
+    def counts(self) -> dict:
+        k = self.kind
+        out = {"nodes": self.n_nodes, "players": self.n_players, "terminals": int((k == N_TERMINAL).sum()),
+               "chance_nodes": int((k == N_CHANCE).sum()), "decision_nodes": int((k == N_DECISION).sum())}
+        for p in range(self.n_players):
+            out[f"infosets_{p}"] = self.n_infosets(p)
+        return out
+
+
+def nplayer_from_two_player(tree: Tree, n_players: int = 2) -> NTree:
+    """The two-player tree in the n-player format: player 1 is player 0,
+    player 2 is player 1 (payoff -u1); any further players never act and
+    receive 0 (their only sequence is the empty one)."""
+    if n_players < 2:
+        raise ValueError("n_players >= 2")
+    k = tree.kind
+    kind = np.where(k == CHANCE, N_CHANCE, np.where(k == TERMINAL, N_TERMINAL, N_DECISION)).astype(np.int8)
+    actor = np.where(k == P1, 0, np.where(k == P2, 1, -1)).astype(np.int8)
+    pay = np.zeros((tree.n_nodes, n_players))
+    term = k == TERMINAL
+    pay[term, 0] = tree.payoff[term]
+    pay[term, 1] = -tree.payoff[term]
+    return NTree(n_players, tree.parent, kind, actor, tree.infoset, tree.action, tree.chance_prob, pay,
+                 name=(tree.name or "game") + f"_as_{n_players}p", meta=dict(tree.meta))
+
+
+def random_nplayer_game(n_players: int, seed: int, depth: int, chance: dict, actions=(2, 3),
+                        n_classes=2, payoff="normal", zero_sum=True, name="") -> NTree:
+    """Layered random n-player game with perfect recall (the n-player form of
+    ``random_game``): decision levels cycle players 0, 1, ..., n-1, skipping
+    chance levels; each player observes chance event e only through its own
+    partition of the outcomes into classes; all actions are public, and a
+    player's infoset key is (public history, its observed classes).
+
+    payoff: 'normal' (N(0,1) rounded to float32) or 'int2' (integers in
+    [-2, 2]) per player; zero_sum: the last player receives minus the sum of
+    the others' payoffs."""
+    rng = np.random.default_rng(seed)
+    n = n_players
+    partitions = {d: [_random_partition(rng, chance[d], n_classes) for _ in range(n)] for d in sorted(chance)}
+    actions = np.asarray(actions, dtype=np.int64)
+    actor_at, nxt = {}, 0
+    for d in range(depth):
+        if d in chance:
+            continue
+        actor_at[d] = nxt
+        nxt = (nxt + 1) % n
+    pub = np.zeros(1, dtype=np.int64)
+    obs = [np.zeros(1, np.int64) for _ in range(n)]
+    par_l, kind_l, act_l, inf_l, edge_l, cp_l = [], [], [], [], [], []
+    par = np.array([-1], dtype=np.int64)
+    edge = np.array([-1], dtype=np.int64)
+    cp = np.array([1.0])
+    base = 0
+    n_inf = [0] * n
+    term_pay = None
+    for d in range(depth + 1):
+        m = pub.shape[0]
+        par_l.append(par)
+        edge_l.append(edge)
+        cp_l.append(cp)
+        if d == depth:
+            kind_l.append(np.full(m, N_TERMINAL, np.int8))
+            act_l.append(np.full(m, -1, np.int8))
+            inf_l.append(np.full(m, -1, np.int64))
+            if payoff == "normal":
+                pv = rng.standard_normal((m, n)).astype(np.float32).astype(np.float64)
+            elif payoff == "int2":
+                pv = rng.integers(-2, 3, (m, n)).astype(np.float64)
+            else:
+                raise ValueError(payoff)
+            if zero_sum:
+                pv[:, n - 1] = -pv[:, : n - 1].sum(axis=1)
+            term_pay = pv
+            break
+        idx = np.arange(m, dtype=np.int64)
+        if d in chance:
+            k = chance[d]
+            kind_l.append(np.full(m, N_CHANCE, np.int8))
+            act_l.append(np.full(m, -1, np.int8))
+            inf_l.append(np.full(m, -1, np.int64))
+            cpar = np.repeat(idx, k)
+            cedge = np.tile(np.arange(k, dtype=np.int64), m)
+            cpub = pub[cpar]
+            obs = [obs[q][cpar] * 16 + partitions[d][q][cedge] for q in range(n)]
+            cp = np.full(cpar.shape[0], 1.0 / k)
+        else:
+            p = actor_at[d]
+            kind_l.append(np.full(m, N_DECISION, np.int8))
+            act_l.append(np.full(m, p, np.int8))
+            key = pub * 4096 + obs[p]
+            uk, inv = np.unique(key, return_inverse=True)
+            na_inf = rng.choice(actions, size=uk.shape[0])
+            inf_l.append(inv.astype(np.int64) + n_inf[p])
+            n_inf[p] += uk.shape[0]
+            nch = na_inf[inv]
+            cpar = np.repeat(idx, nch)
+            starts = np.cumsum(nch) - nch
+            cedge = np.arange(cpar.shape[0], dtype=np.int64) - np.repeat(starts, nch)
+            _, cpub = np.unique(pub[cpar] * 8 + cedge, return_inverse=True)
+            obs = [obs[q][cpar] for q in range(n)]
+            cp = np.ones(cpar.shape[0])
+        pub = cpub.astype(np.int64)
+        par = cpar + base
+        edge = cedge
+        base += m
+    parent = np.concatenate(par_l)
+    pay = np.zeros((parent.shape[0], n))
+    pay[parent.shape[0] - term_pay.shape[0]:] = term_pay
+    meta = {"seed": seed, "depth": depth, "chance": dict(chance), "players": n}
+    return NTree(n, parent, np.concatenate(kind_l), np.concatenate(act_l), np.concatenate(inf_l),
+                 np.concatenate(edge_l), np.concatenate(cp_l), pay, name=name, meta=meta)
+
+
+def small_nplayer_game(n_players: int = 3, seed: int = 1) -> NTree:
+    """A few hundred nodes: the size the oracle runs in well under a second."""
+    return random_nplayer_game(n_players, seed, depth=2 * n_players, chance={0: 3}, actions=(2, 3),
+                               name=f"small_{n_players}p_s{seed}")
+
+
+def large_nplayer_game(n_players: int = 3, seed: int = 5) -> NTree:
+    """4.84M nodes (3 players): a chance deal of 8 outcomes that each player
+    observes through its own partition into 4 classes, then 14 decision
+    levels of 2-3 actions with the players in turn, and 2.9M terminals with
+    zero-sum N(0,1) payoffs."""
+    return random_nplayer_game(n_players, seed, depth=15, chance={0: 8}, actions=(2, 3), n_classes=4,
+                               name=f"large_{n_players}p_s{seed}")
+
+
+def kuhn3_game(ante: float = 1.0, bet: float = 1.0) -> NTree:
+    """Three-player Kuhn poker: a deck of four ranked cards, one dealt to each
+    player (24 equally likely deals), antes of 1, one betting round in seat
+    order.  Before any bet a player checks (action 0) or bets 1 (action 1);
+    after a bet every other player still to respond, in seat order from the
+    bettor, folds (0) or calls (1).  Among the players who did not fold, the
+    highest card takes the pot.  A player's infoset is its card and the public
+    action history."""
+    n = 3
+    parent, kind, actor, infoset, action, cprob, pay = [], [], [], [], [], [], []
+    inf_ids = [dict() for _ in range(n)]
+
+    def new_node(par, k, who, act, prob):
+        parent.append(par)
+        kind.append(k)
+        actor.append(who)
+        infoset.append(-1)
+        action.append(act)
+        cprob.append(prob)
+        pay.append([0.0] * n)
+        return len(parent) - 1
+
+    deals = [(a, b, c) for a in range(4) for b in range(4) for c in range(4) if len({a, b, c}) == 3]
+    root = new_node(-1, N_CHANCE, -1, -1, 1.0)
+
+    def play(node_par, act, cards, hist, bettor, responded, folded):
+        # hist: public actions so far; bettor: seat that bet (or -1);
+        # responded: seats that answered the bet
+        if bettor < 0:
+            seat = len(hist)
+            if seat == n:   # everyone checked: showdown for the antes
+                return showdown(node_par, act, cards, -1, set())
+        else:
+            order = [(bettor + k) % n for k in range(1, n)]
+            todo = [s for s in order if s not in responded]
+            if not todo:
+                return showdown(node_par, act, cards, bettor, folded)
+            seat = todo[0]
+        node = new_node(node_par, N_DECISION, seat, act, 1.0)
+        key = (cards[seat], tuple(hist))
+        ids = inf_ids[seat]
+        if key not in ids:
+            ids[key] = len(ids)
+        infoset[node] = ids[key]
+        for a in (0, 1):
+            if bettor < 0:
+                play(node, a, cards, hist + [a], seat if a == 1 else -1, set(), set())
+            else:
+                play(node, a, cards, hist + [a], bettor, responded | {seat},
+                     folded | ({seat} if a == 0 else set()))
+        return node
+
+    def showdown(node_par, act, cards, bettor, folded):
+        node = new_node(node_par, N_TERMINAL, -1, act, 1.0)
+        contrib = [ante] * n
+        if bettor >= 0:
+            contrib[bettor] += bet
+            for s in range(n):
+                if s != bettor and s not in folded:
+                    contrib[s] += bet
+        live = [s for s in range(n) if s not in folded]
+        win = max(live, key=lambda s: cards[s])
+        pot = sum(contrib)
+        pay[node] = [(pot if s == win else 0.0) - contrib[s] for s in range(n)]
+        return node
+
+    for k, cards in enumerate(deals):
+        play(root, k, cards, [], -1, set(), set())
+    # the deal's children carry its probability
+    cp = np.asarray(cprob)
+    par = np.asarray(parent)
+    cp[par == root] = 1.0 / len(deals)
+    return NTree(n, par, kind, actor, infoset, action, cp, np.asarray(pay), name="kuhn3")
+
+
+def nplayer_normal_form(tensors, name="normal_form") -> NTree:
+    """An n-player normal-form game as a tree: player 0 moves, then player 1
+    without seeing player 0's action, ..., each player with one infoset;
+    tensors[i][a_0, ..., a_{n-1}] is player i's payoff."""
+    tensors = [np.asarray(t, dtype=np.float64) for t in tensors]
+    n = len(tensors)
+    shape = tensors[0].shape
+    parent, kind, actor, infoset, action = [-1], [N_DECISION], [0], [0], [-1]
+    frontier = [(0, ())]
+    for p in range(n):
+        nxt = []
+        for node, hist in frontier:
+            for a in range(shape[p]):
+                parent.append(node)
+                action.append(a)
+                last = p == n - 1
+                kind.append(N_TERMINAL if last else N_DECISION)
+                actor.append(-1 if last else p + 1)
+                infoset.append(-1 if last else 0)
+                nxt.append((len(parent) - 1, hist + (a,)))
+        frontier = nxt
+    pay = np.zeros((len(parent), n))
+    for node, hist in frontier:
+        pay[node] = [t[hist] for t in tensors]
+    return NTree(n, np.asarray(parent), np.asarray(kind), np.asarray(actor), np.asarray(infoset),
+                 np.asarray(action), np.ones(len(parent)), pay, name=name)
