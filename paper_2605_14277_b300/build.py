@@ -8,9 +8,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcfr.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("capi.cu", "compiler.cpp")]
+SOURCES = [os.path.join(CSRC, f) for f in ("capi.cu", "compiler.cpp", "nplayer.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("kernels.cuh", "staged.cuh", "layout.h")] + [
-    os.path.join(os.path.dirname(HERE), "include", "cfr.h")]
+    os.path.join(os.path.dirname(HERE), "include", "cfr.h"), os.path.join(os.path.dirname(HERE), "include", "cfr_nplayer.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-shared"]

@@ -315,7 +315,7 @@ __device__ __forceinline__ float value_of(const DevPlayer &P, int s) {
     return v;
 }
 
-__device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const ItemParams &ip) {
+__device__ inline void up_infoset_cfr(const DevPlayer &P, int j, int variant, const ItemParams &ip) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     const int na = s1 - s0;
     const bool pred = predictive(variant);
@@ -345,7 +345,7 @@ __device__ void up_infoset_cfr(const DevPlayer &P, int j, int variant, const Ite
 // the bottom-up step in FP64 (precision 64): the same arithmetic as
 // up_infoset_cfr on the FP64 state, with regret matching's division exact
 // (IEEE) and the FP64 parameters
-__device__ void up_infoset_cfr64(const DevPlayer &P, int j, int variant, const ItemParams64 &ip) {
+__device__ inline void up_infoset_cfr64(const DevPlayer &P, int j, int variant, const ItemParams64 &ip) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     const bool pred = predictive(variant);
     double ev = 0.0;
@@ -374,7 +374,7 @@ __device__ void up_infoset_cfr64(const DevPlayer &P, int j, int variant, const I
 }
 
 // best-response step (MODE_BR, FP64): V = u + sum children, ev = max_a V
-__device__ void up_infoset_br(const DevPlayer &P, int j) {
+__device__ inline void up_infoset_br(const DevPlayer &P, int j) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     double best = -INFINITY;
     for (int s = s0; s < s1; s++) {

@@ -1,0 +1,958 @@
+// n-player sequence-form CFR (include/cfr_nplayer.h): the utility step is the
+// contraction of each player's payoff tensor with the other players'
+// sequence-form strategies ("tensor operations in multiplayer settings",
+// Sec. 2.1); every other step is the two-player path's per-infoset arithmetic
+// (kernels.cuh: up_infoset_cfr, up_infoset_br, the float-float sums).
+//
+// Layout per player (host compile below):
+// * the player's decision points numbered level by level (a level's children
+//   are the next level), within a level by parent sequence, then by the
+//   caller's infoset id; sequences numbered by decision point, actions in
+//   order; sequence 0 is the empty one.  So each decision point's sequences
+//   are contiguous (inf_seq), each sequence's child decision points are
+//   contiguous (seq_child) and each level is one range of both.
+// * the payoff tensor as a CSR over the player's sequences: one entry per
+//   terminal with a nonzero payoff for the player, holding pi_c(z) payoff(z)
+//   (FP32 and FP64) and the other players' sequences at z (cols, n-1 per
+//   entry, in player order).
+//
+// Passes per player (one launch each; a level per launch, so the level
+// barrier is the launch boundary and no kernel waits on another):
+//   rows   u[s] = sum_e val[e] prod_k x_k[col_k[e]]      thread per sequence
+//   up     level by level, deepest first: up_infoset_cfr  thread per decision point
+//   avg    xbar += t^gamma x (x = 0 adds nothing: skipped) thread per sequence
+//   down   level by level, from the top: x = x[p_j] b      thread per decision point
+// Iterations are captured as CUDA graphs; the parameters of iteration t come
+// from a table that a kernel fills from a device counter at the graph's start.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cfr_nplayer.h"
+#include "kernels.cuh"
+
+using namespace cfrb;
+
+namespace {
+
+constexpr int kMaxP = CFRN_MAX_PLAYERS;
+constexpr int kThreadsN = 256;
+
+thread_local std::string g_nerr;
+
+int nfail(int status, const std::string &m) {
+    g_nerr = m;
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// host compile
+// ---------------------------------------------------------------------------
+struct NPlayerHost {
+    int32_t J = 0, S = 0;                 // decision points; non-empty sequences
+    std::vector<int32_t> inf_seq;         // [J + 1] first sequence of each decision point
+    std::vector<int32_t> seq_child;       // [S + 2] first child decision point of each sequence
+    std::vector<int32_t> inf_par;         // [J] parent sequence p_j
+    std::vector<int32_t> lvl;             // [L + 1] decision points of each level
+    std::vector<int32_t> caller_inf;      // [J] caller infoset id of each decision point
+    std::vector<int32_t> seq_of_caller;   // [S + 1] sequence of each caller sequence (0 = empty)
+    std::vector<int32_t> m_ptr;           // [S + 2]
+    std::vector<int32_t> m_col;           // [nnz * (n - 1)]
+    std::vector<float> m_val;
+    std::vector<double> m_val64;
+};
+
+struct NGameHost {
+    int n = 0;
+    int64_t nodes = 0;
+    NPlayerHost pl[kMaxP];
+};
+
+std::string at(int64_t i) { return " at node " + std::to_string(i); }
+
+int compile_nplayer(const cfrn_tree_desc &t, NGameHost *g) {
+    const int64_t N = t.n_nodes;
+    const int n = t.n_players;
+    if (n < 2 || n > kMaxP) return nfail(CFR_ERR_INVALID, "n_players must be 2.." + std::to_string(kMaxP));
+    if (N < 1) return nfail(CFR_ERR_INVALID, "empty tree");
+    if (N >= INT32_MAX) return nfail(CFR_ERR_INVALID, "tree too large for 32-bit indices");
+    if (!t.parent || !t.kind || !t.actor || !t.infoset || !t.action || !t.chance_prob || !t.payoff)
+        return nfail(CFR_ERR_ARG, "NULL array in the tree");
+    if (t.parent[0] != -1) return nfail(CFR_ERR_INVALID, "node 0 must be the root (parent -1)");
+    g->n = n;
+    g->nodes = N;
+    // children per node, action-index checks, infoset sizes
+    std::vector<int32_t> nch(N, 0);
+    std::vector<uint8_t> seen;   // per child slot
+    int32_t J[kMaxP] = {0};
+    for (int64_t i = 0; i < N; i++) {
+        const int k = t.kind[i];
+        if (k < 0 || k > 2) return nfail(CFR_ERR_INVALID, "bad node kind" + at(i));
+        if (k == CFRN_DECISION) {
+            const int a = t.actor[i];
+            if (a < 0 || a >= n) return nfail(CFR_ERR_INVALID, "bad actor" + at(i));
+            if (t.infoset[i] < 0) return nfail(CFR_ERR_INVALID, "negative infoset id" + at(i));
+            J[a] = std::max(J[a], t.infoset[i] + 1);
+        }
+        if (i > 0) {
+            const int64_t q = t.parent[i];
+            if (q < 0 || q >= i) return nfail(CFR_ERR_INVALID, "parent must precede child" + at(i));
+            if (t.kind[q] == CFRN_TERMINAL) return nfail(CFR_ERR_INVALID, "terminal with children" + at(q));
+            nch[q]++;
+        }
+    }
+    // action indices 0..nch-1 exactly once per parent
+    {
+        std::vector<int64_t> first(N + 1, 0);
+        for (int64_t i = 0; i < N; i++) first[i + 1] = first[i] + nch[i];
+        seen.assign(first[N], 0);
+        for (int64_t i = 1; i < N; i++) {
+            const int64_t q = t.parent[i];
+            const int32_t a = t.action[i];
+            if (a < 0 || a >= nch[q]) return nfail(CFR_ERR_INVALID, "action index out of range" + at(i));
+            if (seen[first[q] + a]) return nfail(CFR_ERR_INVALID, "duplicate action index" + at(i));
+            seen[first[q] + a] = 1;
+        }
+    }
+    std::vector<double> psum(N, 0.0);
+    for (int64_t i = 1; i < N; i++)
+        if (t.kind[t.parent[i]] == CFRN_CHANCE) {
+            const double p = t.chance_prob[i];
+            if (!(p >= 0.0 && p <= 1.0)) return nfail(CFR_ERR_INVALID, "chance probability outside [0, 1]" + at(i));
+            psum[t.parent[i]] += p;
+        }
+    for (int64_t i = 0; i < N; i++) {
+        if (t.kind[i] != CFRN_TERMINAL && nch[i] == 0) return nfail(CFR_ERR_INVALID, "non-terminal leaf" + at(i));
+        if (t.kind[i] == CFRN_CHANCE && std::fabs(psum[i] - 1.0) > 1e-9)
+            return nfail(CFR_ERR_INVALID, "chance probabilities do not sum to 1" + at(i));
+    }
+    // actions per infoset (every node of an infoset has the same count)
+    std::vector<int32_t> nact[kMaxP], coff[kMaxP];
+    for (int p = 0; p < n; p++) nact[p].assign(J[p], -1);
+    for (int64_t i = 0; i < N; i++)
+        if (t.kind[i] == CFRN_DECISION) {
+            int32_t &na = nact[t.actor[i]][t.infoset[i]];
+            if (na >= 0 && na != nch[i]) return nfail(CFR_ERR_INVALID, "infoset action counts differ" + at(i));
+            na = nch[i];
+        }
+    int32_t Sc[kMaxP];
+    for (int p = 0; p < n; p++) {
+        coff[p].assign(J[p], 0);
+        int64_t s = 1;
+        for (int32_t j = 0; j < J[p]; j++) {
+            if (nact[p][j] < 0) return nfail(CFR_ERR_INVALID, "player " + std::to_string(p) + ": infoset id " +
+                                                                  std::to_string(j) + " has no node (ids must be dense)");
+            coff[p][j] = (int32_t)s;
+            s += nact[p][j];
+        }
+        if (s >= INT32_MAX) return nfail(CFR_ERR_INVALID, "too many sequences");
+        Sc[p] = (int32_t)(s - 1);
+    }
+    // each node's current caller sequence of every player, chance reach,
+    // parent caller sequence and level of every infoset (perfect recall)
+    std::vector<int32_t> seq((size_t)N * n, 0);
+    std::vector<double> reach(N, 1.0);
+    std::vector<int32_t> ipar[kMaxP], ilev[kMaxP], iown[kMaxP];
+    for (int p = 0; p < n; p++) {
+        ipar[p].assign(J[p], -1);
+        ilev[p].assign(J[p], -1);
+    }
+    // decision point owning each caller sequence (for levels)
+    for (int p = 0; p < n; p++) {
+        iown[p].assign((size_t)Sc[p] + 1, -1);
+        for (int32_t j = 0; j < J[p]; j++)
+            for (int32_t a = 0; a < nact[p][j]; a++) iown[p][coff[p][j] + a] = j;
+    }
+    for (int64_t i = 0; i < N; i++) {
+        if (i > 0) {
+            const int64_t q = t.parent[i];
+            std::memcpy(&seq[(size_t)i * n], &seq[(size_t)q * n], sizeof(int32_t) * n);
+            reach[i] = reach[q];
+            if (t.kind[q] == CFRN_DECISION) seq[(size_t)i * n + t.actor[q]] = coff[t.actor[q]][t.infoset[q]] + t.action[i];
+            else if (t.kind[q] == CFRN_CHANCE) reach[i] *= t.chance_prob[i];
+        }
+        if (t.kind[i] == CFRN_DECISION) {
+            const int p = t.actor[i];
+            const int32_t j = t.infoset[i], s = seq[(size_t)i * n + p];
+            if (ipar[p][j] < 0) {
+                ipar[p][j] = s;
+                ilev[p][j] = s == 0 ? 0 : ilev[p][iown[p][s]] + 1;
+            } else if (ipar[p][j] != s) {
+                return nfail(CFR_ERR_INVALID, "imperfect recall: infoset " + std::to_string(j) + " of player " +
+                                                  std::to_string(p) + " is reached through different own histories" + at(i));
+            }
+        }
+    }
+    // per player: level-by-level numbering
+    for (int p = 0; p < n; p++) {
+        NPlayerHost &P = g->pl[p];
+        P.J = J[p];
+        P.S = Sc[p];
+        int L = 0;
+        for (int32_t j = 0; j < J[p]; j++) L = std::max(L, ilev[p][j] + 1);
+        std::vector<std::vector<int32_t>> bylev(L);
+        for (int32_t j = 0; j < J[p]; j++) bylev[ilev[p][j]].push_back(j);
+        P.seq_of_caller.assign((size_t)Sc[p] + 1, 0);
+        P.caller_inf.clear();
+        P.inf_seq.assign(1, 1);
+        P.inf_par.clear();
+        P.lvl.assign(1, 0);
+        int32_t snext = 1;
+        for (int l = 0; l < L; l++) {
+            std::vector<int32_t> &v = bylev[l];
+            // by parent sequence (already numbered: one level up), then caller id
+            std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) {
+                const int32_t pa = P.seq_of_caller[ipar[p][a]], pb = P.seq_of_caller[ipar[p][b]];
+                return pa != pb ? pa < pb : a < b;
+            });
+            for (int32_t j : v) {
+                P.caller_inf.push_back(j);
+                P.inf_par.push_back(P.seq_of_caller[ipar[p][j]]);
+                for (int32_t a = 0; a < nact[p][j]; a++) P.seq_of_caller[coff[p][j] + a] = snext + a;
+                snext += nact[p][j];
+                P.inf_seq.push_back(snext);
+            }
+            P.lvl.push_back((int32_t)P.caller_inf.size());
+        }
+        // child decision points of each sequence: contiguous, in sequence order
+        P.seq_child.assign((size_t)P.S + 2, 0);
+        for (int32_t j = 0; j < P.J; j++) P.seq_child[P.inf_par[j] + 1]++;
+        for (int64_t s = 0; s < (int64_t)P.S + 1; s++) P.seq_child[s + 1] += P.seq_child[s];
+        // (the numbering puts them in that order: check it)
+        for (int32_t j = 1; j < P.J; j++)
+            if (P.inf_par[j] < P.inf_par[j - 1]) return nfail(CFR_ERR_INVALID, "internal: child order");
+    }
+    // payoff tensors: one CSR per player over its sequences
+    std::vector<int64_t> term;
+    for (int64_t i = 0; i < N; i++)
+        if (t.kind[i] == CFRN_TERMINAL) term.push_back(i);
+    for (int p = 0; p < n; p++) {
+        NPlayerHost &P = g->pl[p];
+        std::vector<int32_t> cnt((size_t)P.S + 2, 0);
+        for (int64_t z : term)
+            if (t.payoff[(size_t)z * n + p] != 0.0 && reach[z] != 0.0)
+                cnt[P.seq_of_caller[seq[(size_t)z * n + p]] + 1]++;
+        for (int64_t s = 0; s < (int64_t)P.S + 1; s++) cnt[s + 1] += cnt[s];
+        P.m_ptr = cnt;
+        const int64_t nnz = cnt[P.S + 1];
+        if (nnz * (n - 1) >= INT32_MAX) return nfail(CFR_ERR_INVALID, "payoff tensor too large");
+        P.m_col.assign((size_t)nnz * (n - 1), 0);
+        P.m_val.assign(nnz, 0.f);
+        P.m_val64.assign(nnz, 0.0);
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t z : term) {
+            const double v = t.payoff[(size_t)z * n + p] * reach[z];
+            if (t.payoff[(size_t)z * n + p] == 0.0 || reach[z] == 0.0) continue;
+            const int32_t e = fill[P.seq_of_caller[seq[(size_t)z * n + p]]]++;
+            P.m_val64[e] = v;
+            P.m_val[e] = (float)v;
+            int c = 0;
+            for (int k = 0; k < n; k++)
+                if (k != p) P.m_col[(size_t)e * (n - 1) + c++] = g->pl[k].seq_of_caller[seq[(size_t)z * n + k]];
+        }
+    }
+    return CFR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// device passes
+// ---------------------------------------------------------------------------
+namespace {
+
+struct NX {
+    const float *x[kMaxP - 1];      // the other players' x, in player order
+};
+struct NX64 {
+    const double *x[kMaxP - 1];
+};
+
+// u[s] = sum_e val[e] * prod_k x_k[col_k[e]] for the player's sequences s
+// (the payoff tensor contracted with the other players' strategies, Sec. 2.1):
+// one thread per sequence, each product taken left to right from val in
+// player order and the products added in entry (terminal) order, so the result
+// does not depend on the launch shape.  NO: the other players' count.
+template <int NO>
+__global__ void __launch_bounds__(kThreadsN) k_np_rows(const int32_t *__restrict__ m_ptr, const int32_t *__restrict__ m_col,
+                                                       const float *__restrict__ m_val, NX xs, int S1,
+                                                       float *__restrict__ u) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S1) return;
+    const int e0 = m_ptr[s], e1 = m_ptr[s + 1];
+    float acc = 0.f;
+    for (int e = e0; e < e1; e++) {
+        float v = m_val[e];
+        const int32_t *c = m_col + (int64_t)e * NO;
+#pragma unroll
+        for (int k = 0; k < NO; k++) v = __fmul_rn(v, __ldg(xs.x[k] + c[k]));
+        acc = __fadd_rn(acc, v);
+    }
+    u[s] = acc;
+}
+
+// the same in FP64 for the best responses (the others' normalised averages)
+template <int NO>
+__global__ void __launch_bounds__(kThreadsN) k_np_rows64(const int32_t *__restrict__ m_ptr, const int32_t *__restrict__ m_col,
+                                                         const double *__restrict__ m_val, NX64 xs, int S1,
+                                                         double *__restrict__ u) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S1) return;
+    const int e0 = m_ptr[s], e1 = m_ptr[s + 1];
+    double acc = 0.0;
+    for (int e = e0; e < e1; e++) {
+        double v = m_val[e];
+        const int32_t *c = m_col + (int64_t)e * NO;
+#pragma unroll
+        for (int k = 0; k < NO; k++) v *= __ldg(xs.x[k] + c[k]);
+        acc += v;
+    }
+    u[s] = acc;
+}
+
+// one level of ObserveUtility + NextStrategy (Alg. 1/2 with the variant's
+// post-op): the two-player path's per-infoset step on this player's arrays
+__global__ void __launch_bounds__(kThreadsN) k_np_up(DevPlayer P, int j0, int j1, int variant,
+                                                     const ItemParams *__restrict__ par, int slot) {
+    const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= j1) return;
+    const ItemParams ip = par[slot];
+    up_infoset_cfr(P, j, variant, ip);
+}
+
+// xbar += t^gamma x over the player's sequences (the empty one included);
+// a sequence with x = 0 adds exactly nothing and is skipped
+__global__ void __launch_bounds__(kThreadsN) k_np_avg(float2 *__restrict__ xbar, const float *__restrict__ x, int S1,
+                                                      const ItemParams *__restrict__ par, int slot) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S1) return;
+    const float xv = x[s];
+    if (xv != 0.f) xbar[s] = ff_add(xbar[s], ff_mul_f(par[slot].w, xv));
+}
+
+// one level of the sequence form, top-down: x[(j,a)] = x[p_j] b_j[a]
+__global__ void __launch_bounds__(kThreadsN) k_np_down(const int32_t *__restrict__ inf_seq,
+                                                       const int32_t *__restrict__ inf_par,
+                                                       const float *__restrict__ b, float *__restrict__ x, int j0,
+                                                       int j1) {
+    const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= j1) return;
+    const float xp = x[inf_par[j]];
+    for (int s = inf_seq[j]; s < inf_seq[j + 1]; s++) x[s] = __fmul_rn(xp, b[s]);
+}
+
+// initial behavioural strategy: uniform at every decision point
+__global__ void k_np_uniform(const int32_t *__restrict__ inf_seq, float *__restrict__ b, int J) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    const int s0 = inf_seq[j], s1 = inf_seq[j + 1];
+    const float p = uniform_prob(s1 - s0);
+    for (int s = s0; s < s1; s++) b[s] = p;
+}
+
+// parameters of iterations t0+1 .. t0+k (t0 read from the device counter):
+// t^gamma; DCFR's t^alpha/(t^alpha+1) and t^beta/(t^beta+1)
+__global__ void k_np_params(ItemParams *__restrict__ par, const int32_t *__restrict__ t_dev, int k, int variant,
+                            double alpha, double beta, double gamma) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k) return;
+    const int32_t t = *t_dev + s + 1;
+    const double td = (double)t;
+    ItemParams ip;
+    ip.t = t;
+    ip.active = 1;
+    ip.w = ff_from_double(pow(td, gamma));
+    if (variant == VAR_DCFR) {
+        const double ta = pow(td, alpha), tb = pow(td, beta);
+        ip.fpos = ff_from_double(ta / (ta + 1.0));
+        ip.fneg = ff_from_double(tb / (tb + 1.0));
+    } else {
+        ip.fpos = make_float2(1.f, 0.f);
+        ip.fneg = make_float2(1.f, 0.f);
+    }
+    par[s] = ip;
+}
+__global__ void k_np_tick(int32_t *t_dev, int k) { *t_dev += k; }
+
+// the player's normalised average xbar / xbar[empty] (the current x before
+// any iteration), FP64
+__global__ void __launch_bounds__(kThreadsN) k_np_avgnorm(const float2 *__restrict__ xbar, const float *__restrict__ x,
+                                                          double *__restrict__ x64, int S1) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S1) return;
+    const double d0 = (double)xbar[0].x + (double)xbar[0].y;
+    x64[s] = d0 > 0.0 ? ((double)xbar[s].x + (double)xbar[s].y) / d0 : (double)x[s];
+}
+
+// one level of the best response: ev = max_a V
+__global__ void __launch_bounds__(kThreadsN) k_np_br(DevPlayer P, int j0, int j1) {
+    const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < j1) up_infoset_br(P, j);
+}
+
+// out[0] = <x, u> (the player's value against the others), out[1] = its best
+// response's value u[empty] + sum of the top decision points' ev.  One CTA:
+// strided partial sums per thread, then a fixed tree, so the order is fixed.
+__global__ void __launch_bounds__(kThreadsN) k_np_value(const double *__restrict__ x64, const double *__restrict__ u64,
+                                                        int S1, const int32_t *__restrict__ seq_child,
+                                                        const double *__restrict__ ev64, double *__restrict__ out) {
+    __shared__ double part[kThreadsN];
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < S1; s += blockDim.x) acc += x64[s] * u64[s];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = part[0];
+        double br = u64[0];
+        for (int c = seq_child[0]; c < seq_child[1]; c++) br += ev64[c];
+        out[1] = br;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kParamCap = 1024;   // iterations per graph at most (parameter table)
+
+struct NDev {
+    int32_t J = 0, S = 0, L = 0;
+    int64_t nnz = 0;
+    std::vector<int32_t> lvl;     // host copy: decision points of each level
+    int32_t *inf_seq = nullptr, *seq_child = nullptr, *inf_par = nullptr, *m_ptr = nullptr, *m_col = nullptr;
+    float *m_val = nullptr;
+    double *m_val64 = nullptr;
+    float2 *r = nullptr, *xbar = nullptr;
+    float *b = nullptr, *x = nullptr, *u = nullptr, *ev = nullptr, *uq = nullptr;
+    double *u64 = nullptr, *ev64 = nullptr, *x64 = nullptr;
+    DevPlayer dp{};
+};
+
+unsigned blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kThreadsN - 1) / kThreadsN); }
+
+}  // namespace
+
+struct cfrn_ctx {
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    NDev P[kMaxP];
+    NGameHost host;
+    ItemParams *par = nullptr;
+    int32_t *t_dev = nullptr;
+    double *out = nullptr;              // [2 * kMaxP] values and best responses
+    int64_t t = 0;
+    int graph_k = 64;
+    cudaGraphExec_t graph = nullptr;
+    int g_variant = -1, g_alt = -1, g_k = 0;
+    double g_a = 0, g_b = 0, g_g = 0;
+    int64_t launches = 0;               // kernels run (graph replays count theirs)
+    int64_t graph_kernels = 0;          // kernels in the current graph
+    bool capturing = false;
+    bool own_stream = false;
+    int64_t captured = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+#define NCU(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return nfail(CFR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int dalloc(cfrn_ctx *c, T **p, int64_t n) {
+    *p = nullptr;
+    void *q = nullptr;
+    NCU(cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T)));
+    c->allocs.push_back(q);
+    *p = (T *)q;
+    return CFR_OK;
+}
+template <class T>
+int dput(cfrn_ctx *c, T **p, const std::vector<T> &v) {
+    int rc = dalloc(c, p, (int64_t)v.size());
+    if (rc) return rc;
+    if (!v.empty()) NCU(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return CFR_OK;
+}
+
+void counted(cfrn_ctx *c, int k = 1) {
+    if (c->capturing) c->captured += k;
+    else c->launches += k;
+}
+
+int rows(cfrn_ctx *c, int i, float *out) {
+    NDev &P = c->P[i];
+    NX xs{};
+    int k = 0;
+    for (int q = 0; q < c->n; q++)
+        if (q != i) xs.x[k++] = c->P[q].x;
+    const int S1 = P.S + 1;
+    const unsigned g = blocks(S1);
+    cudaStream_t st = c->stream;
+    switch (c->n - 1) {
+    case 1: k_np_rows<1><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 2: k_np_rows<2><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 3: k_np_rows<3><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 4: k_np_rows<4><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 5: k_np_rows<5><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 6: k_np_rows<6><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    default: k_np_rows<7><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    }
+    counted(c);
+    return CFR_OK;
+}
+
+int rows64(cfrn_ctx *c, int i) {
+    NDev &P = c->P[i];
+    NX64 xs{};
+    int k = 0;
+    for (int q = 0; q < c->n; q++)
+        if (q != i) xs.x[k++] = c->P[q].x64;
+    const int S1 = P.S + 1;
+    const unsigned g = blocks(S1);
+    cudaStream_t st = c->stream;
+    switch (c->n - 1) {
+    case 1: k_np_rows64<1><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    case 2: k_np_rows64<2><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    case 3: k_np_rows64<3><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    case 4: k_np_rows64<4><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    case 5: k_np_rows64<5><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    case 6: k_np_rows64<6><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    default: k_np_rows64<7><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val64, xs, S1, P.u64); break;
+    }
+    counted(c);
+    return CFR_OK;
+}
+
+void up(cfrn_ctx *c, int i, int variant, int slot) {
+    NDev &P = c->P[i];
+    for (int l = P.L - 1; l >= 0; l--) {
+        const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
+        k_np_up<<<blocks(j1 - j0), kThreadsN, 0, c->stream>>>(P.dp, j0, j1, variant, c->par, slot);
+        counted(c);
+    }
+}
+
+void avg(cfrn_ctx *c, int i, int slot) {
+    NDev &P = c->P[i];
+    k_np_avg<<<blocks(P.S + 1), kThreadsN, 0, c->stream>>>(P.xbar, P.x, P.S + 1, c->par, slot);
+    counted(c);
+}
+
+void down(cfrn_ctx *c, int i) {
+    NDev &P = c->P[i];
+    for (int l = 0; l < P.L; l++) {
+        const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
+        k_np_down<<<blocks(j1 - j0), kThreadsN, 0, c->stream>>>(P.inf_seq, P.inf_par, P.b, P.x, j0, j1);
+        counted(c);
+    }
+}
+
+void params(cfrn_ctx *c, int k, int variant, double a, double b, double g) {
+    k_np_params<<<blocks(k), kThreadsN, 0, c->stream>>>(c->par, c->t_dev, k, variant, a, b, g);
+    counted(c);
+}
+void tick(cfrn_ctx *c, int k) {
+    k_np_tick<<<1, 1, 0, c->stream>>>(c->t_dev, k);
+    counted(c);
+}
+
+// one iteration (parameters in slot `slot` of the table).  ev: optional
+// events around each kind of pass, [4][2 * n] (start, end per player).
+int iteration(cfrn_ctx *c, int slot, int variant, bool alternating, cudaEvent_t (*ev)[2 * kMaxP] = nullptr) {
+    auto mark = [&](int kind, int i, int end) {
+        if (ev) cudaEventRecord(ev[kind][2 * i + end], c->stream);
+    };
+    if (!alternating)
+        for (int i = 0; i < c->n; i++) {
+            mark(0, i, 0);
+            if (int rc = rows(c, i, c->P[i].u)) return rc;
+            mark(0, i, 1);
+        }
+    for (int i = 0; i < c->n; i++) {
+        if (alternating) {
+            mark(0, i, 0);
+            if (int rc = rows(c, i, c->P[i].u)) return rc;
+            mark(0, i, 1);
+        }
+        mark(1, i, 0);
+        up(c, i, variant, slot);
+        mark(1, i, 1);
+        mark(2, i, 0);
+        avg(c, i, slot);
+        mark(2, i, 1);
+        mark(3, i, 0);
+        down(c, i);
+        mark(3, i, 1);
+    }
+    return CFR_OK;
+}
+
+int run_block(cfrn_ctx *c, int k, int variant, double a, double b, double g, bool alternating) {
+    params(c, k, variant, a, b, g);
+    for (int s = 0; s < k; s++)
+        if (int rc = iteration(c, s, variant, alternating)) return rc;
+    tick(c, k);
+    NCU(cudaGetLastError());
+    return CFR_OK;
+}
+
+int ensure_graph(cfrn_ctx *c, int k, int variant, double a, double b, double g, bool alternating) {
+    if (c->graph && c->g_k == k && c->g_variant == variant && c->g_alt == (int)alternating && c->g_a == a &&
+        c->g_b == b && c->g_g == g)
+        return CFR_OK;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    NCU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->captured = 0;
+    int rc = run_block(c, k, variant, a, b, g, alternating);
+    c->capturing = false;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
+    if (rc) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+    }
+    if (e != cudaSuccess) return nfail(CFR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return nfail(CFR_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    NCU(cudaGraphUpload(c->graph, c->stream));
+    c->graph_kernels = c->captured;
+    c->g_k = k;
+    c->g_variant = variant;
+    c->g_alt = (int)alternating;
+    c->g_a = a;
+    c->g_b = b;
+    c->g_g = g;
+    return CFR_OK;
+}
+
+void free_ctx(cfrn_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int check_player(const cfrn_ctx *c, int p) {
+    if (!c) return nfail(CFR_ERR_ARG, "NULL context");
+    if (p < 0 || p >= c->n) return nfail(CFR_ERR_ARG, "player outside 0..n-1");
+    return CFR_OK;
+}
+
+int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
+    if (!tree || !out) return nfail(CFR_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    cfrn_ctx *c = new cfrn_ctx();
+    int rc = compile_nplayer(*tree, &c->host);
+    auto bail = [&](int r) {
+        free_ctx(c);
+        return r;
+    };
+    if (rc) return bail(rc);
+    // a stream of its own unless one is given (graphs cannot be captured on
+    // the legacy default stream)
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(nfail(CFR_ERR_CUDA, "stream creation failed"));
+        c->own_stream = true;
+    }
+    c->n = c->host.n;
+    for (int p = 0; p < c->n; p++) {
+        NPlayerHost &H = c->host.pl[p];
+        NDev &P = c->P[p];
+        P.J = H.J;
+        P.S = H.S;
+        P.L = (int)H.lvl.size() - 1;
+        P.lvl = H.lvl;
+        P.nnz = (int64_t)H.m_val.size();
+        const int64_t S1 = (int64_t)P.S + 1;
+        if ((rc = dput(c, &P.inf_seq, H.inf_seq)) || (rc = dput(c, &P.seq_child, H.seq_child)) ||
+            (rc = dput(c, &P.inf_par, H.inf_par)) || (rc = dput(c, &P.m_ptr, H.m_ptr)) ||
+            (rc = dput(c, &P.m_col, H.m_col)) || (rc = dput(c, &P.m_val, H.m_val)) ||
+            (rc = dput(c, &P.m_val64, H.m_val64)) || (rc = dalloc(c, &P.r, S1)) || (rc = dalloc(c, &P.xbar, S1)) ||
+            (rc = dalloc(c, &P.b, S1)) || (rc = dalloc(c, &P.x, S1)) || (rc = dalloc(c, &P.u, S1)) ||
+            (rc = dalloc(c, &P.uq, S1)) || (rc = dalloc(c, &P.ev, P.J)) || (rc = dalloc(c, &P.u64, S1)) ||
+            (rc = dalloc(c, &P.ev64, P.J)) || (rc = dalloc(c, &P.x64, S1)))
+            return bail(rc);
+        DevPlayer &d = P.dp;
+        d.inf_seq = P.inf_seq;
+        d.seq_child = P.seq_child;
+        d.inf_par = P.inf_par;
+        d.r = P.r;
+        d.b = P.b;
+        d.x = P.x;
+        d.xbar = P.xbar;
+        d.u = P.u;
+        d.ev = P.ev;
+        d.u64 = P.u64;
+        d.ev64 = P.ev64;
+        d.S = (int32_t)S1;
+        d.G = 1;
+        if (cudaMemsetAsync(P.r, 0, S1 * sizeof(float2), c->stream) != cudaSuccess ||
+            cudaMemsetAsync(P.xbar, 0, S1 * sizeof(float2), c->stream) != cudaSuccess ||
+            cudaMemsetAsync(P.b, 0, S1 * sizeof(float), c->stream) != cudaSuccess ||
+            cudaMemsetAsync(P.x, 0, S1 * sizeof(float), c->stream) != cudaSuccess)
+            return bail(nfail(CFR_ERR_CUDA, "initialising the state"));
+        static const float one = 1.0f;
+        if (cudaMemcpyAsync(P.x, &one, sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return bail(nfail(CFR_ERR_CUDA, "initialising x"));
+        if (P.J > 0) k_np_uniform<<<blocks(P.J), kThreadsN, 0, c->stream>>>(P.inf_seq, P.b, P.J);
+        counted(c);
+    }
+    if ((rc = dalloc(c, &c->par, kParamCap)) || (rc = dalloc(c, &c->t_dev, 1)) || (rc = dalloc(c, &c->out, 2 * kMaxP)))
+        return bail(rc);
+    if (cudaMemsetAsync(c->t_dev, 0, sizeof(int32_t), c->stream) != cudaSuccess)
+        return bail(nfail(CFR_ERR_CUDA, "initialising t"));
+    for (int p = 0; p < c->n; p++) down(c, p);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return bail(nfail(CFR_ERR_CUDA, "initial strategies"));
+    // the host copies of the layout are kept for the state read-back
+    for (int p = 0; p < c->n; p++) {
+        NPlayerHost &H = c->host.pl[p];
+        std::vector<int32_t>().swap(H.m_ptr);
+        std::vector<int32_t>().swap(H.m_col);
+        std::vector<float>().swap(H.m_val);
+        std::vector<double>().swap(H.m_val64);
+    }
+    *out = c;
+    return CFR_OK;
+}
+
+// caller numbering: caller sequence c (1..S) of player p is sequence
+// seq_of_caller[c]; arrays of S entries skip the empty sequence
+template <class T, class F>
+void to_caller(const NPlayerHost &H, const std::vector<T> &dev, double *dst, bool with_empty, F conv) {
+    const int64_t S = H.S;
+    if (with_empty) dst[0] = conv(dev[0]);
+    for (int64_t k = 1; k <= S; k++) dst[with_empty ? k : k - 1] = conv(dev[H.seq_of_caller[k]]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int cfrn_load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) { return load(tree, stream, out); }
+
+int cfrn_free(cfrn_ctx *ctx) {
+    free_ctx(ctx);
+    return CFR_OK;
+}
+
+const char *cfrn_last_error(void) { return g_nerr.c_str(); }
+
+int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out) {
+    if (int rc = check_player(ctx, player)) return rc;
+    if (!out) return nfail(CFR_ERR_ARG, "NULL output");
+    const NDev &P = ctx->P[player];
+    out[0] = P.J;
+    out[1] = P.S;
+    out[2] = P.L;
+    out[3] = P.nnz;
+    out[4] = ctx->n;
+    out[5] = ctx->t;
+    return CFR_OK;
+}
+
+int cfrn_set_graph_iterations(cfrn_ctx *ctx, int k) {
+    if (!ctx) return nfail(CFR_ERR_ARG, "NULL context");
+    if (k < 1 || k > kParamCap) return nfail(CFR_ERR_ARG, "graph iterations must be 1..1024");
+    ctx->graph_k = k;
+    return CFR_OK;
+}
+
+int cfrn_iterate(cfrn_ctx *ctx, int64_t n, int variant, double alpha, double beta, double gamma, int alternating) {
+    if (!ctx) return nfail(CFR_ERR_ARG, "NULL context");
+    if (n < 0 || variant < 0 || variant > 4) return nfail(CFR_ERR_ARG, "bad iteration count or variant");
+    if (ctx->t + n >= INT32_MAX) return nfail(CFR_ERR_ARG, "iteration counter would overflow");
+    const bool alt = alternating != 0;
+    while (n > 0) {
+        const int K = ctx->graph_k;
+        if (K > 1 && n >= K) {
+            if (int rc = ensure_graph(ctx, K, variant, alpha, beta, gamma, alt)) return rc;
+            NCU(cudaGraphLaunch(ctx->graph, ctx->stream));
+            ctx->launches += ctx->graph_kernels;
+            ctx->t += K;
+            n -= K;
+        } else {
+            const int k = (int)std::min<int64_t>(n, K);
+            if (int rc = run_block(ctx, k, variant, alpha, beta, gamma, alt)) return rc;
+            ctx->t += k;
+            n -= k;
+        }
+    }
+    return CFR_OK;
+}
+
+int cfrn_sync(cfrn_ctx *ctx) {
+    if (!ctx) return nfail(CFR_ERR_ARG, "NULL context");
+    NCU(cudaStreamSynchronize(ctx->stream));
+    NCU(cudaGetLastError());
+    return CFR_OK;
+}
+
+int cfrn_get_state(cfrn_ctx *ctx, int player, double *r, double *b, double *xbar, int64_t *t) {
+    if (int rc = check_player(ctx, player)) return rc;
+    if (int rc = cfrn_sync(ctx)) return rc;
+    const NDev &P = ctx->P[player];
+    const NPlayerHost &H = ctx->host.pl[player];
+    const int64_t S1 = (int64_t)P.S + 1;
+    auto ff = [](float2 v) { return (double)v.x + (double)v.y; };
+    auto fl = [](float v) { return (double)v; };
+    if (r) {
+        std::vector<float2> h(S1);
+        NCU(cudaMemcpy(h.data(), P.r, S1 * sizeof(float2), cudaMemcpyDeviceToHost));
+        to_caller(H, h, r, false, ff);
+    }
+    if (b) {
+        std::vector<float> h(S1);
+        NCU(cudaMemcpy(h.data(), P.b, S1 * sizeof(float), cudaMemcpyDeviceToHost));
+        to_caller(H, h, b, false, fl);
+    }
+    if (xbar) {
+        std::vector<float2> h(S1);
+        NCU(cudaMemcpy(h.data(), P.xbar, S1 * sizeof(float2), cudaMemcpyDeviceToHost));
+        to_caller(H, h, xbar, true, ff);
+    }
+    if (t) *t = ctx->t;
+    return CFR_OK;
+}
+
+int cfrn_get_values(cfrn_ctx *ctx, int player, double *x, double *u) {
+    if (int rc = check_player(ctx, player)) return rc;
+    const NDev &P = ctx->P[player];
+    const NPlayerHost &H = ctx->host.pl[player];
+    const int64_t S1 = (int64_t)P.S + 1;
+    auto fl = [](float v) { return (double)v; };
+    if (u) {
+        if (int rc = rows(ctx, player, P.uq)) return rc;
+    }
+    if (int rc = cfrn_sync(ctx)) return rc;
+    std::vector<float> h(S1);
+    if (x) {
+        NCU(cudaMemcpy(h.data(), P.x, S1 * sizeof(float), cudaMemcpyDeviceToHost));
+        to_caller(H, h, x, true, fl);
+    }
+    if (u) {
+        NCU(cudaMemcpy(h.data(), P.uq, S1 * sizeof(float), cudaMemcpyDeviceToHost));
+        to_caller(H, h, u, true, fl);
+    }
+    return CFR_OK;
+}
+
+int cfrn_get_average_strategy(cfrn_ctx *ctx, int player, double *out, int64_t len) {
+    if (int rc = check_player(ctx, player)) return rc;
+    const NPlayerHost &H = ctx->host.pl[player];
+    if (!out || len != H.S) return nfail(CFR_ERR_ARG, "output length must be S_p");
+    std::vector<double> xb((size_t)H.S + 1);
+    if (int rc = cfrn_get_state(ctx, player, nullptr, nullptr, xb.data(), nullptr)) return rc;
+    // xbar in the caller numbering: decision point j's parent sequence in
+    // that numbering is read through the layout's maps
+    std::vector<int32_t> caller_of_seq((size_t)H.S + 1, 0);
+    for (int32_t k = 1; k <= H.S; k++) caller_of_seq[H.seq_of_caller[k]] = k;
+    for (int32_t j = 0; j < H.J; j++) {
+        const int32_t s0 = H.inf_seq[j], s1 = H.inf_seq[j + 1];
+        const double d = xb[caller_of_seq[H.inf_par[j]]];
+        for (int32_t s = s0; s < s1; s++) {
+            const int32_t k = caller_of_seq[s];
+            out[k - 1] = d > 0.0 ? xb[k] / d : 1.0 / (double)(s1 - s0);
+        }
+    }
+    return CFR_OK;
+}
+
+int cfrn_nash_conv(cfrn_ctx *ctx, double *nash_conv, double *gains) {
+    if (!ctx || !nash_conv) return nfail(CFR_ERR_ARG, "NULL argument");
+    for (int p = 0; p < ctx->n; p++) {
+        NDev &P = ctx->P[p];
+        k_np_avgnorm<<<blocks(P.S + 1), kThreadsN, 0, ctx->stream>>>(P.xbar, P.x, P.x64, P.S + 1);
+        counted(ctx);
+    }
+    for (int i = 0; i < ctx->n; i++) {
+        NDev &P = ctx->P[i];
+        if (int rc = rows64(ctx, i)) return rc;
+        for (int l = P.L - 1; l >= 0; l--) {
+            const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
+            k_np_br<<<blocks(j1 - j0), kThreadsN, 0, ctx->stream>>>(P.dp, j0, j1);
+            counted(ctx);
+        }
+        k_np_value<<<1, kThreadsN, 0, ctx->stream>>>(P.x64, P.u64, P.S + 1, P.seq_child, P.ev64, ctx->out + 2 * i);
+        counted(ctx);
+    }
+    NCU(cudaGetLastError());
+    double h[2 * kMaxP];
+    NCU(cudaMemcpyAsync(h, ctx->out, sizeof(double) * 2 * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    NCU(cudaStreamSynchronize(ctx->stream));
+    double sum = 0.0;
+    for (int i = 0; i < ctx->n; i++) {
+        const double g = h[2 * i + 1] - h[2 * i];
+        if (gains) gains[i] = g;
+        sum += g;
+    }
+    *nash_conv = sum;
+    return CFR_OK;
+}
+
+int cfrn_time_passes(cfrn_ctx *ctx, int iters, int variant, double alpha, double beta, double gamma, int alternating,
+                     double *us) {
+    if (!ctx || !us) return nfail(CFR_ERR_ARG, "NULL argument");
+    if (iters < 1 || variant < 0 || variant > 4) return nfail(CFR_ERR_ARG, "bad iteration count or variant");
+    cudaEvent_t ev[4][2 * kMaxP];
+    for (auto &row : ev)
+        for (auto &e : row) NCU(cudaEventCreate(&e));
+    double acc[4] = {0, 0, 0, 0};
+    int rc = CFR_OK;
+    for (int it = 0; it < iters && rc == CFR_OK; it++) {
+        params(ctx, 1, variant, alpha, beta, gamma);
+        rc = iteration(ctx, 0, variant, alternating != 0, ev);
+        tick(ctx, 1);
+        ctx->t += 1;
+        if (rc == CFR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = nfail(CFR_ERR_CUDA, "timing run");
+        for (int k = 0; k < 4 && rc == CFR_OK; k++)
+            for (int i = 0; i < ctx->n; i++) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[k][2 * i], ev[k][2 * i + 1]);
+                acc[k] += ms;
+            }
+    }
+    for (auto &row : ev)
+        for (auto &e : row) cudaEventDestroy(e);
+    if (rc) return rc;
+    for (int k = 0; k < 4; k++) us[k] = acc[k] * 1e3 / iters;
+    return CFR_OK;
+}
+
+int64_t cfrn_launches(const cfrn_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -9,13 +9,15 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "cfr.h")
+HEADER_N = os.path.join(ROOT, "include", "cfr_nplayer.h")
 LIB = os.path.join(ROOT, "paper_2605_14277_b300", "libcfr.so")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER, prefix="cfr_"):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)   # drop comments
-    names = re.findall(r"^\s*(?:int|void|const\s+char\s*\*)\s*\*?\s*(cfr_\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:int|int64_t|void|const\s+char\s*\*)\s*\*?\s*(" + prefix + r"\w+)\s*\(", text,
+                       flags=re.M)
     return sorted(set(names))
 
 
@@ -39,6 +41,55 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_function(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert missing == []
+
+
+def test_nplayer_header_and_exports(lib):
+    names = declared_functions(HEADER_N, "cfrn_")
+    for want in ("cfrn_load", "cfrn_iterate", "cfrn_get_state", "cfrn_get_values", "cfrn_nash_conv",
+                 "cfrn_get_average_strategy", "cfrn_free", "cfrn_time_passes", "cfrn_launches"):
+        assert want in names
+    assert [n for n in names if not hasattr(lib, n)] == []
+
+
+def test_nplayer_calls_that_need_no_device(lib):
+    """Invalid trees and arguments are refused before any device work."""
+    import numpy as np
+    from paper_2605_14277_b300 import games as G
+    from paper_2605_14277_b300 import nplayer as NP
+    from paper_2605_14277_b300.cfr import CFRError
+    NP.lib()
+    t = G.kuhn3_game()
+    cases = []
+    bad = G.kuhn3_game(); bad.parent[5] = 7; cases.append((bad, "parent must precede child at node 5"))
+    bad = G.kuhn3_game(); bad.actor[1] = 3; cases.append((bad, "bad actor at node 1"))
+    bad = G.kuhn3_game(); bad.kind[3] = 5; cases.append((bad, "bad node kind at node 3"))
+    bad = G.kuhn3_game()
+    bad.chance_prob[bad.parent == 0] *= 0.5
+    cases.append((bad, "chance probabilities do not sum to 1 at node 0"))
+    bad = G.kuhn3_game(); bad.action[2] = bad.action[3] if bad.parent[2] == bad.parent[3] else 9
+    cases.append((bad, "action index"))
+    bad = G.kuhn3_game()
+    dec = np.flatnonzero(bad.kind == G.N_DECISION)
+    bad.infoset[dec[dec > 30][0]] = 40        # a hole in the ids of that player
+    cases.append((bad, "has no node (ids must be dense)"))
+    two = G.nplayer_from_two_player(G.small_random_game(1), 2)
+    two.n_players = 9
+    cases.append((two, "n_players must be 2..8"))
+    for tree, msg in cases:
+        with pytest.raises(CFRError) as ei:
+            NP.NSolver(tree)
+        assert ei.value.status == -1 and msg in str(ei.value), str(ei.value)
+    # imperfect recall: two nodes of one infoset reached through different own actions
+    bad = G.kuhn3_game()
+    p0 = np.flatnonzero((bad.kind == G.N_DECISION) & (bad.actor == 0))
+    again = p0[bad.parent[p0] != 0][0]          # seat 0 acting a second time (after its own check)
+    bad.infoset[again] = bad.infoset[p0[0]]     # merged with a first-action infoset
+    with pytest.raises(CFRError) as ei:
+        NP.NSolver(bad)
+    assert ei.value.status == -1 and "imperfect recall" in str(ei.value)
+    assert NP.lib().cfrn_sizes(None, 0, None) == -6
+    assert NP.lib().cfrn_iterate(None, 1, 0, 0.0, 0.0, 0.0, 1) == -6
+    assert NP.lib().cfrn_set_graph_iterations(None, 4) == -6
 
 
 def test_calls_that_need_no_device(lib):
