@@ -383,6 +383,8 @@ def run_reference(args):
         return run_reference_batch(args)
     if args.workload == "serve":
         return run_reference_serve(args)
+    if args.workload == "nplayer":
+        return run_reference_nplayer(args)
     tree, variant = workload(args.workload, args.variant)
     # the oracle is sequential: the host's cores each run their own copy of
     # the game (spawned processes), and the job's rate is their sum
@@ -868,6 +870,201 @@ def run_serve(args):
     return 0
 
 
+NP_METRIC = "node-updates/s per CFR iteration (DCFR, three-player game, payoff tensors)"
+
+
+def nplayer_alg_bytes(sizes):
+    """Algorithmic bytes of one n-player iteration, per kind of pass, summed
+    over the players (S_i sequences with the empty one, J_i decision points,
+    Z_i tensor entries of player i; each array element counted once):
+
+    rows(i): 4 (S_i + 1) row pointers + Z_i (4 value + 4 (n - 1) columns)
+             + 4 (S_k + 1) for every other player's x (each entry once)
+             + 4 (S_i + 1) u written
+    up(i):   per sequence 4 u + 8 + 8 regret read and written + 4 + 4
+             strategy read and written + 4 child pointers; per decision point
+             4 segment start + 4 ev written + 4 ev read by its parent
+    avg(i):  per sequence 4 x + 8 + 8 average sums read and written
+    down(i): per sequence 4 b + 4 x written; per decision point 4 parent,
+             4 segment start, 4 parent's x
+    """
+    n = len(sizes)
+    S = [z["S"] + 1 for z in sizes]
+    out = {"rows": 0, "up": 0, "avg": 0, "down": 0}
+    for i, z in enumerate(sizes):
+        out["rows"] += 8 * S[i] + z["nnz"] * 4 * n + 4 * sum(S[k] for k in range(n) if k != i)
+        out["up"] += 32 * S[i] + 12 * z["J"]
+        out["avg"] += 20 * S[i]
+        out["down"] += 8 * S[i] + 12 * z["J"]
+    return out
+
+
+NP_KERNELS = {"rows": "k_np_rows", "up": "k_np_up", "avg": "k_np_avg", "down": "k_np_down"}
+
+
+def run_nplayer(args):
+    """The n-player row: the 4.84M-node three-player game (payoff tensors)
+    under DCFR, node-updates/s over the timed CUDA-graph iterations."""
+    import torch
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2605_14277_b300 import nplayer as NP
+    tree = G.large_nplayer_game(3)
+    variant = args.variant or "dcfr"
+    stream = torch.cuda.Stream()
+    s = NP.NSolver(tree, stream=stream)
+    sizes = [s.size(i) for i in range(tree.n_players)]
+    k_graph = graph_length(args.steps)
+    s.set_graph_iterations(k_graph)
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    s.iterate(args.warmup, variant)
+    s.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n0 = s.launches
+    e0.record(stream)
+    s.iterate(args.steps, variant)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    n_launch = s.launches - n0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    value = sum_over_ranks(tree.n_nodes * args.steps, dist) / (ms * 1e-3)
+    # per kind of pass: CUDA events around its launches (eager, same stream)
+    us = s.time_passes(max(10, min(200, args.steps // 10)), variant)
+    kb = nplayer_alg_bytes(sizes)
+    hbm, src = peaks()
+    dom = max(us, key=lambda k: us[k])
+    achieved = kb[dom] / (us[dom] * 1e-6) / 1e9
+    iter_bytes = sum(kb.values())
+    if rank == 0:
+        e2e_iters = min(args.e2e_iters, 2000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = NP.NSolver(tree, stream=stream)
+        s2.set_graph_iterations(64)
+        s2.iterate(e2e_iters, variant)
+        nc, gains = s2.nash_conv()
+        avgs = [s2.average_strategy(i) for i in range(tree.n_players)]
+        el = time.perf_counter() - t0
+        s2.close()
+        h2d = sum(a.nbytes for a in (tree.parent, tree.kind, tree.actor, tree.infoset, tree.action,
+                                     tree.chance_prob, tree.payoff))
+        d2h = sum(a.nbytes for a in avgs) + 8 * (1 + tree.n_players)
+        e2e = {"value": tree.n_nodes * e2e_iters / el, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_iters,
+               "d2h_bytes_per_step": d2h / e2e_iters, "iterations": e2e_iters, "seconds": el, "nash_conv": nc,
+               "what": "NSolver(host tree) + iterate + NashConv + average strategies, wall clock"}
+        cpu = parity = None
+        if world == 1 and not args.no_cpu:
+            cpu, parity = nplayer_cpu_leg(tree, variant, s, args.cpu_budget)
+        line = {
+            "metric": NP_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 passes, f32+f32 (Kahan) accumulators, f64 NashConv",
+            "data": "synthetic",
+            "config": {"workload": tree.name, "nodes": tree.n_nodes, "players": tree.n_players,
+                       "terminals": int((tree.kind == G.N_TERMINAL).sum()),
+                       "variant": variant + "(1.5,0,2)" if variant == "dcfr" else variant, "updates": "alternating",
+                       "S": [z["S"] for z in sizes], "J": [z["J"] for z in sizes], "nnz": [z["nnz"] for z in sizes],
+                       "levels": [z["levels"] for z in sizes],
+                       "l2": "inputs larger than L2: tensors and state of about 0.3 GB resident vs 126 MiB L2",
+                       "parallelism": f"replicas x{world}", "cuda_graph_iterations": k_graph},
+            "gpu_launches": n_launch,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": f"{NP_KERNELS[dom]} (all its launches of one iteration)",
+                         "alg_bytes_per_iteration": kb[dom], "us_per_iteration": us[dom],
+                         "per_kind": {k: {"alg_bytes": kb[k], "us": us[k],
+                                          "frac": kb[k] / (us[k] * 1e-6) / 1e9 / hbm} for k in us},
+                         "peak_source": src},
+            "iteration": {"alg_bytes": iter_bytes, "alg_GBps": iter_bytes / (ms / args.steps * 1e-3) / 1e9,
+                          "frac_of_peak": iter_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm},
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def nplayer_cpu_leg(tree, variant, s, budget_s):
+    """The n-player oracle on the host: its rate on a bounded number of
+    iterations of the full game, and the timed run's parity (both sides'
+    FP64 NashConv of the GPU's averages)."""
+    from oracle.nplayer import NOracle
+    from paper_2605_14277_b300.cfr import DEFAULT_PARAMS, VARIANTS
+    v = VARIANTS[variant]
+    a, b, g = DEFAULT_PARAMS[v]
+    o = NOracle(tree)
+    t0 = time.perf_counter()
+    o.iterate(1, v, a, b, g)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(50, budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    o.iterate(n, v, a, b, g)
+    el = time.perf_counter() - t0
+    model, nproc = cpu_info()
+    cpu = {"value": tree.n_nodes * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} {variant} iterations of the full {tree.n_nodes}-node game (after 1 untimed), "
+                     "one process (numpy)", "cpu_model": model, "nproc": nproc}
+    for i in range(tree.n_players):
+        st = s.get_state(i)
+        o.r[i][1:] = st["r"]
+        o.b[i][1:] = st["b"]
+        o.xbar[i] = st["xbar"].copy()
+        o.t = st["t"]
+    nc_g, _ = s.nash_conv()
+    nc_o, _ = o.nash_conv()
+    parity = {"t": o.t, "nash_conv": nc_g, "oracle_nash_conv": nc_o,
+              "nash_conv_rel_diff": abs(nc_g - nc_o) / max(abs(nc_o), 1e-300),
+              "what": "FP64 NashConv of the GPU's averages on both sides"}
+    return cpu, parity
+
+
+def run_reference_nplayer(args):
+    """The n-player oracle as it stands, on the same game and metric."""
+    from oracle.nplayer import NOracle
+    from paper_2605_14277_b300.cfr import DEFAULT_PARAMS, VARIANTS
+    tree = G.large_nplayer_game(3)
+    variant = args.variant or "dcfr"
+    v = VARIANTS[variant]
+    a, b, g = DEFAULT_PARAMS[v]
+    o = NOracle(tree)
+    o.iterate(max(1, min(args.warmup, 1)), v, a, b, g)
+    t0 = time.perf_counter()
+    k = 0
+    while k < args.steps and time.perf_counter() - t0 < 60.0:
+        o.iterate(1, v, a, b, g)
+        k += 1
+    el = time.perf_counter() - t0
+    value = tree.n_nodes * k / el
+    model, nproc = cpu_info()
+    sample = f"{k} of {args.steps} requested {variant} iterations of the full {tree.n_nodes}-node game, one process"
+    line = {"metric": NP_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": tree.name, "nodes": tree.n_nodes, "players": tree.n_players, "variant": variant},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": model, "nproc": nproc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
 def cpu_baseline_batch(trees, variant, budget_s=15.0):
     """The FP64 oracle, single-threaded, on a bounded sample of the batch."""
     from oracle.oracle import Oracle
@@ -892,7 +1089,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "poker", "small", "batch", "serve"])
+    ap.add_argument("--workload", default="large", choices=["large", "poker", "small", "batch", "serve", "nplayer"])
     ap.add_argument("--variant", default=None, choices=["cfr", "cfr+", "dcfr", "pcfr+", "pcfr"],
                     help="regret minimiser for the single-game workloads (default: the workload's own)")
     ap.add_argument("--serve-rate", type=float, default=1000.0)
@@ -927,6 +1124,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "nplayer":
+        return run_nplayer(args)
     return run_ours(args)
 
 

@@ -22,6 +22,7 @@
 //   up     level by level, deepest first: up_infoset_cfr  thread per decision point
 //   avg    xbar += t^gamma x (x = 0 adds nothing: skipped) thread per sequence
 //   down   level by level, from the top: x = x[p_j] b      thread per decision point
+// The kernels are launched with programmatic dependent launch (np_enter).
 // Iterations are captured as CUDA graphs; the parameters of iteration t come
 // from a table that a kernel fills from a device counter at the graph's start.
 #include <algorithm>
@@ -268,6 +269,15 @@ int compile_nplayer(const cfrn_tree_desc &t, NGameHost *g) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// Programmatic dependent launch: each of an iteration's kernels is launched
+// so that it may be scheduled as soon as the previous one completes, before
+// that one's memory flush; it waits, first thing, until the previous
+// kernel's writes are visible.  The previous kernel does not trigger its
+// dependents early: the level grids run several waves, and CTAs of the next
+// kernel resident early would take SM slots from the current one's later
+// waves (measured slower).
+__device__ __forceinline__ void np_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 struct NX {
     const float *x[kMaxP - 1];      // the other players' x, in player order
 };
@@ -284,6 +294,7 @@ template <int NO>
 __global__ void __launch_bounds__(kThreadsN) k_np_rows(const int32_t *__restrict__ m_ptr, const int32_t *__restrict__ m_col,
                                                        const float *__restrict__ m_val, NX xs, int S1,
                                                        float *__restrict__ u) {
+    np_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S1) return;
     const int e0 = m_ptr[s], e1 = m_ptr[s + 1];
@@ -321,6 +332,7 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows64(const int32_t *__restri
 // post-op): the two-player path's per-infoset step on this player's arrays
 __global__ void __launch_bounds__(kThreadsN) k_np_up(DevPlayer P, int j0, int j1, int variant,
                                                      const ItemParams *__restrict__ par, int slot) {
+    np_enter();
     const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= j1) return;
     const ItemParams ip = par[slot];
@@ -331,6 +343,7 @@ __global__ void __launch_bounds__(kThreadsN) k_np_up(DevPlayer P, int j0, int j1
 // a sequence with x = 0 adds exactly nothing and is skipped
 __global__ void __launch_bounds__(kThreadsN) k_np_avg(float2 *__restrict__ xbar, const float *__restrict__ x, int S1,
                                                       const ItemParams *__restrict__ par, int slot) {
+    np_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S1) return;
     const float xv = x[s];
@@ -342,6 +355,7 @@ __global__ void __launch_bounds__(kThreadsN) k_np_down(const int32_t *__restrict
                                                        const int32_t *__restrict__ inf_par,
                                                        const float *__restrict__ b, float *__restrict__ x, int j0,
                                                        int j1) {
+    np_enter();
     const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= j1) return;
     const float xp = x[inf_par[j]];
@@ -361,6 +375,7 @@ __global__ void k_np_uniform(const int32_t *__restrict__ inf_seq, float *__restr
 // t^gamma; DCFR's t^alpha/(t^alpha+1) and t^beta/(t^beta+1)
 __global__ void k_np_params(ItemParams *__restrict__ par, const int32_t *__restrict__ t_dev, int k, int variant,
                             double alpha, double beta, double gamma) {
+    np_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k) return;
     const int32_t t = *t_dev + s + 1;
@@ -379,7 +394,10 @@ __global__ void k_np_params(ItemParams *__restrict__ par, const int32_t *__restr
     }
     par[s] = ip;
 }
-__global__ void k_np_tick(int32_t *t_dev, int k) { *t_dev += k; }
+__global__ void k_np_tick(int32_t *t_dev, int k) {
+    np_enter();
+    *t_dev += k;
+}
 
 // the player's normalised average xbar / xbar[empty] (the current x before
 // any iteration), FP64
@@ -492,6 +510,22 @@ int dput(cfrn_ctx *c, T **p, const std::vector<T> &v) {
     return CFR_OK;
 }
 
+// launch a pass kernel with programmatic dependent launch (np_enter)
+template <class... P, class... A>
+cudaError_t np_launch(void (*fn)(P...), unsigned grid, cudaStream_t st, A &&...a) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3((unsigned)kThreadsN);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, std::forward<A>(a)...);
+}
+
 void counted(cfrn_ctx *c, int k = 1) {
     if (c->capturing) c->captured += k;
     else c->launches += k;
@@ -506,15 +540,17 @@ int rows(cfrn_ctx *c, int i, float *out) {
     const int S1 = P.S + 1;
     const unsigned g = blocks(S1);
     cudaStream_t st = c->stream;
+    cudaError_t e = cudaSuccess;
     switch (c->n - 1) {
-    case 1: k_np_rows<1><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 2: k_np_rows<2><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 3: k_np_rows<3><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 4: k_np_rows<4><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 5: k_np_rows<5><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 6: k_np_rows<6><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    default: k_np_rows<7><<<g, kThreadsN, 0, st>>>(P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 1: e = np_launch(k_np_rows<1>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 2: e = np_launch(k_np_rows<2>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 3: e = np_launch(k_np_rows<3>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 4: e = np_launch(k_np_rows<4>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 5: e = np_launch(k_np_rows<5>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 6: e = np_launch(k_np_rows<6>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    default: e = np_launch(k_np_rows<7>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
     }
+    if (e != cudaSuccess) return nfail(CFR_ERR_CUDA, std::string("rows launch: ") + cudaGetErrorString(e));
     counted(c);
     return CFR_OK;
 }
@@ -545,14 +581,15 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
     NDev &P = c->P[i];
     for (int l = P.L - 1; l >= 0; l--) {
         const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
-        k_np_up<<<blocks(j1 - j0), kThreadsN, 0, c->stream>>>(P.dp, j0, j1, variant, c->par, slot);
+        np_launch(k_np_up, blocks(j1 - j0), c->stream, P.dp, j0, j1, variant, (const ItemParams *)c->par, slot);
         counted(c);
     }
 }
 
 void avg(cfrn_ctx *c, int i, int slot) {
     NDev &P = c->P[i];
-    k_np_avg<<<blocks(P.S + 1), kThreadsN, 0, c->stream>>>(P.xbar, P.x, P.S + 1, c->par, slot);
+    np_launch(k_np_avg, blocks(P.S + 1), c->stream, P.xbar, (const float *)P.x, P.S + 1, (const ItemParams *)c->par,
+              slot);
     counted(c);
 }
 
@@ -560,17 +597,18 @@ void down(cfrn_ctx *c, int i) {
     NDev &P = c->P[i];
     for (int l = 0; l < P.L; l++) {
         const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
-        k_np_down<<<blocks(j1 - j0), kThreadsN, 0, c->stream>>>(P.inf_seq, P.inf_par, P.b, P.x, j0, j1);
+        np_launch(k_np_down, blocks(j1 - j0), c->stream, (const int32_t *)P.inf_seq, (const int32_t *)P.inf_par,
+                  (const float *)P.b, P.x, j0, j1);
         counted(c);
     }
 }
 
 void params(cfrn_ctx *c, int k, int variant, double a, double b, double g) {
-    k_np_params<<<blocks(k), kThreadsN, 0, c->stream>>>(c->par, c->t_dev, k, variant, a, b, g);
+    np_launch(k_np_params, blocks(k), c->stream, c->par, (const int32_t *)c->t_dev, k, variant, a, b, g);
     counted(c);
 }
 void tick(cfrn_ctx *c, int k) {
-    k_np_tick<<<1, 1, 0, c->stream>>>(c->t_dev, k);
+    np_launch(k_np_tick, 1u, c->stream, c->t_dev, k);
     counted(c);
 }
 
