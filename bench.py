@@ -899,7 +899,7 @@ def nplayer_alg_bytes(sizes):
     return out
 
 
-NP_KERNELS = {"rows": "k_np_rows", "up": "k_np_up", "avg": "k_np_avg", "down": "k_np_down"}
+NP_KERNELS = {"rows": "k_np_rows", "up": "k_np_up2", "avg": "k_np_avg", "down": "k_np_down"}
 
 
 def run_nplayer(args):

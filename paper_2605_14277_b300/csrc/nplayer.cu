@@ -2,7 +2,8 @@
 // contraction of each player's payoff tensor with the other players'
 // sequence-form strategies ("tensor operations in multiplayer settings",
 // Sec. 2.1); every other step is the two-player path's per-infoset arithmetic
-// (kernels.cuh: up_infoset_cfr, up_infoset_br, the float-float sums).
+// (kernels.cuh: up_infoset_cfr's, with its loads issued together; up_infoset_br;
+// the float-float sums).
 //
 // Layout per player (host compile below):
 // * the player's decision points numbered level by level (a level's children
@@ -19,7 +20,7 @@
 // Passes per player (one launch each; a level per launch, so the level
 // barrier is the launch boundary and no kernel waits on another):
 //   rows   u[s] = sum_e val[e] prod_k x_k[col_k[e]]      thread per sequence
-//   up     level by level, deepest first: up_infoset_cfr  thread per decision point
+//   up     level by level, deepest first: np_up_step      thread per decision point
 //   avg    xbar += t^gamma x (x = 0 adds nothing: skipped) thread per sequence
 //   down   level by level, from the top: x = x[p_j] b      thread per decision point
 // The kernels are launched with programmatic dependent launch (np_enter).
@@ -328,15 +329,86 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows64(const int32_t *__restri
     u[s] = acc;
 }
 
-// one level of ObserveUtility + NextStrategy (Alg. 1/2 with the variant's
-// post-op): the two-player path's per-infoset step on this player's arrays
-__global__ void __launch_bounds__(kThreadsN) k_np_up(DevPlayer P, int j0, int j1, int variant,
-                                                     const ItemParams *__restrict__ par, int slot) {
+// One level of ObserveUtility + NextStrategy (Alg. 1/2 with the variant's
+// post-op): the two-player path's per-infoset step (up_infoset_cfr), for a
+// decision point of at most kNpA actions with its loads issued together: u, b, r and the child pointers of all its sequences at
+// once, then the children's ev (contiguous across its sequences) eight at a
+// time, each added to its own sequence's V in child order.  The arithmetic is
+// up_infoset_cfr's, in the same order (V = u + children left to right;
+// ev = fma chain over the actions; r, the post-op, regret matching), so the
+// results are identical.  Wider decision points take up_infoset_cfr.
+constexpr int kNpA = 4;
+template <int VAR>
+__device__ __forceinline__ void np_up_step(const DevPlayer &P, int j, const ItemParams &ip) {
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    const int na = s1 - s0;
+    if (na > kNpA) {
+        up_infoset_cfr(P, j, VAR, ip);
+        return;
+    }
+    float uv[kNpA], bv[kNpA];
+    float2 rv[kNpA];
+    int cb[kNpA + 1];
+#pragma unroll
+    for (int a = 0; a < kNpA; a++)
+        if (a < na) {
+            uv[a] = P.u[s0 + a];
+            bv[a] = P.b[s0 + a];
+            rv[a] = P.r[s0 + a];
+        }
+#pragma unroll
+    for (int a = 0; a <= kNpA; a++)
+        if (a <= na) cb[a] = P.seq_child[s0 + a];
+    // the children's ev, eight loads in flight; child c belongs to the
+    // action a with cb[a] <= c < cb[a+1]
+    const int c0 = cb[0], c1 = cb[na];
+    for (int c = c0; c < c1; c += 8) {
+        float e[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) e[k] = __ldcg(&P.ev[min(c + k, c1 - 1)]);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int cc = c + k;
+            if (cc < c1) {
+#pragma unroll
+                for (int a = 0; a < kNpA; a++)
+                    if (a < na && cc >= cb[a] && cc < cb[a + 1]) uv[a] += e[k];
+            }
+        }
+    }
+    float ev = 0.f;
+#pragma unroll
+    for (int a = 0; a < kNpA; a++)
+        if (a < na) ev = fmaf(bv[a], uv[a], ev);
+    P.ev[j] = ev;
+    const bool pred = predictive(VAR);
+    float pos = 0.f, q[kNpA];
+#pragma unroll
+    for (int a = 0; a < kNpA; a++)
+        if (a < na) {
+            const float d = uv[a] - ev;
+            float2 r = ff_add_f(rv[a], d);
+            r = post_op_v<VAR>(r, ip.fpos, ip.fneg);
+            P.r[s0 + a] = r;
+            const float rr = pred ? r.x + d : r.x;
+            q[a] = rr > 0.f ? rr : 0.f;
+            pos += q[a];
+        }
+    const RmNorm nrm = rm_norm(pos);
+    const float uni = uniform_prob(na);
+#pragma unroll
+    for (int a = 0; a < kNpA; a++)
+        if (a < na) P.b[s0 + a] = pos > 0.f ? rm_prob(q[a], nrm) : uni;
+}
+
+template <int VAR>
+__global__ void __launch_bounds__(kThreadsN) k_np_up2(DevPlayer P, int j0, int j1, const ItemParams *__restrict__ par,
+                                                      int slot) {
     np_enter();
     const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= j1) return;
     const ItemParams ip = par[slot];
-    up_infoset_cfr(P, j, variant, ip);
+    np_up_step<VAR>(P, j, ip);
 }
 
 // xbar += t^gamma x over the player's sequences (the empty one included);
@@ -581,7 +653,15 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
     NDev &P = c->P[i];
     for (int l = P.L - 1; l >= 0; l--) {
         const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
-        np_launch(k_np_up, blocks(j1 - j0), c->stream, P.dp, j0, j1, variant, (const ItemParams *)c->par, slot);
+        const unsigned g = blocks(j1 - j0);
+        const ItemParams *par = c->par;
+        switch (variant) {
+        case VAR_PLUS: np_launch(k_np_up2<VAR_PLUS>, g, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_DCFR: np_launch(k_np_up2<VAR_DCFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_PCFR_PLUS: np_launch(k_np_up2<VAR_PCFR_PLUS>, g, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_PCFR: np_launch(k_np_up2<VAR_PCFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
+        default: np_launch(k_np_up2<VAR_CFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
+        }
         counted(c);
     }
 }
