@@ -880,26 +880,26 @@ def nplayer_alg_bytes(sizes):
 
     rows(i): 4 (S_i + 1) row pointers + Z_i (4 value + 4 (n - 1) columns)
              + 4 (S_k + 1) for every other player's x (each entry once)
-             + 4 (S_i + 1) u written
+             + 4 (S_i + 1) u written; the average update in the same kernel:
+             per sequence 4 x + 8 + 8 average sums read and written
     up(i):   per sequence 4 u + 8 + 8 regret read and written + 4 + 4
              strategy read and written + 4 child pointers; per decision point
              4 segment start + 4 ev written + 4 ev read by its parent
-    avg(i):  per sequence 4 x + 8 + 8 average sums read and written
     down(i): per sequence 4 b + 4 x written; per decision point 4 parent,
              4 segment start, 4 parent's x
     """
     n = len(sizes)
     S = [z["S"] + 1 for z in sizes]
-    out = {"rows": 0, "up": 0, "avg": 0, "down": 0}
+    out = {"rows": 0, "up": 0, "down": 0}
     for i, z in enumerate(sizes):
-        out["rows"] += 8 * S[i] + z["nnz"] * 4 * n + 4 * sum(S[k] for k in range(n) if k != i)
+        out["rows"] += 8 * S[i] + z["nnz"] * 4 * n + 4 * sum(S[k] for k in range(n) if k != i) + 20 * S[i]
         out["up"] += 32 * S[i] + 12 * z["J"]
-        out["avg"] += 20 * S[i]
         out["down"] += 8 * S[i] + 12 * z["J"]
     return out
 
 
-NP_KERNELS = {"rows": "k_np_rows", "up": "k_np_up2", "avg": "k_np_avg", "down": "k_np_down"}
+NP_KERNELS = {"rows": "k_np_rows (with the average update)", "up": "k_np_up2 and k_np_up_top",
+              "down": "k_np_down and k_np_down_top"}
 
 
 def run_nplayer(args):

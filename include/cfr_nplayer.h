@@ -91,7 +91,7 @@ const char *cfrn_last_error(void);
 /* Sizes of player p (CFR_ERR_ARG for a player outside 0..n-1): out[0]
  * infosets J_p, out[1] non-empty sequences S_p, out[2] levels of its decision
  * points, out[3] nonzeros of its payoff tensor, out[4] players, out[5]
- * iterations done. */
+ * iterations done, out[6] kernel launches of one iteration (all players). */
 int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out);
 
 /* Run n iterations of the variant (CFR_VANILLA, CFR_PLUS, CFR_DCFR,
@@ -136,9 +136,10 @@ int cfrn_get_average_strategy(cfrn_ctx *ctx, int player, double *out, int64_t le
 int cfrn_nash_conv(cfrn_ctx *ctx, double *nash_conv, double *gains);
 
 /* Time each kind of pass with CUDA events over `iters` eager iterations (the
- * state advances): us[0] tensor rows, us[1] bottom-up levels, us[2] average
- * update, us[3] top-down levels, each the mean per iteration summed over
- * players.  Waits for the stream. */
+ * state advances): us[0] tensor rows with the average update (one kernel),
+ * us[1] bottom-up levels, us[2] 0 (no separate kernel), us[3] top-down
+ * levels, each the mean per iteration summed over players.  Waits for the
+ * stream. */
 int cfrn_time_passes(cfrn_ctx *ctx, int iters, int variant, double alpha, double beta, double gamma,
                      int alternating, double *us);
 

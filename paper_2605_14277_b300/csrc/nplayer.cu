@@ -17,11 +17,13 @@
 //   (FP32 and FP64) and the other players' sequences at z (cols, n-1 per
 //   entry, in player order).
 //
-// Passes per player (one launch each; a level per launch, so the level
-// barrier is the launch boundary and no kernel waits on another):
+// Passes per player (a level per launch, so the level barrier is the launch
+// boundary and no kernel waits on another; the small top levels of a player
+// are one launch of one CTA, a block barrier between levels):
 //   rows   u[s] = sum_e val[e] prod_k x_k[col_k[e]]      thread per sequence
+//          and, in the same kernel, the average update xbar += t^gamma x
+//          (x = 0 adds nothing: skipped)
 //   up     level by level, deepest first: np_up_step      thread per decision point
-//   avg    xbar += t^gamma x (x = 0 adds nothing: skipped) thread per sequence
 //   down   level by level, from the top: x = x[p_j] b      thread per decision point
 // The kernels are launched with programmatic dependent launch (np_enter).
 // Iterations are captured as CUDA graphs; the parameters of iteration t come
@@ -291,10 +293,17 @@ struct NX64 {
 // one thread per sequence, each product taken left to right from val in
 // player order and the products added in entry (terminal) order, so the result
 // does not depend on the launch shape.  NO: the other players' count.
+//
+// With `xbar`, the same thread then does the player's average update for its
+// sequence, xbar += t^gamma x (x, the player's own strategy, is the one it
+// plays this iteration: its bottom-up pass, which comes next, does not change
+// it); a sequence with x = 0 adds nothing and is skipped.
 template <int NO>
 __global__ void __launch_bounds__(kThreadsN) k_np_rows(const int32_t *__restrict__ m_ptr, const int32_t *__restrict__ m_col,
                                                        const float *__restrict__ m_val, NX xs, int S1,
-                                                       float *__restrict__ u) {
+                                                       float *__restrict__ u, float2 *__restrict__ xbar,
+                                                       const float *__restrict__ xown,
+                                                       const ItemParams *__restrict__ par, int slot) {
     np_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S1) return;
@@ -308,6 +317,10 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows(const int32_t *__restrict
         acc = __fadd_rn(acc, v);
     }
     u[s] = acc;
+    if (xbar) {
+        const float xv = xown[s];
+        if (xv != 0.f) xbar[s] = ff_add(xbar[s], ff_mul_f(par[slot].w, xv));
+    }
 }
 
 // the same in FP64 for the best responses (the others' normalised averages)
@@ -411,15 +424,39 @@ __global__ void __launch_bounds__(kThreadsN) k_np_up2(DevPlayer P, int j0, int j
     np_up_step<VAR>(P, j, ip);
 }
 
-// xbar += t^gamma x over the player's sequences (the empty one included);
-// a sequence with x = 0 adds exactly nothing and is skipped
-__global__ void __launch_bounds__(kThreadsN) k_np_avg(float2 *__restrict__ xbar, const float *__restrict__ x, int S1,
-                                                      const ItemParams *__restrict__ par, int slot) {
+// The small top levels of a player (levels 0 .. m-1, each at most kTopLevel
+// decision points) in one launch of one CTA: the levels in order, a block
+// barrier between them.  Values of the level below another thread wrote are
+// read through L2 (ld.cg: the writes of a CTA's threads are visible to it
+// after the barrier; L1 could hold a stale line next to them).
+constexpr int kTopLevel = 2048;
+constexpr int kTopThreads = 1024;
+constexpr int kMaxLevels = 32;
+struct NLv {
+    int32_t j[kMaxLevels + 1];
+};
+template <int VAR>
+__global__ void __launch_bounds__(kTopThreads) k_np_up_top(DevPlayer P, NLv lv, int m,
+                                                           const ItemParams *__restrict__ par, int slot) {
     np_enter();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S1) return;
-    const float xv = x[s];
-    if (xv != 0.f) xbar[s] = ff_add(xbar[s], ff_mul_f(par[slot].w, xv));
+    const ItemParams ip = par[slot];
+    for (int l = m - 1; l >= 0; l--) {
+        for (int j = lv.j[l] + threadIdx.x; j < lv.j[l + 1]; j += blockDim.x) np_up_step<VAR>(P, j, ip);
+        __syncthreads();
+    }
+}
+__global__ void __launch_bounds__(kTopThreads) k_np_down_top(const int32_t *__restrict__ inf_seq,
+                                                             const int32_t *__restrict__ inf_par,
+                                                             const float *__restrict__ b, float *__restrict__ x, NLv lv,
+                                                             int m) {
+    np_enter();
+    for (int l = 0; l < m; l++) {
+        for (int j = lv.j[l] + threadIdx.x; j < lv.j[l + 1]; j += blockDim.x) {
+            const float xp = __ldcg(&x[inf_par[j]]);
+            for (int s = inf_seq[j]; s < inf_seq[j + 1]; s++) x[s] = __fmul_rn(xp, b[s]);
+        }
+        __syncthreads();
+    }
 }
 
 // one level of the sequence form, top-down: x[(j,a)] = x[p_j] b_j[a]
@@ -523,6 +560,7 @@ struct NDev {
     int32_t J = 0, S = 0, L = 0;
     int64_t nnz = 0;
     std::vector<int32_t> lvl;     // host copy: decision points of each level
+    int mtop = 0;                 // top levels (from level 0) of at most kTopLevel decision points each
     int32_t *inf_seq = nullptr, *seq_child = nullptr, *inf_par = nullptr, *m_ptr = nullptr, *m_col = nullptr;
     float *m_val = nullptr;
     double *m_val64 = nullptr;
@@ -584,10 +622,10 @@ int dput(cfrn_ctx *c, T **p, const std::vector<T> &v) {
 
 // launch a pass kernel with programmatic dependent launch (np_enter)
 template <class... P, class... A>
-cudaError_t np_launch(void (*fn)(P...), unsigned grid, cudaStream_t st, A &&...a) {
+cudaError_t np_launch_b(void (*fn)(P...), unsigned grid, unsigned block, cudaStream_t st, A &&...a) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3((unsigned)kThreadsN);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -597,13 +635,19 @@ cudaError_t np_launch(void (*fn)(P...), unsigned grid, cudaStream_t st, A &&...a
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, std::forward<A>(a)...);
 }
+template <class... P, class... A>
+cudaError_t np_launch(void (*fn)(P...), unsigned grid, cudaStream_t st, A &&...a) {
+    return np_launch_b(fn, grid, (unsigned)kThreadsN, st, std::forward<A>(a)...);
+}
 
 void counted(cfrn_ctx *c, int k = 1) {
     if (c->capturing) c->captured += k;
     else c->launches += k;
 }
 
-int rows(cfrn_ctx *c, int i, float *out) {
+// the tensor rows of player i into `out`; slot >= 0: also the player's
+// average update with the parameters of that slot
+int rows(cfrn_ctx *c, int i, float *out, int slot = -1) {
     NDev &P = c->P[i];
     NX xs{};
     int k = 0;
@@ -613,14 +657,18 @@ int rows(cfrn_ctx *c, int i, float *out) {
     const unsigned g = blocks(S1);
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
+    float2 *xb = slot >= 0 ? P.xbar : nullptr;
+    const float *xo = P.x;
+    const ItemParams *par = c->par;
+    const int sl = slot >= 0 ? slot : 0;
     switch (c->n - 1) {
-    case 1: e = np_launch(k_np_rows<1>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 2: e = np_launch(k_np_rows<2>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 3: e = np_launch(k_np_rows<3>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 4: e = np_launch(k_np_rows<4>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 5: e = np_launch(k_np_rows<5>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    case 6: e = np_launch(k_np_rows<6>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
-    default: e = np_launch(k_np_rows<7>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out); break;
+    case 1: e = np_launch(k_np_rows<1>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    case 2: e = np_launch(k_np_rows<2>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    case 3: e = np_launch(k_np_rows<3>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    case 4: e = np_launch(k_np_rows<4>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    case 5: e = np_launch(k_np_rows<5>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    case 6: e = np_launch(k_np_rows<6>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    default: e = np_launch(k_np_rows<7>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
     }
     if (e != cudaSuccess) return nfail(CFR_ERR_CUDA, std::string("rows launch: ") + cudaGetErrorString(e));
     counted(c);
@@ -649,9 +697,16 @@ int rows64(cfrn_ctx *c, int i) {
     return CFR_OK;
 }
 
+NLv top_levels(const NDev &P) {
+    NLv lv{};
+    for (int l = 0; l <= P.mtop && l <= kMaxLevels; l++) lv.j[l] = P.lvl[l];
+    return lv;
+}
+
 void up(cfrn_ctx *c, int i, int variant, int slot) {
     NDev &P = c->P[i];
-    for (int l = P.L - 1; l >= 0; l--) {
+    const int lo = P.mtop >= 2 ? P.mtop : 0;   // levels below lo: one launch each
+    for (int l = P.L - 1; l >= lo; l--) {
         const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
         const unsigned g = blocks(j1 - j0);
         const ItemParams *par = c->par;
@@ -664,18 +719,31 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
         }
         counted(c);
     }
-}
-
-void avg(cfrn_ctx *c, int i, int slot) {
-    NDev &P = c->P[i];
-    np_launch(k_np_avg, blocks(P.S + 1), c->stream, P.xbar, (const float *)P.x, P.S + 1, (const ItemParams *)c->par,
-              slot);
-    counted(c);
+    if (lo > 0) {
+        const NLv lv = top_levels(P);
+        const int m = P.mtop;
+        const ItemParams *par = c->par;
+        const unsigned T = kTopThreads;
+        switch (variant) {
+        case VAR_PLUS: np_launch_b(k_np_up_top<VAR_PLUS>, 1u, T, c->stream, P.dp, lv, m, par, slot); break;
+        case VAR_DCFR: np_launch_b(k_np_up_top<VAR_DCFR>, 1u, T, c->stream, P.dp, lv, m, par, slot); break;
+        case VAR_PCFR_PLUS: np_launch_b(k_np_up_top<VAR_PCFR_PLUS>, 1u, T, c->stream, P.dp, lv, m, par, slot); break;
+        case VAR_PCFR: np_launch_b(k_np_up_top<VAR_PCFR>, 1u, T, c->stream, P.dp, lv, m, par, slot); break;
+        default: np_launch_b(k_np_up_top<VAR_CFR>, 1u, T, c->stream, P.dp, lv, m, par, slot); break;
+        }
+        counted(c);
+    }
 }
 
 void down(cfrn_ctx *c, int i) {
     NDev &P = c->P[i];
-    for (int l = 0; l < P.L; l++) {
+    const int lo = P.mtop >= 2 ? P.mtop : 0;
+    if (lo > 0) {
+        np_launch_b(k_np_down_top, 1u, (unsigned)kTopThreads, c->stream, (const int32_t *)P.inf_seq,
+                    (const int32_t *)P.inf_par, (const float *)P.b, P.x, top_levels(P), lo);
+        counted(c);
+    }
+    for (int l = lo; l < P.L; l++) {
         const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
         np_launch(k_np_down, blocks(j1 - j0), c->stream, (const int32_t *)P.inf_seq, (const int32_t *)P.inf_par,
                   (const float *)P.b, P.x, j0, j1);
@@ -701,20 +769,19 @@ int iteration(cfrn_ctx *c, int slot, int variant, bool alternating, cudaEvent_t 
     if (!alternating)
         for (int i = 0; i < c->n; i++) {
             mark(0, i, 0);
-            if (int rc = rows(c, i, c->P[i].u)) return rc;
+            if (int rc = rows(c, i, c->P[i].u, slot)) return rc;
             mark(0, i, 1);
         }
     for (int i = 0; i < c->n; i++) {
         if (alternating) {
             mark(0, i, 0);
-            if (int rc = rows(c, i, c->P[i].u)) return rc;
+            if (int rc = rows(c, i, c->P[i].u, slot)) return rc;
             mark(0, i, 1);
         }
         mark(1, i, 0);
         up(c, i, variant, slot);
         mark(1, i, 1);
         mark(2, i, 0);
-        avg(c, i, slot);
         mark(2, i, 1);
         mark(3, i, 0);
         down(c, i);
@@ -812,6 +879,7 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
         P.L = (int)H.lvl.size() - 1;
         P.lvl = H.lvl;
         P.nnz = (int64_t)H.m_val.size();
+        while (P.mtop < P.L && P.mtop < kMaxLevels && P.lvl[P.mtop + 1] - P.lvl[P.mtop] <= kTopLevel) P.mtop++;
         const int64_t S1 = (int64_t)P.S + 1;
         if ((rc = dput(c, &P.inf_seq, H.inf_seq)) || (rc = dput(c, &P.seq_child, H.seq_child)) ||
             (rc = dput(c, &P.inf_par, H.inf_par)) || (rc = dput(c, &P.m_ptr, H.m_ptr)) ||
@@ -900,6 +968,13 @@ int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out) {
     out[3] = P.nnz;
     out[4] = ctx->n;
     out[5] = ctx->t;
+    int64_t k = 0;   // kernels of one iteration: every player's rows, bottom-up and top-down launches
+    for (int p = 0; p < ctx->n; p++) {
+        const NDev &Q = ctx->P[p];
+        const int levels = Q.mtop >= 2 ? Q.L - Q.mtop + 1 : Q.L;
+        k += 1 + 2 * levels;
+    }
+    out[6] = k;
     return CFR_OK;
 }
 

@@ -85,10 +85,10 @@ class NSolver:
             pass
 
     def size(self, p: int) -> dict:
-        out = np.zeros(6, np.int64)
+        out = np.zeros(7, np.int64)
         _check(lib().cfrn_sizes(self._h, p, _ptr(out)), "cfrn_sizes")
         return {"J": int(out[0]), "S": int(out[1]), "levels": int(out[2]), "nnz": int(out[3]),
-                "players": int(out[4]), "t": int(out[5])}
+                "players": int(out[4]), "t": int(out[5]), "kernels_per_iteration": int(out[6])}
 
     @property
     def t(self) -> int:
@@ -141,7 +141,7 @@ class NSolver:
         _check(lib().cfrn_time_passes(self._h, int(iters), v, float(a0 if alpha is None else alpha),
                                       float(b0 if beta is None else beta), float(g0 if gamma is None else gamma),
                                       int(bool(alternating)), _ptr(us)), "cfrn_time_passes")
-        return {"rows": us[0], "up": us[1], "avg": us[2], "down": us[3]}
+        return {"rows": us[0], "up": us[1], "down": us[3]}
 
     @property
     def launches(self) -> int:

@@ -304,10 +304,13 @@ def test_launch_count(NP):
     tree = G.small_nplayer_game(3, 1)
     s = NP.NSolver(tree)
     L = [s.sizes[i]["levels"] for i in range(3)]
+    per_iter = s.sizes[0]["kernels_per_iteration"]
+    # every player: rows (with the average update), then its bottom-up and
+    # top-down levels, the small top levels merged into one launch each way
+    assert 3 + 2 * 3 <= per_iter <= sum(1 + 2 * l for l in L)
     before = s.launches
     s.set_graph_iterations(16)
     s.iterate(32, "dcfr")
     s.sync()
-    per_iter = sum(1 + 2 * l + 1 for l in L)      # rows, up levels, average, down levels
     assert s.launches - before == 32 * per_iter + 2 * 2   # plus a parameter fill and a tick per graph
     s.close()
