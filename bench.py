@@ -68,15 +68,18 @@ def _workload(name):
     raise ValueError(name)
 
 
-def sources_sha256():
-    """sha256 over the kernel sources (file name, then contents, in name order)."""
-    import glob
+TWO_PLAYER_SOURCES = ("capi.cu", "compiler.cpp", "kernels.cuh", "layout.h", "staged.cuh")
+NPLAYER_SOURCES = ("kernels.cuh", "layout.h", "nplayer.cu")
+
+
+def sources_sha256(files=TWO_PLAYER_SOURCES):
+    """sha256 over the sources a path's kernels are built from (file name,
+    then contents, in name order): by default the two-player passes'."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2605_14277_b300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(os.path.basename(f).encode())
-            h.update(open(f, "rb").read())
+    for name in sorted(files):
+        h.update(name.encode())
+        h.update(open(os.path.join(ROOT, "paper_2605_14277_b300", "csrc", name), "rb").read())
     return h.hexdigest()
 
 
