@@ -117,6 +117,13 @@ int cfrn_sync(cfrn_ctx *ctx);
  * done.  Any pointer may be NULL.  Waits for the stream. */
 int cfrn_get_state(cfrn_ctx *ctx, int player, double *r, double *b, double *xbar, int64_t *t);
 
+/* Resume player p from a checkpoint, in cfrn_get_state's layout: r[S_p],
+ * b[S_p] (every infoset's entries >= 0 and summing to 1 within 1e-5, else
+ * CFR_ERR_ARG), xbar[S_p+1]; the sequence form x is rebuilt from b.  Any of
+ * the three may be NULL (left as it is).  t >= 0 sets the context's iteration
+ * counter (shared by the players), t < 0 leaves it.  Waits for the stream. */
+int cfrn_set_state(cfrn_ctx *ctx, int player, const double *r, const double *b, const double *xbar, int64_t t);
+
 /* Player p's sequence-form strategy x[S_p+1] (the one it plays next; empty
  * sequence first) and the utility u[S_p+1] that the payoff tensor gives
  * against the other players' current strategies (FP32, computed by the same

@@ -1042,6 +1042,55 @@ int cfrn_get_state(cfrn_ctx *ctx, int player, double *r, double *b, double *xbar
     return CFR_OK;
 }
 
+int cfrn_set_state(cfrn_ctx *ctx, int player, const double *r, const double *b, const double *xbar, int64_t t) {
+    if (int rc = check_player(ctx, player)) return rc;
+    if (t >= INT32_MAX) return nfail(CFR_ERR_ARG, "iteration counter too large");
+    if (int rc = cfrn_sync(ctx)) return rc;
+    NDev &P = ctx->P[player];
+    const NPlayerHost &H = ctx->host.pl[player];
+    const int64_t S1 = (int64_t)P.S + 1;
+    auto ff = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    if (b) {   // a distribution at every decision point (caller numbering: off_j + a)
+        std::vector<int32_t> nact((size_t)H.J, 0), caller_off((size_t)H.J + 1, 0);
+        for (int32_t j = 0; j < H.J; j++) nact[H.caller_inf[j]] = H.inf_seq[j + 1] - H.inf_seq[j];
+        for (int32_t j = 0; j < H.J; j++) caller_off[j + 1] = caller_off[j] + nact[j];
+        for (int32_t j = 0; j < H.J; j++) {
+            double sum = 0.0;
+            for (int32_t a = caller_off[j]; a < caller_off[j + 1]; a++) {
+                if (!(b[a] >= 0.0)) return nfail(CFR_ERR_ARG, "strategy entries must be >= 0");
+                sum += b[a];
+            }
+            if (std::fabs(sum - 1.0) > 1e-5) return nfail(CFR_ERR_ARG, "strategy of an infoset does not sum to 1");
+        }
+    }
+    if (r) {
+        std::vector<float2> h(S1, make_float2(0.f, 0.f));
+        for (int64_t k = 1; k <= P.S; k++) h[H.seq_of_caller[k]] = ff(r[k - 1]);
+        NCU(cudaMemcpy(P.r, h.data(), S1 * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    if (xbar) {
+        std::vector<float2> h(S1);
+        h[0] = ff(xbar[0]);
+        for (int64_t k = 1; k <= P.S; k++) h[H.seq_of_caller[k]] = ff(xbar[k]);
+        NCU(cudaMemcpy(P.xbar, h.data(), S1 * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    if (b) {
+        std::vector<float> h(S1, 0.f);
+        for (int64_t k = 1; k <= P.S; k++) h[H.seq_of_caller[k]] = (float)b[k - 1];
+        NCU(cudaMemcpy(P.b, h.data(), S1 * sizeof(float), cudaMemcpyHostToDevice));
+        down(ctx, player);   // the sequence form of the strategy to be played next
+    }
+    if (t >= 0) {
+        const int32_t tt = (int32_t)t;
+        NCU(cudaMemcpy(ctx->t_dev, &tt, sizeof(tt), cudaMemcpyHostToDevice));
+        ctx->t = t;
+    }
+    return cfrn_sync(ctx);
+}
+
 int cfrn_get_values(cfrn_ctx *ctx, int player, double *x, double *u) {
     if (int rc = check_player(ctx, player)) return rc;
     const NDev &P = ctx->P[player];

@@ -38,6 +38,7 @@ def lib():
         L.cfrn_sync.argtypes = [P]
         L.cfrn_get_state.argtypes = [P, i, P, P, P, P]
         L.cfrn_get_values.argtypes = [P, i, P, P]
+        L.cfrn_set_state.argtypes = [P, i, P, P, P, i64]
         L.cfrn_get_average_strategy.argtypes = [P, i, P, i64]
         L.cfrn_nash_conv.argtypes = [P, P, P]
         L.cfrn_time_passes.argtypes = [P, i, i, d, d, d, i, P]
@@ -115,6 +116,19 @@ class NSolver:
         t = ctypes.c_int64()
         _check(lib().cfrn_get_state(self._h, p, _ptr(r), _ptr(b), _ptr(xb), ctypes.byref(t)), "cfrn_get_state")
         return {"r": r, "b": b, "xbar": xb, "t": t.value}
+
+    def set_state(self, p: int, r=None, b=None, xbar=None, t: int = -1):
+        S = self.sizes[p]["S"]
+
+        def arr(a, n):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, np.float64)
+            if a.shape != (n,):
+                raise ValueError(f"expected {n} entries, got {a.shape}")
+            return a
+        r, b, xbar = arr(r, S), arr(b, S), arr(xbar, S + 1)
+        _check(lib().cfrn_set_state(self._h, p, _ptr(r), _ptr(b), _ptr(xbar), int(t)), "cfrn_set_state")
 
     def get_values(self, p: int):
         S = self.sizes[p]["S"]

@@ -314,3 +314,38 @@ def test_launch_count(NP):
     s.sync()
     assert s.launches - before == 32 * per_iter + 2 * 2   # plus a parameter fill and a tick per graph
     s.close()
+
+
+def test_checkpoint_resume(NP):
+    """A context resumed from another's state continues with the same bits;
+    a state taken from the oracle gives one-step parity."""
+    tree = G.small_nplayer_game(3, 1)
+    a = NP.NSolver(tree)
+    a.iterate(30, "pcfr+")
+    b = NP.NSolver(tree)
+    for i in range(3):
+        st = a.get_state(i)
+        b.set_state(i, st["r"], st["b"], st["xbar"], st["t"])
+    assert b.t == 30
+    for i in range(3):
+        xa, xb = a.get_values(i)[0], b.get_values(i)[0]
+        assert np.array_equal(xa, xb)
+    a.iterate(20, "pcfr+")
+    b.iterate(20, "pcfr+")
+    for i in range(3):
+        sa, sb = a.get_state(i), b.get_state(i)
+        for key in ("r", "b", "xbar"):
+            assert np.array_equal(sa[key], sb[key]), key
+    # the oracle's state after 15 iterations, resumed on the GPU
+    o = NOracle(tree)
+    o.iterate(15, DCFR, 1.5, 0.0, 2.0)
+    c = NP.NSolver(tree)
+    for i in range(3):
+        c.set_state(i, o.r[i][1:], o.b[i][1:], o.xbar[i], o.t)
+    check_one_step(c, tree, "dcfr", True, "resumed from the oracle")
+    # refused: a strategy that is not a distribution
+    bad = a.get_state(0)["b"].copy()
+    bad[0] += 0.5
+    from paper_2605_14277_b300.cfr import CFRError
+    with pytest.raises(CFRError):
+        a.set_state(0, b=bad)
