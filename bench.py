@@ -901,6 +901,14 @@ def nplayer_alg_bytes(sizes):
     return out
 
 
+def nplayer_config(tree, variant):
+    """The keys that name the n-player workload, shared by both arms' lines."""
+    return {"workload": tree.name, "nodes": tree.n_nodes, "players": tree.n_players,
+            "terminals": int((tree.kind == G.N_TERMINAL).sum()),
+            "variant": variant + "(1.5,0,2)" if variant == "dcfr" else variant,
+            "updates": "alternating"}
+
+
 NP_KERNELS = {"rows": "k_np_rows (with the average update)", "up": "k_np_up2 and k_np_up_top",
               "down": "k_np_down and k_np_down_top"}
 
@@ -979,9 +987,7 @@ def run_nplayer(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 passes, f32+f32 (Kahan) accumulators, f64 NashConv",
             "data": "synthetic",
-            "config": {"workload": tree.name, "nodes": tree.n_nodes, "players": tree.n_players,
-                       "terminals": int((tree.kind == G.N_TERMINAL).sum()),
-                       "variant": variant + "(1.5,0,2)" if variant == "dcfr" else variant, "updates": "alternating",
+            "config": {**nplayer_config(tree, variant),
                        "S": [z["S"] for z in sizes], "J": [z["J"] for z in sizes], "nnz": [z["nnz"] for z in sizes],
                        "levels": [z["levels"] for z in sizes],
                        "l2": "inputs larger than L2: tensors and state of about 0.3 GB resident vs 126 MiB L2",
@@ -1060,7 +1066,7 @@ def run_reference_nplayer(args):
     line = {"metric": NP_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / k, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": tree.name, "nodes": tree.n_nodes, "players": tree.n_players, "variant": variant},
+            "config": nplayer_config(tree, variant),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "cpu_model": model, "nproc": nproc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -55,3 +55,19 @@ def test_reference_arm_variant_flag():
     d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")][0])
     assert d["config"]["variant"] == "pcfr" and d["config"]["updates"] == "alternating"
     assert "pcfr iterations" in d["cpu_baseline"]["sample"]
+
+
+def test_reference_arm_nplayer():
+    """The n-player workload's reference arm: the n-player oracle on the
+    4.84M-node three-player game, the GPU arm's workload keys."""
+    r = run_bench(["--impl", "reference", "--workload", "nplayer", "--steps", "1", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2605_14277_b300 import games as G
+    assert d["config"] == bench.nplayer_config(G.large_nplayer_game(3), "dcfr")
