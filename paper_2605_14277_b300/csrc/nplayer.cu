@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows64(const int32_t *__restri
 // ev = fma chain over the actions; r, the post-op, regret matching), so the
 // results are identical.  Wider decision points take up_infoset_cfr.
 constexpr int kNpA = 4;
+constexpr int kNpKids = 16;   // children's ev loads in flight (8: slower on wide top levels; 32: spills)
 template <int VAR>
 __device__ __forceinline__ void np_up_step(const DevPlayer &P, int j, const ItemParams &ip) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
@@ -372,15 +373,19 @@ __device__ __forceinline__ void np_up_step(const DevPlayer &P, int j, const Item
 #pragma unroll
     for (int a = 0; a <= kNpA; a++)
         if (a <= na) cb[a] = P.seq_child[s0 + a];
-    // the children's ev, eight loads in flight; child c belongs to the
+    // the children's ev, kNpKids loads in flight; child c belongs to the
     // action a with cb[a] <= c < cb[a+1]
-    const int c0 = cb[0], c1 = cb[na];
-    for (int c = c0; c < c1; c += 8) {
-        float e[8];
+    int c1 = cb[0];   // cb[na], with static indices only (cb stays in registers)
 #pragma unroll
-        for (int k = 0; k < 8; k++) e[k] = __ldcg(&P.ev[min(c + k, c1 - 1)]);
+    for (int a = 1; a <= kNpA; a++)
+        if (a == na) c1 = cb[a];
+    const int c0 = cb[0];
+    for (int c = c0; c < c1; c += kNpKids) {
+        float e[kNpKids];
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < kNpKids; k++) e[k] = __ldcg(&P.ev[min(c + k, c1 - 1)]);
+#pragma unroll
+        for (int k = 0; k < kNpKids; k++) {
             const int cc = c + k;
             if (cc < c1) {
 #pragma unroll
