@@ -82,6 +82,13 @@ typedef struct cfrn_ctx cfrn_ctx;
  * Errors: CFR_ERR_INVALID (bad tree), CFR_ERR_CUDA (allocation or copy). */
 int cfrn_load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out);
 
+/* Compile the tree on the host only (no device work): CFR_OK, or
+ * cfrn_load's CFR_ERR_INVALID / CFR_ERR_ARG with the same message.  sizes
+ * (may be NULL) receives 4 entries per player: infosets J_p, non-empty
+ * sequences S_p, levels of its decision points, nonzeros of its payoff
+ * tensor (terminals where its payoff and the chance reach are nonzero). */
+int cfrn_check_tree(const cfrn_tree_desc *tree, int64_t *sizes);
+
 /* Release the context (waits for its stream first).  NULL is accepted. */
 int cfrn_free(cfrn_ctx *ctx);
 

@@ -956,6 +956,21 @@ extern "C" {
 
 int cfrn_load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) { return load(tree, stream, out); }
 
+int cfrn_check_tree(const cfrn_tree_desc *tree, int64_t *sizes) {
+    if (!tree) return nfail(CFR_ERR_ARG, "NULL tree");
+    NGameHost g;
+    if (int rc = compile_nplayer(*tree, &g)) return rc;
+    if (sizes)
+        for (int p = 0; p < g.n; p++) {
+            const NPlayerHost &H = g.pl[p];
+            sizes[4 * p + 0] = H.J;
+            sizes[4 * p + 1] = H.S;
+            sizes[4 * p + 2] = (int64_t)H.lvl.size() - 1;
+            sizes[4 * p + 3] = (int64_t)H.m_val.size();
+        }
+    return CFR_OK;
+}
+
 int cfrn_free(cfrn_ctx *ctx) {
     free_ctx(ctx);
     return CFR_OK;

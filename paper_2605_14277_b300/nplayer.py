@@ -30,6 +30,7 @@ def lib():
         P, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         L.cfrn_load.argtypes = [ctypes.POINTER(NTreeDesc), P, ctypes.POINTER(P)]
         L.cfrn_free.argtypes = [P]
+        L.cfrn_check_tree.argtypes = [ctypes.POINTER(NTreeDesc), P]
         L.cfrn_last_error.argtypes = []
         L.cfrn_last_error.restype = ctypes.c_char_p
         L.cfrn_sizes.argtypes = [P, i, P]
@@ -57,16 +58,30 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
+def _desc(tree):
+    keep = [np.ascontiguousarray(tree.parent, np.int32), np.ascontiguousarray(tree.kind, np.int8),
+            np.ascontiguousarray(tree.actor, np.int8), np.ascontiguousarray(tree.infoset, np.int32),
+            np.ascontiguousarray(tree.action, np.int32), np.ascontiguousarray(tree.chance_prob, np.float64),
+            np.ascontiguousarray(tree.payoff, np.float64).reshape(-1)]
+    return NTreeDesc(int(tree.n_nodes), int(tree.n_players), *[a.ctypes.data for a in keep]), keep
+
+
+def check_tree(tree):
+    """Compile the tree on the host only: per player {J, S, levels, nnz}
+    (raises CFRError on an invalid tree)."""
+    desc, keep = _desc(tree)
+    out = np.zeros(4 * max(1, int(tree.n_players)), np.int64)
+    _check(lib().cfrn_check_tree(ctypes.byref(desc), _ptr(out)), "cfrn_check_tree")
+    return [{"J": int(out[4 * p]), "S": int(out[4 * p + 1]), "levels": int(out[4 * p + 2]), "nnz": int(out[4 * p + 3])}
+            for p in range(int(tree.n_players))]
+
+
 class NSolver:
     """One n-player game on the current CUDA device (include/cfr_nplayer.h)."""
 
     def __init__(self, tree, stream=None):
         L = lib()
-        self._keep = [np.ascontiguousarray(tree.parent, np.int32), np.ascontiguousarray(tree.kind, np.int8),
-                      np.ascontiguousarray(tree.actor, np.int8), np.ascontiguousarray(tree.infoset, np.int32),
-                      np.ascontiguousarray(tree.action, np.int32), np.ascontiguousarray(tree.chance_prob, np.float64),
-                      np.ascontiguousarray(tree.payoff, np.float64).reshape(-1)]
-        desc = NTreeDesc(int(tree.n_nodes), int(tree.n_players), *[a.ctypes.data for a in self._keep])
+        desc, self._keep = _desc(tree)
         h = ctypes.c_void_p()
         _check(L.cfrn_load(ctypes.byref(desc), _cfr._stream_handle(stream), ctypes.byref(h)), "cfrn_load")
         self._h = h

@@ -140,3 +140,31 @@ def test_load_rejects_bad_arguments_before_device_work(lib):
     bad = _Opts(0, 0)
     bad.reserved[3] = 1
     assert lib.cfr_load_batch_opts(None, 1, None, ctypes.byref(bad), ctypes.byref(h)) == -6
+
+
+def test_nplayer_host_compile_matches_the_oracle(lib):
+    """The n-player host compiler (no device): every player's infoset,
+    sequence and level counts and tensor nonzeros equal the n-player oracle's
+    own parse of the same tree; invalid trees give the loader's message."""
+    import numpy as np
+    from oracle.nplayer import NGame
+    from paper_2605_14277_b300 import games as G
+    from paper_2605_14277_b300 import nplayer as NP
+    from paper_2605_14277_b300.cfr import CFRError
+    trees = [G.kuhn3_game(), G.small_nplayer_game(3, 1), G.small_nplayer_game(4, 2),
+             G.random_nplayer_game(5, 3, depth=6, chance={0: 2}, actions=(2, 3), zero_sum=False),
+             G.random_nplayer_game(8, 4, depth=9, chance={0: 2}, actions=(1, 2), zero_sum=False),
+             G.nplayer_from_two_player(G.poker_game(), 3),
+             G.nplayer_normal_form([np.arange(12.0).reshape(2, 3, 2) - 5.0] * 3)]
+    for tree in trees:
+        got = NP.check_tree(tree)
+        g = NGame(tree)
+        for p, P in enumerate(g.pl):
+            nz = int(np.count_nonzero((g.tpay[:, p] != 0.0) & (g.treach != 0.0)))
+            want = {"J": P.J, "S": P.S, "levels": len(P.levels), "nnz": nz}
+            assert got[p] == want, (tree.name, p, got[p], want)
+    bad = G.kuhn3_game()
+    bad.parent[5] = 7
+    with pytest.raises(CFRError) as ei:
+        NP.check_tree(bad)
+    assert "parent must precede child at node 5" in str(ei.value)
