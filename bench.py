@@ -544,9 +544,10 @@ def run_ours(args):
             "parity": parity,
         }
         if not args.no_sub and world == 1:
-            # the batched and served workloads, bounded, in the same run
+            # the batched, served and n-player workloads, bounded, in the same run
             line["batch"] = batch_summary(args, stream)
             line["serve"] = serve_summary(args, local)
+            line["nplayer"] = nplayer_summary(args, stream)
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -913,6 +914,78 @@ NP_KERNELS = {"rows": "k_np_rows (with the average update)", "up": "k_np_up2 and
               "down": "k_np_down and k_np_down_top"}
 
 
+def nplayer_timed(NP, tree, variant, steps, warmup, stream, dist=None, sampler=None):
+    """Load the n-player game, warm up, time `steps` iterations (CUDA graphs,
+    events on the solver's stream, barriers and the max over ranks), then
+    each kind of pass eagerly.  Returns the solver and the figures."""
+    import torch
+    s = NP.NSolver(tree, stream=stream)
+    sizes = [s.size(i) for i in range(tree.n_players)]
+    k_graph = graph_length(steps)
+    s.set_graph_iterations(k_graph)
+    s.prepare_graph(variant)   # captured before the timed region
+    if sampler:
+        sampler.start()
+    s.iterate(warmup, variant)
+    s.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n0 = s.launches
+    e0.record(stream)
+    s.iterate(steps, variant)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    n_launch = s.launches - n0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    # per kind of pass: CUDA events around its launches (eager, same stream)
+    us = s.time_passes(max(10, min(200, steps // 10)), variant)
+    kb = nplayer_alg_bytes(sizes)
+    hbm, src = peaks()
+    dom = max(us, key=lambda k: us[k])
+    achieved = kb[dom] / (us[dom] * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": f"{NP_KERNELS[dom]} (all its launches of one iteration)",
+                "alg_bytes_per_iteration": kb[dom], "us_per_iteration": us[dom],
+                "per_kind": {k: {"alg_bytes": kb[k], "us": us[k], "frac": kb[k] / (us[k] * 1e-6) / 1e9 / hbm}
+                             for k in us},
+                "peak_source": src}
+    return s, {"sizes": sizes, "k_graph": k_graph, "ms": ms, "n_launch": n_launch, "clocks": clocks,
+               "roofline": roofline, "iter_bytes": sum(kb.values()), "hbm": hbm}
+
+
+def nplayer_summary(args, stream):
+    """The n-player row, bounded, for the default line: the same game and
+    timing as `--workload nplayer` with 512 iterations, and the FP64 NashConv
+    parity of the timed run (the oracle evaluates the GPU's averages)."""
+    from oracle.nplayer import NOracle
+    from paper_2605_14277_b300 import nplayer as NP
+    tree = G.large_nplayer_game(3)
+    variant = "dcfr"
+    s, f = nplayer_timed(NP, tree, variant, 512, 64, stream)
+    o = NOracle(tree)
+    for i in range(tree.n_players):
+        st = s.get_state(i)
+        o.r[i][1:], o.b[i][1:], o.xbar[i], o.t = st["r"], st["b"], st["xbar"].copy(), st["t"]
+    nc_g, _ = s.nash_conv()
+    nc_o, _ = o.nash_conv()
+    s.close()
+    ms = f["ms"]
+    return {"metric": NP_METRIC, "workload": nplayer_config(tree, variant),
+            "value": tree.n_nodes * 512 / (ms * 1e-3), "unit": UNIT, "us_per_iteration": ms / 512 * 1e3,
+            "steps": 512, "warmup": 64, "cuda_graph_iterations": f["k_graph"], "gpu_launches": f["n_launch"],
+            "iteration_frac_of_peak": f["iter_bytes"] / (ms / 512 * 1e-3) / 1e9 / f["hbm"],
+            "roofline": f["roofline"],
+            "parity": {"t": o.t, "nash_conv": nc_g, "oracle_nash_conv": nc_o,
+                       "nash_conv_rel_diff": abs(nc_g - nc_o) / max(abs(nc_o), 1e-300)}}
+
+
 def run_nplayer(args):
     """The n-player row: the 4.84M-node three-player game (payoff tensors)
     under DCFR, node-updates/s over the timed CUDA-graph iterations."""
@@ -930,38 +1003,10 @@ def run_nplayer(args):
     tree = G.large_nplayer_game(3)
     variant = args.variant or "dcfr"
     stream = torch.cuda.Stream()
-    s = NP.NSolver(tree, stream=stream)
-    sizes = [s.size(i) for i in range(tree.n_players)]
-    k_graph = graph_length(args.steps)
-    s.set_graph_iterations(k_graph)
-    sampler = ClockSampler(gpu_uuid(local))
-    sampler.start()
-    s.iterate(args.warmup, variant)
-    s.sync()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    n0 = s.launches
-    e0.record(stream)
-    s.iterate(args.steps, variant)
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.synchronize()
-    n_launch = s.launches - n0
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    s, f = nplayer_timed(NP, tree, variant, args.steps, args.warmup, stream, dist, ClockSampler(gpu_uuid(local)))
+    sizes, k_graph, ms, n_launch, clocks = f["sizes"], f["k_graph"], f["ms"], f["n_launch"], f["clocks"]
     value = sum_over_ranks(tree.n_nodes * args.steps, dist) / (ms * 1e-3)
-    # per kind of pass: CUDA events around its launches (eager, same stream)
-    us = s.time_passes(max(10, min(200, args.steps // 10)), variant)
-    kb = nplayer_alg_bytes(sizes)
-    hbm, src = peaks()
-    dom = max(us, key=lambda k: us[k])
-    achieved = kb[dom] / (us[dom] * 1e-6) / 1e9
-    iter_bytes = sum(kb.values())
+    iter_bytes, hbm = f["iter_bytes"], f["hbm"]
     if rank == 0:
         e2e_iters = min(args.e2e_iters, 2000)
         torch.cuda.synchronize()
@@ -993,12 +1038,7 @@ def run_nplayer(args):
                        "l2": "inputs larger than L2: tensors and state of about 0.3 GB resident vs 126 MiB L2",
                        "parallelism": f"replicas x{world}", "cuda_graph_iterations": k_graph},
             "gpu_launches": n_launch,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "kernel": f"{NP_KERNELS[dom]} (all its launches of one iteration)",
-                         "alg_bytes_per_iteration": kb[dom], "us_per_iteration": us[dom],
-                         "per_kind": {k: {"alg_bytes": kb[k], "us": us[k],
-                                          "frac": kb[k] / (us[k] * 1e-6) / 1e9 / hbm} for k in us},
-                         "peak_source": src},
+            "roofline": f["roofline"],
             "iteration": {"alg_bytes": iter_bytes, "alg_GBps": iter_bytes / (ms / args.steps * 1e-3) / 1e9,
                           "frac_of_peak": iter_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm},
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,

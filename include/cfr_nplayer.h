@@ -114,6 +114,11 @@ int cfrn_iterate(cfrn_ctx *ctx, int64_t n, int variant, double alpha, double bet
  * every pass eagerly. */
 int cfrn_set_graph_iterations(cfrn_ctx *ctx, int k);
 
+/* Capture (and upload) the CUDA graph cfrn_iterate would use for these
+ * arguments, without running it, so that a later timed cfrn_iterate does not
+ * pay for the capture.  CFR_ERR_ARG for a bad variant. */
+int cfrn_prepare_graph(cfrn_ctx *ctx, int variant, double alpha, double beta, double gamma, int alternating);
+
 /* Wait for the context's stream; CFR_ERR_CUDA if a kernel failed. */
 int cfrn_sync(cfrn_ctx *ctx);
 

@@ -1028,6 +1028,13 @@ int cfrn_iterate(cfrn_ctx *ctx, int64_t n, int variant, double alpha, double bet
     return CFR_OK;
 }
 
+int cfrn_prepare_graph(cfrn_ctx *ctx, int variant, double alpha, double beta, double gamma, int alternating) {
+    if (!ctx) return nfail(CFR_ERR_ARG, "NULL context");
+    if (variant < 0 || variant > 4) return nfail(CFR_ERR_ARG, "bad variant");
+    if (ctx->graph_k < 2) return CFR_OK;   // eager launches: no graph
+    return ensure_graph(ctx, ctx->graph_k, variant, alpha, beta, gamma, alternating != 0);
+}
+
 int cfrn_sync(cfrn_ctx *ctx) {
     if (!ctx) return nfail(CFR_ERR_ARG, "NULL context");
     NCU(cudaStreamSynchronize(ctx->stream));

@@ -37,6 +37,7 @@ def lib():
         L.cfrn_iterate.argtypes = [P, i64, i, d, d, d, i]
         L.cfrn_set_graph_iterations.argtypes = [P, i]
         L.cfrn_sync.argtypes = [P]
+        L.cfrn_prepare_graph.argtypes = [P, i, d, d, d, i]
         L.cfrn_get_state.argtypes = [P, i, P, P, P, P]
         L.cfrn_get_values.argtypes = [P, i, P, P]
         L.cfrn_set_state.argtypes = [P, i, P, P, P, i64]
@@ -121,6 +122,13 @@ class NSolver:
         g = g0 if gamma is None else gamma
         _check(lib().cfrn_iterate(self._h, int(n), v, float(a), float(b), float(g), int(bool(alternating))),
                "cfrn_iterate")
+
+    def prepare_graph(self, variant="dcfr", alpha=None, beta=None, gamma=None, alternating=True):
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        a0, b0, g0 = DEFAULT_PARAMS[v]
+        _check(lib().cfrn_prepare_graph(self._h, v, float(a0 if alpha is None else alpha),
+                                        float(b0 if beta is None else beta), float(g0 if gamma is None else gamma),
+                                        int(bool(alternating))), "cfrn_prepare_graph")
 
     def sync(self):
         _check(lib().cfrn_sync(self._h), "cfrn_sync")

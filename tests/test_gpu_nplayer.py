@@ -310,6 +310,8 @@ def test_launch_count(NP):
     assert 3 + 2 * 3 <= per_iter <= sum(1 + 2 * l for l in L)
     before = s.launches
     s.set_graph_iterations(16)
+    s.prepare_graph("dcfr")
+    assert s.launches == before          # capturing runs nothing
     s.iterate(32, "dcfr")
     s.sync()
     assert s.launches - before == 32 * per_iter + 2 * 2   # plus a parameter fill and a tick per graph
