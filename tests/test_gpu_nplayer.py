@@ -102,10 +102,13 @@ def abs_utility(game, i, xs):
     return u
 
 
-def check_one_step(s, tree, variant, alternating, what=""):
+def check_one_step(s, tree, variant, alternating, what="", params=None):
     """One iteration from the GPU's state: the GPU's, against the step the
-    oracle's primitives take from the same state, element-wise."""
+    oracle's primitives take from the same state, element-wise.  params:
+    (alpha, beta, gamma) instead of the variant's defaults."""
     v, (a, b, g) = VARIANTS[variant]
+    if params is not None:
+        a, b, g = params
     n = tree.n_players
     o = oracle_from_gpu(tree, s)
     game = o.g
@@ -117,7 +120,7 @@ def check_one_step(s, tree, variant, alternating, what=""):
         assert elementwise(u_g, u_o, abs_utility(game, i, xg)) <= TOL, ("u", i, what)
     init = [(o.r[i].copy(), o.b[i].copy(), o.xbar[i].copy()) for i in range(n)]
     tt = float(o.t + 1)
-    s.iterate(1, variant, alternating=alternating)
+    s.iterate(1, variant, alpha=a, beta=b, gamma=g, alternating=alternating)
     out = [s.get_state(i) for i in range(n)]
     # The oracle's step for each player, from the oracle's own primitives
     # (Alg. 1 ObserveUtility, the post-op, regret matching, the average):
@@ -351,3 +354,16 @@ def test_checkpoint_resume(NP):
     from paper_2605_14277_b300.cfr import CFRError
     with pytest.raises(CFRError):
         a.set_state(0, b=bad)
+
+
+@pytest.mark.parametrize("variant,params", [("dcfr", (1.0, 0.5, 3.0)), ("dcfr", (2.0, -0.5, 0.0)),
+                                            ("cfr+", (0.0, 0.0, 2.0)), ("pcfr", (0.0, 0.0, 1.5))])
+def test_nondefault_parameters(NP, variant, params):
+    """Non-default DCFR discounts and averaging exponents, both schedules."""
+    for name in ("kuhn3", "four"):
+        tree = games()[name]
+        for alternating in (True, False):
+            s = NP.NSolver(tree)
+            s.iterate(5, variant, *params, alternating=alternating)
+            check_one_step(s, tree, variant, alternating, (name, params), params=params)
+            s.close()
