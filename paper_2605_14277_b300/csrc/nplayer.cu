@@ -48,6 +48,8 @@ namespace {
 
 constexpr int kMaxP = CFRN_MAX_PLAYERS;
 constexpr int kThreadsN = 256;
+constexpr int kLongRow = 32;    // tensor rows of this many entries or more are summed by a warp
+constexpr int kWideKids = 16;   // levels with this many child decision points per sequence go one warp per point
 
 thread_local std::string g_nerr;
 
@@ -303,24 +305,54 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows(const int32_t *__restrict
                                                        const float *__restrict__ m_val, NX xs, int S1,
                                                        float *__restrict__ u, float2 *__restrict__ xbar,
                                                        const float *__restrict__ xown,
-                                                       const ItemParams *__restrict__ par, int slot) {
+                                                       const ItemParams *__restrict__ par, int slot, int long_min) {
     np_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S1) return;
     const int e0 = m_ptr[s], e1 = m_ptr[s + 1];
+    if (e1 - e0 < long_min) {   // longer rows: k_np_rows_long
+        float acc = 0.f;
+        for (int e = e0; e < e1; e++) {
+            float v = m_val[e];
+            const int32_t *c = m_col + (int64_t)e * NO;
+#pragma unroll
+            for (int k = 0; k < NO; k++) v = __fmul_rn(v, __ldg(xs.x[k] + c[k]));
+            acc = __fadd_rn(acc, v);
+        }
+        u[s] = acc;
+    }
+    if (xbar) {
+        const float xv = xown[s];
+        if (xv != 0.f) xbar[s] = ff_add(xbar[s], ff_mul_f(par[slot].w, xv));
+    }
+}
+
+// Rows of kLongRow or more entries (games with many players between a
+// player's decisions), one warp per row: lane k takes the entries k, k+32,
+// ... in order, then a fixed butterfly adds the lanes' sums.  long_rows: the
+// rows' sequences, listed at load.
+template <int NO>
+__global__ void __launch_bounds__(kThreadsN) k_np_rows_long(const int32_t *__restrict__ m_ptr,
+                                                            const int32_t *__restrict__ m_col,
+                                                            const float *__restrict__ m_val, NX xs,
+                                                            const int32_t *__restrict__ long_rows, int n_long,
+                                                            float *__restrict__ u) {
+    np_enter();
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= n_long) return;   // whole warps
+    const int s = long_rows[w];
+    const int e0 = m_ptr[s], e1 = m_ptr[s + 1];
     float acc = 0.f;
-    for (int e = e0; e < e1; e++) {
+    for (int e = e0 + lane; e < e1; e += 32) {
         float v = m_val[e];
         const int32_t *c = m_col + (int64_t)e * NO;
 #pragma unroll
         for (int k = 0; k < NO; k++) v = __fmul_rn(v, __ldg(xs.x[k] + c[k]));
         acc = __fadd_rn(acc, v);
     }
-    u[s] = acc;
-    if (xbar) {
-        const float xv = xown[s];
-        if (xv != 0.f) xbar[s] = ff_add(xbar[s], ff_mul_f(par[slot].w, xv));
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) u[s] = acc;
 }
 
 // the same in FP64 for the best responses (the others' normalised averages)
@@ -427,6 +459,32 @@ __global__ void __launch_bounds__(kThreadsN) k_np_up2(DevPlayer P, int j0, int j
     if (j >= j1) return;
     const ItemParams ip = par[slot];
     np_up_step<VAR>(P, j, ip);
+}
+
+// A level whose sequences have many child decision points (kWideKids or
+// more on average), one warp per decision point: for each of its sequences
+// lane k sums the children k, k+32, ... in order, a fixed butterfly adds the
+// lanes' sums, lane 0 adds them to u; then lane 0 takes the decision point's
+// step with an empty child map (P's seq_child all zero), so V = that u.
+template <int VAR>
+__global__ void __launch_bounds__(kThreadsN) k_np_up_wide(DevPlayer P, const int32_t *__restrict__ seq_child, int j0,
+                                                          int j1, const ItemParams *__restrict__ par, int slot) {
+    np_enter();
+    const int j = j0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= j1) return;   // whole warps
+    const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
+    for (int s = s0; s < s1; s++) {
+        const int c0 = seq_child[s], c1 = seq_child[s + 1];
+        float part = 0.f;
+        for (int c = c0 + lane; c < c1; c += 32) part = __fadd_rn(part, __ldcg(&P.ev[c]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+        if (lane == 0) P.u[s] = __fadd_rn(P.u[s], part);
+    }
+    if (lane == 0) {
+        const ItemParams ip = par[slot];
+        np_up_step<VAR>(P, j, ip);
+    }
 }
 
 // The small top levels of a player (levels 0 .. m-1, each at most kTopLevel
@@ -572,7 +630,12 @@ struct NDev {
     float2 *r = nullptr, *xbar = nullptr;
     float *b = nullptr, *x = nullptr, *u = nullptr, *ev = nullptr, *uq = nullptr;
     double *u64 = nullptr, *ev64 = nullptr, *x64 = nullptr;
+    int32_t *nokids = nullptr;    // [S + 2] zeros: an empty child map (wide levels' step)
+    int32_t *long_rows = nullptr; // sequences whose tensor rows have kLongRow or more entries
+    int n_long = 0;
+    std::vector<uint8_t> wide;    // per level: kWideKids or more child decision points per sequence
     DevPlayer dp{};
+    DevPlayer dp_nokids{};        // dp with the empty child map
 };
 
 unsigned blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kThreadsN - 1) / kThreadsN); }
@@ -666,17 +729,34 @@ int rows(cfrn_ctx *c, int i, float *out, int slot = -1) {
     const float *xo = P.x;
     const ItemParams *par = c->par;
     const int sl = slot >= 0 ? slot : 0;
+    const int lm = P.n_long > 0 ? kLongRow : INT32_MAX;   // rows left to k_np_rows_long
     switch (c->n - 1) {
-    case 1: e = np_launch(k_np_rows<1>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
-    case 2: e = np_launch(k_np_rows<2>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
-    case 3: e = np_launch(k_np_rows<3>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
-    case 4: e = np_launch(k_np_rows<4>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
-    case 5: e = np_launch(k_np_rows<5>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
-    case 6: e = np_launch(k_np_rows<6>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
-    default: e = np_launch(k_np_rows<7>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl); break;
+    case 1: e = np_launch(k_np_rows<1>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
+    case 2: e = np_launch(k_np_rows<2>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
+    case 3: e = np_launch(k_np_rows<3>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
+    case 4: e = np_launch(k_np_rows<4>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
+    case 5: e = np_launch(k_np_rows<5>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
+    case 6: e = np_launch(k_np_rows<6>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
+    default: e = np_launch(k_np_rows<7>, g, st, P.m_ptr, P.m_col, P.m_val, xs, S1, out, xb, xo, par, sl, lm); break;
     }
     if (e != cudaSuccess) return nfail(CFR_ERR_CUDA, std::string("rows launch: ") + cudaGetErrorString(e));
     counted(c);
+    if (P.n_long > 0) {
+        const unsigned gl = blocks(32ll * P.n_long);
+        const int32_t *lr = P.long_rows;
+        const int nl = P.n_long;
+        switch (c->n - 1) {
+        case 1: e = np_launch(k_np_rows_long<1>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        case 2: e = np_launch(k_np_rows_long<2>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        case 3: e = np_launch(k_np_rows_long<3>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        case 4: e = np_launch(k_np_rows_long<4>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        case 5: e = np_launch(k_np_rows_long<5>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        case 6: e = np_launch(k_np_rows_long<6>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        default: e = np_launch(k_np_rows_long<7>, gl, st, P.m_ptr, P.m_col, P.m_val, xs, lr, nl, out); break;
+        }
+        if (e != cudaSuccess) return nfail(CFR_ERR_CUDA, std::string("long rows launch: ") + cudaGetErrorString(e));
+        counted(c);
+    }
     return CFR_OK;
 }
 
@@ -713,8 +793,23 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
     const int lo = P.mtop >= 2 ? P.mtop : 0;   // levels below lo: one launch each
     for (int l = P.L - 1; l >= lo; l--) {
         const int j0 = P.lvl[l], j1 = P.lvl[l + 1];
-        const unsigned g = blocks(j1 - j0);
         const ItemParams *par = c->par;
+        if (P.wide[l]) {
+            const unsigned gw = blocks(32ll * (j1 - j0));
+            const int32_t *sc = P.seq_child;
+            switch (variant) {
+            case VAR_PLUS: np_launch(k_np_up_wide<VAR_PLUS>, gw, c->stream, P.dp_nokids, sc, j0, j1, par, slot); break;
+            case VAR_DCFR: np_launch(k_np_up_wide<VAR_DCFR>, gw, c->stream, P.dp_nokids, sc, j0, j1, par, slot); break;
+            case VAR_PCFR_PLUS:
+                np_launch(k_np_up_wide<VAR_PCFR_PLUS>, gw, c->stream, P.dp_nokids, sc, j0, j1, par, slot);
+                break;
+            case VAR_PCFR: np_launch(k_np_up_wide<VAR_PCFR>, gw, c->stream, P.dp_nokids, sc, j0, j1, par, slot); break;
+            default: np_launch(k_np_up_wide<VAR_CFR>, gw, c->stream, P.dp_nokids, sc, j0, j1, par, slot); break;
+            }
+            counted(c);
+            continue;
+        }
+        const unsigned g = blocks(j1 - j0);
         switch (variant) {
         case VAR_PLUS: np_launch(k_np_up2<VAR_PLUS>, g, c->stream, P.dp, j0, j1, par, slot); break;
         case VAR_DCFR: np_launch(k_np_up2<VAR_DCFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
@@ -884,8 +979,35 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
         P.L = (int)H.lvl.size() - 1;
         P.lvl = H.lvl;
         P.nnz = (int64_t)H.m_val.size();
-        while (P.mtop < P.L && P.mtop < kMaxLevels && P.lvl[P.mtop + 1] - P.lvl[P.mtop] <= kTopLevel) P.mtop++;
         const int64_t S1 = (int64_t)P.S + 1;
+        // levels whose sequences have kWideKids or more child decision points
+        // on average are worked one warp per decision point
+        P.wide.assign(P.L, 0);
+        for (int l = 0; l < P.L; l++) {
+            const int64_t s0 = H.inf_seq[H.lvl[l]], s1 = H.inf_seq[H.lvl[l + 1]];
+            const int64_t kids = (int64_t)H.seq_child[s1] - H.seq_child[s0];
+            P.wide[l] = s1 > s0 && kids >= (int64_t)kWideKids * (s1 - s0);
+        }
+        while (P.mtop < P.L && P.mtop < kMaxLevels && P.lvl[P.mtop + 1] - P.lvl[P.mtop] <= kTopLevel &&
+               !P.wide[P.mtop])
+            P.mtop++;
+        {
+            // rows of kLongRow or more entries go to a warp each, when they hold
+            // at least a tenth of the player's entries (else one more launch
+            // costs more than their serial sums)
+            std::vector<int32_t> lr;
+            int64_t in_long = 0;
+            for (int64_t s = 0; s < S1; s++)
+                if (H.m_ptr[s + 1] - H.m_ptr[s] >= kLongRow) {
+                    lr.push_back((int32_t)s);
+                    in_long += H.m_ptr[s + 1] - H.m_ptr[s];
+                }
+            if (10 * in_long < (int64_t)H.m_val.size()) lr.clear();
+            P.n_long = (int)lr.size();
+            if ((rc = dput(c, &P.long_rows, lr)) || (rc = dalloc(c, &P.nokids, S1 + 1))) return bail(rc);
+            if (cudaMemsetAsync(P.nokids, 0, (S1 + 1) * sizeof(int32_t), c->stream) != cudaSuccess)
+                return bail(nfail(CFR_ERR_CUDA, "initialising the empty child map"));
+        }
         if ((rc = dput(c, &P.inf_seq, H.inf_seq)) || (rc = dput(c, &P.seq_child, H.seq_child)) ||
             (rc = dput(c, &P.inf_par, H.inf_par)) || (rc = dput(c, &P.m_ptr, H.m_ptr)) ||
             (rc = dput(c, &P.m_col, H.m_col)) || (rc = dput(c, &P.m_val, H.m_val)) ||
@@ -908,6 +1030,8 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
         d.ev64 = P.ev64;
         d.S = (int32_t)S1;
         d.G = 1;
+        P.dp_nokids = d;
+        P.dp_nokids.seq_child = P.nokids;
         if (cudaMemsetAsync(P.r, 0, S1 * sizeof(float2), c->stream) != cudaSuccess ||
             cudaMemsetAsync(P.xbar, 0, S1 * sizeof(float2), c->stream) != cudaSuccess ||
             cudaMemsetAsync(P.b, 0, S1 * sizeof(float), c->stream) != cudaSuccess ||
@@ -992,7 +1116,7 @@ int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out) {
     for (int p = 0; p < ctx->n; p++) {
         const NDev &Q = ctx->P[p];
         const int levels = Q.mtop >= 2 ? Q.L - Q.mtop + 1 : Q.L;
-        k += 1 + 2 * levels;
+        k += 1 + (Q.n_long > 0 ? 1 : 0) + 2 * levels;
     }
     out[6] = k;
     return CFR_OK;
