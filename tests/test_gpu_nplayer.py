@@ -46,6 +46,10 @@ def games():
         "four": G.random_nplayer_game(4, 7, depth=8, chance={0: 3, 4: 2}, actions=(2, 3)),
         "five_general_sum": G.random_nplayer_game(5, 3, depth=6, chance={0: 2}, actions=(2, 3), zero_sum=False),
         "two_in_three": G.nplayer_from_two_player(G.small_random_game(1), 3),
+        # six players: the first three have levels of ~110 child decision
+        # points per sequence (worked a warp per decision point), the last
+        # three tensor rows of 32 and more entries (a warp per row)
+        "six_wide": G.random_nplayer_game(6, 11, depth=10, chance={0: 3}, actions=(2, 3)),
     }
 
 
