@@ -193,6 +193,9 @@ class NGame:
 
     @staticmethod
     def post_op(r, variant, t, alpha, beta):
+        """the variant's step after ObserveUtility: CFR+ and PCFR+ floor the
+        regrets (Alg. 3, Alg. 5); DCFR discounts positive ones by
+        t^alpha / (t^alpha + 1), negative ones by t^beta / (t^beta + 1) (Alg. 4)"""
         if variant in (CFR_PLUS, PCFR_PLUS):
             r[1:] = np.maximum(r[1:], 0.0)
         elif variant == DCFR:
@@ -201,7 +204,9 @@ class NGame:
             r[1:] = np.where(r[1:] > 0.0, r[1:] * fp, np.where(r[1:] < 0.0, r[1:] * fn, r[1:]))
 
     def best_response(self, i, xs):
-        """value of player i's best response to the others' sequence-form xs"""
+        """value of player i's best response to the others' sequence-form xs:
+        the bottom-up pass of Alg. 1 with ev_j = max_a V[(j, a)] in place of
+        the strategy's weighted sum; V[0] is the value"""
         P = self.pl[i]
         V = self.utility(i, xs)
         for js in reversed(P.levels):
@@ -225,6 +230,10 @@ class NOracle:
         return NGame.sequence_form(self.g.pl[i], self.b[i])
 
     def _update(self, i, u, xplayed, variant, t, alpha, beta, gamma):
+        """player i's half of iteration t: the average (xbar += t^gamma x^t),
+        ObserveUtility (Alg. 1), the post-op (Alg. 3-4), NextStrategy; for
+        PCFR+ and PCFR, NextStrategy*(m = u) of Alg. 5 (back up r, observe the
+        prediction with the previous strategy, regret matching, restore r)"""
         P = self.g.pl[i]
         self.xbar[i] += t ** gamma * xplayed
         NGame.observe_utility(P, u, self.b[i], self.r[i])
@@ -238,6 +247,9 @@ class NOracle:
             self.b[i] = NGame.regret_matching(P, self.r[i])
 
     def iterate(self, T, variant, alpha=1.5, beta=0.0, gamma=2.0, alternating=True):
+        """T iterations; alternating: players 0..n-1 in turn, each seeing the
+        strategies the players before it just recomputed (Sec. 3.5.1);
+        simultaneous: every utility from the iteration's start"""
         n = self.g.n
         for _ in range(T):
             t = float(self.t + 1)
@@ -258,7 +270,9 @@ class NOracle:
         return [self.xbar[i] / self.xbar[i][0] if self.xbar[i][0] > 0.0 else self.x(i) for i in range(self.g.n)]
 
     def nash_conv(self, xs=None):
-        """(NashConv, per-player gains) of the profile xs (default: the averages)"""
+        """(NashConv, per-player gains) of the profile xs (default: the
+        averages): sum over players of best response minus own value, the
+        n-player form of the exploitability Sec. 4 reports"""
         xs = self.average_profile() if xs is None else xs
         gains = []
         for i in range(self.g.n):
