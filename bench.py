@@ -910,8 +910,9 @@ def nplayer_config(tree, variant):
             "updates": "alternating"}
 
 
-NP_KERNELS = {"rows": "k_np_rows (with the average update)", "up": "k_np_up2 and k_np_up_top",
-              "down": "k_np_down and k_np_down_top"}
+NP_KERNELS = {"rows": "k_np_rows and k_np_rows_long (with the average update)",
+              "up": "k_np_up2, k_np_up_wide and k_np_up_top",
+              "down": "k_np_down_walk (k_np_down and k_np_down_top for players it does not take)"}
 
 
 def nplayer_timed(NP, tree, variant, steps, warmup, stream, dist=None, sampler=None):

@@ -534,6 +534,65 @@ __global__ void __launch_bounds__(kThreadsN) k_np_down(const int32_t *__restrict
     for (int s = inf_seq[j]; s < inf_seq[j + 1]; s++) x[s] = __fmul_rn(xp, b[s]);
 }
 
+// All levels of the sequence form in one launch: a decision point j walks
+// its ancestor sequences p_j, p_(owner of p_j), ... up to the empty sequence
+// through seq_up (the parent sequence of each sequence's decision point),
+// then multiplies their b from the top down, which is the product the
+// level-by-level pass forms, rounding for rounding:
+// x[p_j] = ((1 * b[top]) * ...) * b[p_j], then x[(j,a)] = x[p_j] b_j[a].
+// The walk is a chain of dependent loads, so each thread takes U decision
+// points (j, j + T, ..., T the grid's threads) and interleaves their walks;
+// D bounds a walk's length (a player's levels minus one).  No thread waits
+// on another.
+template <int D, int U>
+__global__ void __launch_bounds__(kThreadsN) k_np_down_walk(const int32_t *__restrict__ inf_seq,
+                                                            const int32_t *__restrict__ inf_par,
+                                                            const int32_t *__restrict__ seq_up,
+                                                            const float *__restrict__ b, float *__restrict__ x, int J) {
+    np_enter();
+    const int64_t T = (int64_t)gridDim.x * blockDim.x, t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // every walk's first loads, and the b of each point's first kNpA
+    // actions, issued together
+    int q[U], d[U], s0[U], s1[U];
+    float bs[U][kNpA];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t j = t + u * T;
+        const bool in = j < J;
+        q[u] = in ? inf_par[j] : 0;
+        s0[u] = in ? inf_seq[j] : 0;
+        s1[u] = in ? inf_seq[j + 1] : 0;
+        d[u] = 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+#pragma unroll
+        for (int a = 0; a < kNpA; a++) bs[u][a] = s0[u] + a < s1[u] ? b[s0[u] + a] : 0.0f;
+    float bb[U][D];
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (q[u] != 0) {
+                bb[u][k] = b[q[u]];
+                q[u] = seq_up[q[u]];
+                d[u] = k + 1;
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        float xp = 1.0f;
+#pragma unroll
+        for (int k = D - 1; k >= 0; k--)
+            if (k < d[u]) xp = __fmul_rn(xp, bb[u][k]);
+#pragma unroll
+        for (int a = 0; a < kNpA; a++)
+            if (s0[u] + a < s1[u]) x[s0[u] + a] = __fmul_rn(xp, bs[u][a]);
+        for (int s = s0[u] + kNpA; s < s1[u]; s++) x[s] = __fmul_rn(xp, b[s]);
+    }
+}
+constexpr int kWalk = 16;   // longest walk (players of at most kWalk + 1 levels)
+
 // initial behavioural strategy: uniform at every decision point
 __global__ void k_np_uniform(const int32_t *__restrict__ inf_seq, float *__restrict__ b, int J) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -631,6 +690,8 @@ struct NDev {
     float *b = nullptr, *x = nullptr, *u = nullptr, *ev = nullptr, *uq = nullptr;
     double *u64 = nullptr, *ev64 = nullptr, *x64 = nullptr;
     int32_t *nokids = nullptr;    // [S + 2] zeros: an empty child map (wide levels' step)
+    int32_t *seq_up = nullptr;    // [S + 1] parent sequence of each sequence's decision point (top-down walk)
+    bool walk = false;            // top-down in one walking launch (2 to kWalk + 1 levels)
     int32_t *long_rows = nullptr; // sequences whose tensor rows have kLongRow or more entries
     int n_long = 0;
     std::vector<uint8_t> wide;    // per level: kWideKids or more child decision points per sequence
@@ -837,6 +898,18 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
 
 void down(cfrn_ctx *c, int i) {
     NDev &P = c->P[i];
+    if (P.walk) {
+        const int32_t *is = P.inf_seq, *ip = P.inf_par, *su = P.seq_up;
+        const float *b = P.b;
+        if (P.L - 1 <= 4)
+            np_launch(k_np_down_walk<4, 2>, blocks((P.J + 1) / 2), c->stream, is, ip, su, b, P.x, P.J);
+        else if (P.L - 1 <= 8)
+            np_launch(k_np_down_walk<8, 2>, blocks((P.J + 1) / 2), c->stream, is, ip, su, b, P.x, P.J);
+        else
+            np_launch(k_np_down_walk<kWalk, 1>, blocks(P.J), c->stream, is, ip, su, b, P.x, P.J);
+        counted(c);
+        return;
+    }
     const int lo = P.mtop >= 2 ? P.mtop : 0;
     if (lo > 0) {
         np_launch_b(k_np_down_top, 1u, (unsigned)kTopThreads, c->stream, (const int32_t *)P.inf_seq,
@@ -971,6 +1044,7 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
         c->own_stream = true;
     }
     c->n = c->host.n;
+    std::vector<int32_t> ups[kMaxP];   // host sources of the seq_up uploads, alive until the sync below
     for (int p = 0; p < c->n; p++) {
         NPlayerHost &H = c->host.pl[p];
         NDev &P = c->P[p];
@@ -1007,6 +1081,16 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
             if ((rc = dput(c, &P.long_rows, lr)) || (rc = dalloc(c, &P.nokids, S1 + 1))) return bail(rc);
             if (cudaMemsetAsync(P.nokids, 0, (S1 + 1) * sizeof(int32_t), c->stream) != cudaSuccess)
                 return bail(nfail(CFR_ERR_CUDA, "initialising the empty child map"));
+        }
+        // top-down in one walking launch for players of 2 to kWalk + 1 levels
+        // (one level: its single launch needs no walk)
+        P.walk = P.J > 0 && P.L >= 2 && P.L - 1 <= kWalk;
+        if (P.walk) {
+            std::vector<int32_t> &up = ups[p];
+            up.assign((size_t)S1, 0);
+            for (int32_t j = 0; j < P.J; j++)
+                for (int32_t s = H.inf_seq[j]; s < H.inf_seq[j + 1]; s++) up[s] = H.inf_par[j];
+            if ((rc = dput(c, &P.seq_up, up))) return bail(rc);
         }
         if ((rc = dput(c, &P.inf_seq, H.inf_seq)) || (rc = dput(c, &P.seq_child, H.seq_child)) ||
             (rc = dput(c, &P.inf_par, H.inf_par)) || (rc = dput(c, &P.m_ptr, H.m_ptr)) ||
@@ -1116,7 +1200,7 @@ int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out) {
     for (int p = 0; p < ctx->n; p++) {
         const NDev &Q = ctx->P[p];
         const int levels = Q.mtop >= 2 ? Q.L - Q.mtop + 1 : Q.L;
-        k += 1 + (Q.n_long > 0 ? 1 : 0) + 2 * levels;
+        k += 1 + (Q.n_long > 0 ? 1 : 0) + levels + (Q.walk ? 1 : levels);
     }
     out[6] = k;
     return CFR_OK;

@@ -297,6 +297,64 @@ def test_degenerate_games(NP):
     s.close()
 
 
+def ladder_game(n, width, depth, split, seed):
+    """A deep perfect-information game: a chance deal of `width`, then the
+    players take turns (0, 1, ..., n-1, 0, ...) to stop (a terminal with N(0,1)
+    payoffs) or go on, for `depth` turns, with a chance split of two after turn
+    `split`.  Every player has depth / n levels: the first ones of `width`
+    decision points, the rest of 2 * width."""
+    rng = np.random.default_rng(seed)
+    parent, kind, actor, infoset, action, cprob = [-1], [G.N_CHANCE], [-1], [-1], [-1], [1.0]
+    n_inf = [0] * n
+
+    def add(par, k, who, act, p):
+        parent.append(par)
+        kind.append(k)
+        actor.append(who)
+        infoset.append(-1)
+        action.append(act)
+        cprob.append(p)
+        return len(parent) - 1
+
+    heads = [add(0, G.N_DECISION, 0, e, 1.0 / width) for e in range(width)]
+    for step in range(depth):
+        who = step % n
+        nxt = []
+        for h in heads:
+            kind[h], actor[h] = G.N_DECISION, who
+            infoset[h] = n_inf[who]
+            n_inf[who] += 1
+            add(h, G.N_TERMINAL, -1, 0, 1.0)
+            if step == depth - 1:
+                add(h, G.N_TERMINAL, -1, 1, 1.0)
+            elif step == split:
+                c = add(h, G.N_CHANCE, -1, 1, 1.0)
+                nxt += [add(c, G.N_DECISION, -1, e, 0.5) for e in range(2)]
+            else:
+                nxt.append(add(h, G.N_DECISION, -1, 1, 1.0))
+        heads = nxt
+    kind = np.array(kind, np.int8)
+    pay = np.where((kind == G.N_TERMINAL)[:, None], rng.standard_normal((len(kind), n)).astype(np.float32), 0.0)
+    pay[:, n - 1] = -pay[:, : n - 1].sum(axis=1)
+    return G.NTree(n, np.array(parent), kind, np.array(actor), np.array(infoset), np.array(action),
+                   np.array(cprob), pay.astype(np.float64))
+
+
+def test_deep_players_take_the_level_by_level_top_down(NP):
+    """Players with more than 17 levels build x level by level (the merged top
+    levels in one launch, the wider ones a launch each) instead of in one
+    walking launch; both agree with the oracle."""
+    tree = ladder_game(3, 1500, 60, 29, 4)
+    s = NP.NSolver(tree)
+    assert all(sz["levels"] == 20 for sz in s.sizes)
+    check_one_step(s, tree, "dcfr", True, "ladder")
+    s.iterate(10, "pcfr+")
+    check_one_step(s, tree, "pcfr+", False, "ladder, t=11")
+    o = oracle_from_gpu(tree, s)
+    assert s.nash_conv()[0] == pytest.approx(o.nash_conv()[0], rel=1e-9, abs=1e-12)
+    s.close()
+
+
 def test_large_game_one_step(NP):
     """The 4.8M-node three-player game: one iteration from the GPU's state at
     t = 3 against the oracle on the full vectors."""
