@@ -491,8 +491,11 @@ __global__ void __launch_bounds__(kThreadsN) k_np_up_wide(DevPlayer P, const int
 // decision points) in one launch of one CTA: the levels in order, a block
 // barrier between them.  Values of the level below another thread wrote are
 // read through L2 (ld.cg: the writes of a CTA's threads are visible to it
-// after the barrier; L1 could hold a stale line next to them).
-constexpr int kTopLevel = 2048;
+// after the barrier; L1 could hold a stale line next to them).  A level of
+// more decision points gets a launch of its own: one SM's scattered loads of
+// its children's ev (a sector each) would take longer than a launch boundary
+// (a three-player game's top launch of 4, 64 and 1,119 points took 24 us).
+constexpr int kTopLevel = 256;
 constexpr int kTopThreads = 1024;
 constexpr int kMaxLevels = 32;
 struct NLv {
