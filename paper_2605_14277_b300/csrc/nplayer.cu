@@ -719,6 +719,7 @@ struct cfrn_ctx {
     cudaGraphExec_t graph = nullptr;
     int g_variant = -1, g_alt = -1, g_k = 0;
     double g_a = 0, g_b = 0, g_g = 0;
+    int sms = 148;                      // SMs of the device (level launches spread over them)
     int64_t launches = 0;               // kernels run (graph replays count theirs)
     int64_t graph_kernels = 0;          // kernels in the current graph
     bool capturing = false;
@@ -873,13 +874,19 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
             counted(c);
             continue;
         }
-        const unsigned g = blocks(j1 - j0);
+        // blocks of 32 to kThreadsN threads, about one per SM when the level
+        // is small: its children's ev are scattered loads, and one SM's share
+        // of them bounds the launch
+        const int64_t n = j1 - j0;
+        const unsigned tb =
+            (unsigned)std::min<int64_t>(kThreadsN, std::max<int64_t>(32, ((n + c->sms - 1) / c->sms + 31) / 32 * 32));
+        const unsigned g = (unsigned)((n + tb - 1) / tb);
         switch (variant) {
-        case VAR_PLUS: np_launch(k_np_up2<VAR_PLUS>, g, c->stream, P.dp, j0, j1, par, slot); break;
-        case VAR_DCFR: np_launch(k_np_up2<VAR_DCFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
-        case VAR_PCFR_PLUS: np_launch(k_np_up2<VAR_PCFR_PLUS>, g, c->stream, P.dp, j0, j1, par, slot); break;
-        case VAR_PCFR: np_launch(k_np_up2<VAR_PCFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
-        default: np_launch(k_np_up2<VAR_CFR>, g, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_PLUS: np_launch_b(k_np_up2<VAR_PLUS>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_DCFR: np_launch_b(k_np_up2<VAR_DCFR>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_PCFR_PLUS: np_launch_b(k_np_up2<VAR_PCFR_PLUS>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
+        case VAR_PCFR: np_launch_b(k_np_up2<VAR_PCFR>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
+        default: np_launch_b(k_np_up2<VAR_CFR>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
         }
         counted(c);
     }
@@ -1045,6 +1052,12 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
             return bail(nfail(CFR_ERR_CUDA, "stream creation failed"));
         c->own_stream = true;
+    }
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c->sms < 1)
+            return bail(nfail(CFR_ERR_CUDA, "querying the device"));
     }
     c->n = c->host.n;
     std::vector<int32_t> ups[kMaxP];   // host sources of the seq_up uploads, alive until the sync below
