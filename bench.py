@@ -877,7 +877,7 @@ def run_serve(args):
 NP_METRIC = "node-updates/s per CFR iteration (DCFR, three-player game, payoff tensors)"
 
 
-def nplayer_alg_bytes(sizes):
+def nplayer_alg_bytes(sizes, deepest_seqs=None):
     """Algorithmic bytes of one n-player iteration, per kind of pass, summed
     over the players (S_i sequences with the empty one, J_i decision points,
     Z_i tensor entries of player i; each array element counted once):
@@ -887,8 +887,10 @@ def nplayer_alg_bytes(sizes):
              + 4 (S_i + 1) u written; the average update in the same kernel:
              per sequence 4 x + 8 + 8 average sums read and written
     up(i):   per sequence 4 u + 8 + 8 regret read and written + 4 + 4
-             strategy read and written + 4 child pointers; per decision point
-             4 segment start + 4 ev written + 4 ev read by its parent
+             strategy read and written + 4 child pointers (none on the
+             player's deepest level, whose sequences have no children:
+             deepest_seqs[i] of them); per decision point 4 segment start
+             + 4 ev written + 4 ev read by its parent
     down(i): per sequence 4 b + 4 x written; per decision point 4 parent,
              4 segment start, 4 parent's x
     """
@@ -897,7 +899,7 @@ def nplayer_alg_bytes(sizes):
     out = {"rows": 0, "up": 0, "down": 0}
     for i, z in enumerate(sizes):
         out["rows"] += 8 * S[i] + z["nnz"] * 4 * n + 4 * sum(S[k] for k in range(n) if k != i) + 20 * S[i]
-        out["up"] += 32 * S[i] + 12 * z["J"]
+        out["up"] += 32 * S[i] + 12 * z["J"] - 4 * (deepest_seqs[i] if deepest_seqs else 0)
         out["down"] += 8 * S[i] + 12 * z["J"]
     return out
 
@@ -947,7 +949,7 @@ def nplayer_timed(NP, tree, variant, steps, warmup, stream, dist=None, sampler=N
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
     # per kind of pass: CUDA events around its launches (eager, same stream)
     us = s.time_passes(max(10, min(200, steps // 10)), variant)
-    kb = nplayer_alg_bytes(sizes)
+    kb = nplayer_alg_bytes(sizes, [lv[-1][1] if lv else 0 for lv in (s.level_sizes(i) for i in range(tree.n_players))])
     hbm, src = peaks()
     dom = max(us, key=lambda k: us[k])
     achieved = kb[dom] / (us[dom] * 1e-6) / 1e9

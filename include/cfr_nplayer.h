@@ -101,6 +101,13 @@ const char *cfrn_last_error(void);
  * iterations done, out[6] kernel launches of one iteration (all players). */
 int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out);
 
+/* The player's decision points and sequences per level (level 0: the decision
+ * points whose parent sequence is the empty one; level l + 1: those below a
+ * sequence of level l): out[2l] decision points, out[2l + 1] sequences, for l
+ * < min(levels, cap); out (host, 2 * cap entries) belongs to the caller.
+ * Errors: CFR_ERR_ARG (bad player, NULL out, cap < 0). */
+int cfrn_level_sizes(const cfrn_ctx *ctx, int player, int64_t *out, int cap);
+
 /* Run n iterations of the variant (CFR_VANILLA, CFR_PLUS, CFR_DCFR,
  * CFR_PCFR_PLUS, CFR_PCFR) with DCFR's alpha, beta and the averaging exponent
  * gamma (iteration t adds t^gamma x^t to the average); alternating != 0 for

@@ -410,7 +410,9 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows64(const int32_t *__restri
 // results are identical.  Wider decision points take up_infoset_cfr.
 constexpr int kNpA = 4;
 constexpr int kNpKids = 16;   // children's ev loads in flight (8: slower on wide top levels; 32: spills)
-template <int VAR>
+// LEAF: a player's deepest level, whose sequences have no child decision
+// points (their child ranges are not read).
+template <int VAR, bool LEAF = false>
 __device__ __forceinline__ void np_up_step(const DevPlayer &P, int j, const ItemParams &ip) {
     const int s0 = P.inf_seq[j], s1 = P.inf_seq[j + 1];
     const int na = s1 - s0;
@@ -430,7 +432,7 @@ __device__ __forceinline__ void np_up_step(const DevPlayer &P, int j, const Item
         }
 #pragma unroll
     for (int a = 0; a <= kNpA; a++)
-        if (a <= na) cb[a] = P.seq_child[s0 + a];
+        if (a <= na) cb[a] = LEAF ? 0 : P.seq_child[s0 + a];
     // the children's ev, kNpKids loads in flight; child c belongs to the
     // action a with cb[a] <= c < cb[a+1]
     int c1 = cb[0];   // cb[na], with static indices only (cb stays in registers)
@@ -477,14 +479,14 @@ __device__ __forceinline__ void np_up_step(const DevPlayer &P, int j, const Item
         if (a < na) P.b[s0 + a] = pos > 0.f ? rm_prob(q[a], nrm) : uni;
 }
 
-template <int VAR>
+template <int VAR, bool LEAF>
 __global__ void __launch_bounds__(kThreadsN) k_np_up2(DevPlayer P, int j0, int j1, const ItemParams *__restrict__ par,
                                                       int slot) {
     np_enter();
     const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= j1) return;
     const ItemParams ip = par[slot];
-    np_up_step<VAR>(P, j, ip);
+    np_up_step<VAR, LEAF>(P, j, ip);
 }
 
 // A level whose sequences have many child decision points (kWideKids or
@@ -891,6 +893,18 @@ NLv top_levels(const NDev &P) {
     return lv;
 }
 
+template <bool LEAF>
+void launch_up2(int variant, unsigned g, unsigned tb, cudaStream_t st, const DevPlayer &dp, int j0, int j1,
+                const ItemParams *par, int slot) {
+    switch (variant) {
+    case VAR_PLUS: np_launch_b(k_np_up2<VAR_PLUS, LEAF>, g, tb, st, dp, j0, j1, par, slot); break;
+    case VAR_DCFR: np_launch_b(k_np_up2<VAR_DCFR, LEAF>, g, tb, st, dp, j0, j1, par, slot); break;
+    case VAR_PCFR_PLUS: np_launch_b(k_np_up2<VAR_PCFR_PLUS, LEAF>, g, tb, st, dp, j0, j1, par, slot); break;
+    case VAR_PCFR: np_launch_b(k_np_up2<VAR_PCFR, LEAF>, g, tb, st, dp, j0, j1, par, slot); break;
+    default: np_launch_b(k_np_up2<VAR_CFR, LEAF>, g, tb, st, dp, j0, j1, par, slot); break;
+    }
+}
+
 void up(cfrn_ctx *c, int i, int variant, int slot) {
     NDev &P = c->P[i];
     const int lo = P.mtop >= 2 ? P.mtop : 0;   // levels below lo: one launch each
@@ -919,13 +933,10 @@ void up(cfrn_ctx *c, int i, int variant, int slot) {
         const unsigned tb =
             (unsigned)std::min<int64_t>(kThreadsN, std::max<int64_t>(32, ((n + c->sms - 1) / c->sms + 31) / 32 * 32));
         const unsigned g = (unsigned)((n + tb - 1) / tb);
-        switch (variant) {
-        case VAR_PLUS: np_launch_b(k_np_up2<VAR_PLUS>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
-        case VAR_DCFR: np_launch_b(k_np_up2<VAR_DCFR>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
-        case VAR_PCFR_PLUS: np_launch_b(k_np_up2<VAR_PCFR_PLUS>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
-        case VAR_PCFR: np_launch_b(k_np_up2<VAR_PCFR>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
-        default: np_launch_b(k_np_up2<VAR_CFR>, g, tb, c->stream, P.dp, j0, j1, par, slot); break;
-        }
+        if (l == P.L - 1)
+            launch_up2<true>(variant, g, tb, c->stream, P.dp, j0, j1, par, slot);
+        else
+            launch_up2<false>(variant, g, tb, c->stream, P.dp, j0, j1, par, slot);
         counted(c);
     }
     if (lo > 0) {
@@ -1259,6 +1270,18 @@ int cfrn_sizes(const cfrn_ctx *ctx, int player, int64_t *out) {
         k += 1 + (Q.n_long > 0 ? 1 : 0) + levels + (Q.walk ? 1 : levels);
     }
     out[6] = k;
+    return CFR_OK;
+}
+
+int cfrn_level_sizes(const cfrn_ctx *ctx, int player, int64_t *out, int cap) {
+    if (int rc = check_player(ctx, player)) return rc;
+    if (!out || cap < 0) return nfail(CFR_ERR_ARG, "NULL output or negative capacity");
+    const NDev &P = ctx->P[player];
+    const NPlayerHost &H = ctx->host.pl[player];
+    for (int l = 0; l < std::min(P.L, cap); l++) {
+        out[2 * l] = P.lvl[l + 1] - P.lvl[l];
+        out[2 * l + 1] = (int64_t)H.inf_seq[P.lvl[l + 1]] - H.inf_seq[P.lvl[l]];
+    }
     return CFR_OK;
 }
 

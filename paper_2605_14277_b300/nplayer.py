@@ -34,6 +34,7 @@ def lib():
         L.cfrn_last_error.argtypes = []
         L.cfrn_last_error.restype = ctypes.c_char_p
         L.cfrn_sizes.argtypes = [P, i, P]
+        L.cfrn_level_sizes.argtypes = [P, i, P, i]
         L.cfrn_iterate.argtypes = [P, i64, i, d, d, d, i]
         L.cfrn_set_graph_iterations.argtypes = [P, i]
         L.cfrn_sync.argtypes = [P]
@@ -106,6 +107,13 @@ class NSolver:
         _check(lib().cfrn_sizes(self._h, p, _ptr(out)), "cfrn_sizes")
         return {"J": int(out[0]), "S": int(out[1]), "levels": int(out[2]), "nnz": int(out[3]),
                 "players": int(out[4]), "t": int(out[5]), "kernels_per_iteration": int(out[6])}
+
+    def level_sizes(self, p: int):
+        """[(decision points, sequences)] of player p's levels, from the top."""
+        L = self.sizes[p]["levels"]
+        out = np.zeros(2 * max(1, L), np.int64)
+        _check(lib().cfrn_level_sizes(self._h, p, _ptr(out), L), "cfrn_level_sizes")
+        return [(int(out[2 * l]), int(out[2 * l + 1])) for l in range(L)]
 
     @property
     def t(self) -> int:

@@ -355,6 +355,18 @@ def test_deep_players_take_the_level_by_level_top_down(NP):
     s.close()
 
 
+def test_level_sizes_match_the_oracle_levels(NP):
+    """cfrn_level_sizes: decision points and sequences per level, against the
+    oracle's own level numbering of each player's sequence form."""
+    for name, tree in games().items():
+        s = NP.NSolver(tree)
+        g = NGame(tree)
+        for i, P in enumerate(g.pl):
+            want = [(len(js), len(P.seqs_of(js))) for js in P.levels]
+            assert s.level_sizes(i) == want, (name, i)
+        s.close()
+
+
 def test_large_game_one_step(NP):
     """The 4.8M-node three-player game: one iteration from the GPU's state at
     t = 3 against the oracle on the full vectors."""
