@@ -353,6 +353,45 @@ __global__ void __launch_bounds__(kThreadsN) k_np_rows(const int32_t *__restrict
     }
 }
 
+// G lanes per row for players with long rows: lane k takes the entries k,
+// k+G, ... in order, a fixed butterfly over the G lanes adds their sums, and
+// lane 0 stores u and does the average update.  G is taken from the game
+// alone (row_lanes below), so the order depends only on the game.  A group's
+// lanes are all in the same warp and share its row, so a group is active or
+// exits as a whole.
+template <int NO, int G>
+__global__ void __launch_bounds__(kThreadsN) k_np_rows_g(const int32_t *__restrict__ m_ptr,
+                                                         const int32_t *__restrict__ m_col,
+                                                         const float *__restrict__ m_val, NX xs, int S1,
+                                                         float *__restrict__ u, float2 *__restrict__ xbar,
+                                                         const float *__restrict__ xown,
+                                                         const ItemParams *__restrict__ par, int slot, int long_min) {
+    np_enter();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = tid / G;
+    if (s >= S1) return;
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+    const int e0 = m_ptr[s], e1 = m_ptr[s + 1];
+    if (e1 - e0 < long_min) {   // longer rows: k_np_rows_long
+        float acc = 0.f;
+        for (int e = e0 + lane; e < e1; e += G) {
+            float v = m_val[e];
+            const int32_t *c = m_col + (int64_t)e * NO;
+#pragma unroll
+            for (int k = 0; k < NO; k++) v = __fmul_rn(v, __ldg(xs.x[k] + c[k]));
+            acc = __fadd_rn(acc, v);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(gmask, acc, o, G));
+        if (lane == 0) u[s] = acc;
+    }
+    if (xbar && lane == 0) {
+        const float xv = xown[s];
+        if (xv != 0.f) xbar[s] = ff_add(xbar[s], ff_mul_f(par[slot].w, xv));
+    }
+}
+
 // Rows of kLongRow or more entries (games with many players between a
 // player's decisions), one warp per row: lane k takes the entries k, k+32,
 // ... in order, then a fixed butterfly adds the lanes' sums.  long_rows: the
@@ -726,6 +765,7 @@ struct NDev {
     int32_t *long_rows = nullptr; // sequences whose tensor rows have kLongRow or more entries
     int n_long = 0;
     bool row_batch = false;       // rows k_np_rows takes average kRowBatch entries or more
+    int row_lanes = 1;            // lanes per row (4, 8, 16: k_np_rows_g)
     std::vector<uint8_t> wide;    // per level: kWideKids or more child decision points per sequence
     DevPlayer dp{};
     DevPlayer dp_nokids{};        // dp with the empty child map
@@ -809,11 +849,31 @@ void counted(cfrn_ctx *c, int k = 1) {
 
 // the tensor rows of player i into `out`; slot >= 0: also the player's
 // average update with the parameters of that slot
+// Lanes per row for a player's rows (nnz entries over rows rows, the long
+// rows left out), from per-player timings of the 3- to 8-player games: about
+// two entries per lane (one thread per row below 8 entries: there more
+// lanes only add shuffles and threads), and 16 lanes for players of at most
+// kFewRows rows, whose launches are too small to fill the device otherwise.
+constexpr int64_t kFewRows = 2048;
+int row_lanes(int64_t nnz, int64_t rows) {
+    if (rows <= 0 || nnz < 2 * rows) return 1;
+    if (rows <= kFewRows) return 16;
+    if (nnz >= 16 * rows) return 8;
+    if (nnz >= 8 * rows) return 4;
+    return 1;
+}
+
 template <int NO>
 cudaError_t launch_rows(bool batch, unsigned g, cudaStream_t st, const NDev &P, NX xs, int S1, float *out, float2 *xb,
                         const float *xo, const ItemParams *par, int sl, int lm) {
     const int32_t *mp = P.m_ptr, *mc = P.m_col;
     const float *mv = P.m_val;
+    switch (P.row_lanes) {
+    case 4: return np_launch(k_np_rows_g<NO, 4>, blocks(4ll * S1), st, mp, mc, mv, xs, S1, out, xb, xo, par, sl, lm);
+    case 8: return np_launch(k_np_rows_g<NO, 8>, blocks(8ll * S1), st, mp, mc, mv, xs, S1, out, xb, xo, par, sl, lm);
+    case 16: return np_launch(k_np_rows_g<NO, 16>, blocks(16ll * S1), st, mp, mc, mv, xs, S1, out, xb, xo, par, sl, lm);
+    default: break;
+    }
     if constexpr (NO <= kRowBatchMaxOthers)
         if (batch) return np_launch(k_np_rows<NO, kRowBatch>, g, st, mp, mc, mv, xs, S1, out, xb, xo, par, sl, lm);
     return np_launch(k_np_rows<NO, 1>, g, st, mp, mc, mv, xs, S1, out, xb, xo, par, sl, lm);
@@ -1145,6 +1205,7 @@ int load(const cfrn_tree_desc *tree, void *stream, cfrn_ctx **out) {
             P.n_long = (int)lr.size();
             const int64_t short_nnz = (int64_t)H.m_val.size() - (lr.empty() ? 0 : in_long);
             P.row_batch = short_nnz >= (int64_t)kRowBatch * (S1 - P.n_long);
+            P.row_lanes = row_lanes(short_nnz, S1 - P.n_long);
             if ((rc = dput(c, &P.long_rows, lr)) || (rc = dalloc(c, &P.nokids, S1 + 1))) return bail(rc);
             if (cudaMemsetAsync(P.nokids, 0, (S1 + 1) * sizeof(int32_t), c->stream) != cudaSuccess)
                 return bail(nfail(CFR_ERR_CUDA, "initialising the empty child map"));
