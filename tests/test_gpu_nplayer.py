@@ -377,6 +377,23 @@ def test_large_game_one_step(NP):
     s.close()
 
 
+def test_five_player_large_game_one_step(NP):
+    """The 4.06M-node five-player game at t = 3 against the oracle on the full
+    vectors: its players' rows take every row path (player 0, 95k rows of
+    17 entries: 8 lanes a row; player 1, 8.8 entries: 4 lanes; players 2-3,
+    one thread a row; player 4 and part of player 0, rows of 32 and more
+    entries: a warp each)."""
+    tree = G.large_nplayer_game(5)
+    game = NGame(tree)
+    avg = [np.bincount(game.tseq[:, i], minlength=P.S + 1) for i, P in enumerate(game.pl)]
+    short = [c[c < 32] for c in avg]
+    assert 16 <= short[0].mean() and len(short[0]) > 2048 and 8 <= short[1].mean() < 16
+    s = NP.NSolver(tree)
+    s.iterate(3, "dcfr")
+    check_one_step(s, tree, "dcfr", True, "large, five players")
+    s.close()
+
+
 def test_launch_count(NP):
     tree = G.small_nplayer_game(3, 1)
     s = NP.NSolver(tree)
